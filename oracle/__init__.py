@@ -1,0 +1,251 @@
+"""CPU oracle for BootMMPM (arXiv 2310.12441, Algorithm 1) -- TEST INFRASTRUCTURE.
+
+Only tests/, the smoke check of __graft_entry__ and the benchmark's CPU
+baseline leg may import this package.  It is independent of the CUDA path:
+it shares no code with it and imports nothing from the product package.
+
+The arithmetic lives in bootmmpm_oracle.c (plain C, exact integers,
+schoolbook negacyclic products).  This module marshals numpy arrays into it.
+
+Parity pins (tests/test_oracle_*.py) tie every function here to what the
+paper fixes: the MMPM group law and closed forms (Lemma 3, Example 1,
+Lemma 6), the look-up property (Lemma 7), the exact error identities of the
+external product (Eq. (error:grow)), of sample extraction (Eq.
+(equ-sam-extr)) and of key switching (Eq. (equ-key-swi)), the FHEW/TFHE test
+polynomial for m = 1, and end-to-end decryption of bootstrapped outputs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from .build import build_oracle
+
+_lib = None
+
+u64p = C.POINTER(C.c_uint64)
+u32p = C.POINTER(C.c_uint32)
+i8p = C.POINTER(C.c_int8)
+
+
+class _Params(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("N", C.c_uint32), ("log2_B", C.c_uint32),
+                ("l_B", C.c_uint32), ("log2_Bks", C.c_uint32), ("l_ks", C.c_uint32),
+                ("Q", C.c_uint64)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build_oracle())
+        L.orc_poly_mul.argtypes = [C.c_uint32, C.c_uint64, u64p, u64p, u64p]
+        L.orc_mmpm_apply.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64, u64p, u64p]
+        L.orc_test_vector.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64, u32p, u64p]
+        L.orc_decompose.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, u64p]
+        L.orc_external_product.argtypes = [C.POINTER(_Params), u64p, u64p, u64p, u64p, u64p]
+        L.orc_cmux.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_uint64, u64p, u64p, u64p, C.c_int]
+        L.orc_blind_rotate.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_uint32, u64p,
+                                       C.c_uint32, u64p, u32p, u64p, C.c_int]
+        L.orc_blind_rotate.restype = C.c_int
+        L.orc_sample_extract.argtypes = [C.c_uint32, C.c_uint64, u64p, u64p, u64p]
+        L.orc_ks_gadget.argtypes = [C.POINTER(_Params), C.c_uint32]
+        L.orc_ks_gadget.restype = C.c_uint64
+        L.orc_ks_digits.argtypes = [C.POINTER(_Params), C.c_uint64, u32p]
+        L.orc_key_switch.argtypes = [C.POINTER(_Params), u64p, u64p, u64p]
+        L.orc_keygen_bsk.argtypes = [C.POINTER(_Params), i8p, i8p, u64p, i8p, C.c_uint32,
+                                     C.c_uint32, u64p]
+        L.orc_keygen_ksk.argtypes = [C.POINTER(_Params), i8p, i8p, u64p, i8p, u64p]
+        L.orc_encrypt.argtypes = [C.c_uint32, C.c_uint64, C.c_uint32, i8p, u32p, u64p, i8p,
+                                  C.c_size_t, u64p]
+        L.orc_lwe_phase.argtypes = [C.c_uint32, C.c_uint64, i8p, u64p]
+        L.orc_lwe_phase.restype = C.c_uint64
+        L.orc_decrypt.argtypes = [C.c_uint32, C.c_uint64, C.c_uint32, i8p, u64p, C.c_size_t, u32p]
+        L.orc_rlwe_phase.argtypes = [C.c_uint32, C.c_uint64, i8p, u64p, u64p, u64p]
+        L.orc_bootstrap.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_uint32, u64p, C.c_uint32,
+                                    u64p, u64p, u32p, C.c_size_t, u64p]
+        L.orc_bootstrap.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a, dtype, ptr):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ptr)
+
+
+def _params(kp) -> _Params:
+    return _Params(kp.n, kp.N, kp.log2_B, kp.l_B, kp.log2_Bks, kp.l_ks, kp.Q)
+
+
+# -- ring and group ---------------------------------------------------------
+
+def poly_mul(N: int, Q: int, a, b) -> np.ndarray:
+    a, pa = _p(a, np.uint64, u64p)
+    b, pb = _p(b, np.uint64, u64p)
+    out = np.empty(N, np.uint64)
+    lib().orc_poly_mul(N, Q, pa, pb, out.ctypes.data_as(u64p))
+    return out
+
+
+def mmpm_apply(N: int, m: int, Q: int, c: int, vec) -> np.ndarray:
+    """P(c) times an RLWE vector [m][2][N]."""
+    vec, pv = _p(vec, np.uint64, u64p)
+    out = np.empty((m, 2, N), np.uint64)
+    lib().orc_mmpm_apply(N, m, Q, int(c), pv, out.ctypes.data_as(u64p))
+    return out
+
+
+def test_vector(N: int, m: int, t: int, Q: int, lut) -> np.ndarray:
+    lut, pl = _p(lut, np.uint32, u32p)
+    v = np.empty((m, N), np.uint64)
+    lib().orc_test_vector(N, m, t, Q, pl, v.ctypes.data_as(u64p))
+    return v
+
+
+def decompose(x: int, log2_B: int, l_B: int) -> np.ndarray:
+    d = np.empty(l_B, np.uint64)
+    lib().orc_decompose(int(x), log2_B, l_B, d.ctypes.data_as(u64p))
+    return d
+
+
+# -- RLWE / RGSW --------------------------------------------------------------
+
+def external_product(kp, a, b, C_rgsw):
+    a, pa = _p(a, np.uint64, u64p)
+    b, pb = _p(b, np.uint64, u64p)
+    Cr, pc = _p(C_rgsw, np.uint64, u64p)
+    oa = np.empty(kp.N, np.uint64)
+    ob = np.empty(kp.N, np.uint64)
+    prm = _params(kp)
+    lib().orc_external_product(C.byref(prm), pa, pb, pc, oa.ctypes.data_as(u64p),
+                               ob.ctypes.data_as(u64p))
+    return oa, ob
+
+
+def cmux(kp, m: int, ak: int, Cp, Cm, acc, parallel: bool = True) -> np.ndarray:
+    acc = np.array(acc, dtype=np.uint64, copy=True, order="C")
+    Cp, pp = _p(Cp, np.uint64, u64p)
+    Cm, pm = _p(Cm, np.uint64, u64p)
+    prm = _params(kp)
+    lib().orc_cmux(C.byref(prm), m, int(ak), pp, pm, acc.ctypes.data_as(u64p), int(parallel))
+    return acc
+
+
+def blind_rotate(kp, m: int, t: int, bsk, ct, lut, parallel: bool = True) -> np.ndarray:
+    bsk, pb = _p(bsk, np.uint64, u64p)
+    ct, pc = _p(ct, np.uint64, u64p)
+    lut, pl = _p(lut, np.uint32, u32p)
+    acc = np.empty((m, 2, kp.N), np.uint64)
+    prm = _params(kp)
+    rc = lib().orc_blind_rotate(C.byref(prm), m, t, pb, bsk.shape[0], pc, pl,
+                                acc.ctypes.data_as(u64p), int(parallel))
+    if rc != 0:
+        raise ValueError("ciphertext uses a bootstrapping key that was not provided")
+    return acc
+
+
+def sample_extract(N: int, Q: int, a, b) -> np.ndarray:
+    a, pa = _p(a, np.uint64, u64p)
+    b, pb = _p(b, np.uint64, u64p)
+    out = np.empty(N + 1, np.uint64)
+    lib().orc_sample_extract(N, Q, pa, pb, out.ctypes.data_as(u64p))
+    return out
+
+
+def ks_gadget(kp, j: int) -> int:
+    prm = _params(kp)
+    return int(lib().orc_ks_gadget(C.byref(prm), j))
+
+
+def ks_digits(kp, a: int) -> np.ndarray:
+    prm = _params(kp)
+    d = np.empty(kp.l_ks, np.uint32)
+    lib().orc_ks_digits(C.byref(prm), int(a), d.ctypes.data_as(u32p))
+    return d
+
+
+def key_switch(kp, lwe_N, ksk) -> np.ndarray:
+    lwe_N, pl = _p(lwe_N, np.uint64, u64p)
+    ksk, pk = _p(ksk, np.uint64, u64p)
+    out = np.empty(kp.n + 1, np.uint64)
+    prm = _params(kp)
+    lib().orc_key_switch(C.byref(prm), pl, pk, out.ctypes.data_as(u64p))
+    return out
+
+
+# -- keys, encryption -------------------------------------------------------------
+
+def keygen_bsk(kp, rnd: dict, k0: int = 0, k1: int | None = None) -> np.ndarray:
+    """[k1-k0][2][2 l_B][2][N] coefficient-domain bootstrapping keys."""
+    k1 = rnd["bsk_mask"].shape[0] if k1 is None else k1
+    s, ps = _p(rnd["s"], np.int8, i8p)
+    z, pz = _p(rnd["z"], np.int8, i8p)
+    mk, pm = _p(rnd["bsk_mask"], np.uint64, u64p)
+    er, pe = _p(rnd["bsk_err"], np.int8, i8p)
+    out = np.empty((k1 - k0, 2, 2 * kp.l_B, 2, kp.N), np.uint64)
+    prm = _params(kp)
+    lib().orc_keygen_bsk(C.byref(prm), ps, pz, pm, pe, k0, k1, out.ctypes.data_as(u64p))
+    return out
+
+
+def keygen_ksk(kp, rnd: dict) -> np.ndarray:
+    """[N][l_ks][B_ks-1][n+1] key-switching keys."""
+    s, ps = _p(rnd["s"], np.int8, i8p)
+    z, pz = _p(rnd["z"], np.int8, i8p)
+    mk, pm = _p(rnd["ksk_mask"], np.uint64, u64p)
+    er, pe = _p(rnd["ksk_err"], np.int8, i8p)
+    out = np.empty((kp.N, kp.l_ks, kp.Bks - 1, kp.n + 1), np.uint64)
+    prm = _params(kp)
+    lib().orc_keygen_ksk(C.byref(prm), ps, pz, pm, pe, out.ctypes.data_as(u64p))
+    return out
+
+
+def encrypt(n: int, q: int, t: int, s, msg, mask, err) -> np.ndarray:
+    s, ps = _p(s, np.int8, i8p)
+    msg, pmsg = _p(msg, np.uint32, u32p)
+    mask, pm = _p(mask, np.uint64, u64p)
+    err, pe = _p(err, np.int8, i8p)
+    count = msg.shape[0]
+    ct = np.empty((count, n + 1), np.uint64)
+    lib().orc_encrypt(n, q, t, ps, pmsg, pm, pe, count, ct.ctypes.data_as(u64p))
+    return ct
+
+
+def lwe_phase(n: int, q: int, s, ct) -> int:
+    s, ps = _p(s, np.int8, i8p)
+    ct, pc = _p(ct, np.uint64, u64p)
+    return int(lib().orc_lwe_phase(n, q, ps, pc))
+
+
+def decrypt(n: int, q: int, t: int, s, ct) -> np.ndarray:
+    s, ps = _p(s, np.int8, i8p)
+    ct, pc = _p(np.atleast_2d(ct), np.uint64, u64p)
+    out = np.empty(ct.shape[0], np.uint32)
+    lib().orc_decrypt(n, q, t, ps, pc, ct.shape[0], out.ctypes.data_as(u32p))
+    return out
+
+
+def rlwe_phase(N: int, Q: int, z, a, b) -> np.ndarray:
+    z, pz = _p(z, np.int8, i8p)
+    a, pa = _p(a, np.uint64, u64p)
+    b, pb = _p(b, np.uint64, u64p)
+    out = np.empty(N, np.uint64)
+    lib().orc_rlwe_phase(N, Q, pz, pa, pb, out.ctypes.data_as(u64p))
+    return out
+
+
+def bootstrap(kp, m: int, t: int, bsk, ksk, ct_in, luts) -> np.ndarray:
+    """Algorithm 1 (modulus switches excluded) for count ciphertexts."""
+    bsk, pb = _p(bsk, np.uint64, u64p)
+    ksk, pk = _p(ksk, np.uint64, u64p)
+    ct_in, pc = _p(np.atleast_2d(ct_in), np.uint64, u64p)
+    luts, pl = _p(np.atleast_2d(luts), np.uint32, u32p)
+    count = ct_in.shape[0]
+    out = np.empty((count, kp.n + 1), np.uint64)
+    prm = _params(kp)
+    rc = lib().orc_bootstrap(C.byref(prm), m, t, pb, bsk.shape[0], pk, pc, pl, count,
+                             out.ctypes.data_as(u64p))
+    if rc != 0:
+        raise ValueError("ciphertext uses a bootstrapping key that was not provided")
+    return out

@@ -1,0 +1,32 @@
+"""Builds the oracle's shared library (plain C, gcc, OpenMP when available).
+
+Test infrastructure only: see the header of bootmmpm_oracle.c.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "bootmmpm_oracle.c")
+LIB = os.path.join(HERE, "liboracle.so")
+
+
+def build_oracle(force: bool = False, verbose: bool = False) -> str:
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", LIB + ".tmp", SRC]
+    for extra in (["-fopenmp"], []):
+        cmd = base[:2] + extra + base[2:]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode == 0:
+            os.replace(LIB + ".tmp", LIB)
+            if verbose:
+                print(" ".join(cmd), file=sys.stderr)
+            return LIB
+    raise RuntimeError("oracle build failed:\n" + r.stderr)
+
+
+if __name__ == "__main__":
+    print(build_oracle(force=True, verbose=True))
