@@ -1,0 +1,333 @@
+"""Benchmark: BootMMPM bootstraps/s on one GB300 (batched, bit-exact).
+
+One step = one batch of the workload (default: 4096 ciphertexts, n = 630,
+N = 1024, m = 4, t = 2^10) through the whole hot path: test vector and ACC
+initialisation, n CMux steps, sample extraction, key switching.  Inputs sit
+in HBM before the timed region; L2 is flushed between timed steps (the keys,
+236 MiB BSK and 518 MiB KSK, exceed L2 anyway).
+
+Also reported: the plain form (one ciphertext per launch), the end-to-end
+rate through the host-buffer C-ABI call, the blind-rotation kernel's integer
+roofline, SM clocks during the timed region, and the CPU oracle's rate on a
+bounded sample (`--impl reference` prints the oracle arm alone).
+
+Multi-GPU: independent replicas (weak scaling), one process per GPU under
+torchrun; each rank bootstraps its own batch; value = total / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2310_12441_gb300 import params as P  # noqa: E402
+from paper_2310_12441_gb300 import synth  # noqa: E402
+
+METRIC = "bootstraps/s on 1 GB300 (batched, bit-exact)"
+
+
+def modmuls_per_bootstrap(kp, m):
+    """Algorithmic 64-bit modular multiplications of one bootstrap: per CMux
+    step and row, 4 l_B forward and 2 inverse negacyclic NTTs of (N/2) log2 N
+    butterflies, and 8 l_B N multiply-accumulates against the key."""
+    import math
+    N, lB = kp.N, kp.l_B
+    return kp.n * m * ((4 * lB + 2) * (N // 2) * int(math.log2(N)) + 8 * lB * N)
+
+
+class ClockSampler:
+    """Samples nvidia-smi during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 7
+                          for i in range(4) if r[3 + i].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(sm)}
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle arm
+# ---------------------------------------------------------------------------
+
+def oracle_rate(w, cores_hint=None, steps_sample=8, seed=0):
+    """Oracle bootstraps/s on a bounded sample: `cores` ciphertexts of the
+    workload with only the first `steps_sample` CMux steps (the others have
+    a_k = 0), then scaled to n steps; the key switch is timed in full."""
+    import oracle
+    kp, m, t = w.keys, w.shape.m, w.shape.t
+    cores = cores_hint or os.cpu_count() or 1
+    S = cores
+    rnd = synth.key_randomness(kp, 1000 + w.seed_base, bsk_keys=steps_sample)
+    bsk = oracle.keygen_bsk(kp, rnd)
+    ksk = oracle.keygen_ksk(kp, rnd)
+    qp = 2 * kp.N * m
+    msg = synth.messages(t, S, 3000 + w.seed_base + seed)
+    enc = synth.encryption_randomness(kp.n, qp, kp.sigma, S, 4000 + w.seed_base + seed,
+                                      prefix=steps_sample)
+    ct = oracle.encrypt(kp.n, qp, t, rnd["s"], msg, enc["mask"], enc["err"])
+    luts, _ = synth.luts(t, S, 2000 + w.seed_base + seed)
+    t0 = time.perf_counter()
+    oracle.bootstrap(kp, m, t, bsk, ksk, ct, luts)
+    dt = time.perf_counter() - t0
+    # split: time one key switch per ciphertext separately to scale the rest
+    t1 = time.perf_counter()
+    lwe = np.zeros((S, kp.N + 1), np.uint64)
+    for i in range(S):
+        oracle.key_switch(kp, lwe[i], ksk)
+    ks = (time.perf_counter() - t1) / S          # serial, one core
+    per_ct_rot = max(dt - ks, 1e-9)              # wall, S in parallel
+    per_boot_wall = per_ct_rot * kp.n / steps_sample + ks
+    rate = S / per_boot_wall
+    sample = (f"{S} ciphertexts x first {steps_sample} of {kp.n} CMux steps "
+              f"(+ full key switch), scaled to n steps; {dt:.1f} s wall")
+    return rate, cores, sample
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    for s in range(args.steps):
+        r, cores, sample = oracle_rate(w, steps_sample=4, seed=s)
+        vals.append(r)
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "bootstraps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * w.count / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": config_of(w, args),
+            "cpu_baseline": {"value": v, "unit": "bootstraps/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "bootstraps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(w, args):
+    kp = w.keys
+    return {"workload": w.name, "count": args.count or w.count, "n": kp.n, "N": kp.N,
+            "m": w.shape.m, "t": w.shape.t, "Q": kp.Q, "B": kp.B, "l_B": kp.l_B,
+            "B_ks": kp.Bks, "l_ks": kp.l_ks, "l2": "flushed between timed steps",
+            "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2310_12441_gb300 import api
+
+    rank, world, local = dist_info()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kp, m, t = w.keys, w.shape.m, w.shape.t
+    count = args.count or w.count
+    api.load(build_if_needed=(rank == 0))
+
+    rnd = synth.key_randomness(kp, 1000 + w.seed_base)
+    sk, ek = api.bm_keygen(kp, rnd, local)
+    del rnd
+    qp = 2 * kp.N * m
+    seed = w.seed_base + 100 * rank
+    msg = synth.messages(t, count, 3000 + seed)
+    enc = synth.encryption_randomness(kp.n, qp, kp.sigma, count, 4000 + seed)
+    ct = api.bm_encrypt(sk, qp, t, msg, enc["mask"], enc["err"])
+    luts, _ = synth.luts(t, count, 2000 + seed, mix=w.lut_mix)
+    W = kp.n + 1
+    jobs = api.make_jobs(0, m, t, np.arange(count) * W, np.arange(count) * t, np.arange(count) * W)
+    d_in = api.to_device_u64(ct.ravel(), dev)
+    d_lut = api.to_device_u32(luts.ravel(), dev)
+    d_out = torch.zeros(count * W, dtype=torch.int64, device=dev)
+    ws = api.workspace(api.bm_workspace_bytes([ek], jobs), dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        api.bm_bootstrap_batch([ek], jobs, d_in, d_lut, d_out, ws, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    assert api.bm_workspace_status(ws, stream) == 0
+
+    # correctness spot check of this run's outputs: decryption (whole batch)
+    out = api.from_device_u64(d_out).reshape(count, W)
+    dec_in = api.bm_decrypt(sk, qp, t, ct)
+    dec_out = api.bm_decrypt(sk, kp.Q, t, out)
+    failures = int((dec_out != luts[np.arange(count), dec_in]).sum())
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(ms))
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = count * world * args.steps / (total_ms * 1e-3)
+
+    # kernel-level timing of the blind rotation alone (same jobs, same launch
+    # configuration; bm_blind_rotate adds one ACC copy of m*2*N words per job)
+    d_acc = torch.zeros(count * 2 * m * kp.N, dtype=torch.int64, device=dev)
+    jobs_acc = jobs.copy()
+    jobs_acc["out_off"] = np.arange(count) * 2 * m * kp.N
+    rot_ms = []
+    for i in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        api.bm_blind_rotate([ek], jobs_acc, 1 << 30, d_in, d_lut, d_acc, ws, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        rot_ms.append(a.elapsed_time(b))
+    del d_acc
+
+    result = {"metric": METRIC, "value": value, "unit": "bootstraps/s", "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+              "data": "synthetic", "config": config_of(w, args),
+              "decrypt_failures": failures, "gpu_launches": 2 * args.steps}
+    if rank == 0:
+        clocks = clk.summary()
+        result["clocks"] = clocks
+        # roofline of the dominant kernel: blind rotation
+        peak = api.bm_modmul_peak(local, 1 << 14)
+        mm = modmuls_per_bootstrap(kp, m) * count
+        rot_s = float(np.mean(rot_ms)) * 1e-3
+        result["roofline"] = {"bound": "alu", "achieved": mm / rot_s / 1e9,
+                              "peak": peak / 1e9, "unit": "Gmodmul/s",
+                              "frac": (mm / rot_s) / peak, "traffic": None,
+                              "kernel": "k_blind_rotate", "kernel_ms": rot_s * 1e3,
+                              "modmuls_per_launch": mm}
+        # plain form: one ciphertext per launch
+        if args.plain:
+            P_ = min(args.plain, count)
+            j1 = [jobs[i:i + 1] for i in range(P_)]
+            for i in range(2):
+                api.bm_bootstrap_batch([ek], j1[i], d_in, d_lut, d_out, ws, stream)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for i in range(P_):
+                api.bm_bootstrap_batch([ek], j1[i], d_in, d_lut, d_out, ws, stream)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            pv = P_ / (a.elapsed_time(b) * 1e-3)
+            result["plain"] = {"value": pv, "unit": "bootstraps/s", "ciphertexts": P_,
+                               "batched_over_plain": value / pv}
+        # end to end through the host-buffer C-ABI call (pinned host memory)
+        h_in = torch.from_numpy(ct.ravel().view(np.int64)).pin_memory()
+        h_lut = torch.from_numpy(luts.ravel().view(np.int32)).pin_memory()
+        h_out = torch.zeros(count * W, dtype=torch.int64).pin_memory()
+        ws2 = api.workspace(api.bm_workspace_bytes([ek], jobs) + api.bm_host_staging_bytes([ek], jobs) + 4096, dev)
+        api.bm_bootstrap_batch_host([ek], jobs, h_in, h_lut, h_out, ws2, stream)
+        e2e_ms = []
+        for i in range(max(1, min(args.steps, 3))):
+            flush.fill_(2)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            api.bm_bootstrap_batch_host([ek], jobs, h_in, h_lut, h_out, ws2, stream)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        result["e2e"] = {"value": count / (np.mean(e2e_ms) * 1e-3), "unit": "bootstraps/s",
+                         "h2d_bytes_per_step": int(h_in.numel() * 8 + h_lut.numel() * 4),
+                         "d2h_bytes_per_step": int(h_out.numel() * 8)}
+        if not args.no_cpu:
+            r, cores, sample = oracle_rate(w, steps_sample=args.cpu_steps)
+            result["cpu_baseline"] = {"value": r, "unit": "bootstraps/s", "cores": cores,
+                                      "kind": "oracle", "sample": sample}
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=P.BATCH_N1024.name, choices=sorted(P.WORKLOADS))
+    ap.add_argument("--count", type=int, default=0, help="override the batch size")
+    ap.add_argument("--plain", type=int, default=64, help="ciphertexts timed in the plain form")
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    w = P.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

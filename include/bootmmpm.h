@@ -1,0 +1,207 @@
+/*
+ * bootmmpm.h -- C ABI of libbootmmpm.so: BootMMPM functional bootstrapping
+ * (Liu and Li, "Large-Plaintext Functional Bootstrapping in FHE with Small
+ * Bootstrapping Keys", arXiv 2310.12441) on NVIDIA GB300 (sm_103a).
+ *
+ * The library runs the data-parallel hot path of Algorithm 1 on the GPU:
+ * test-vector construction and ACC initialisation, n CMux steps over the
+ * monic monomial permutation matrices P(c) (blind rotation), sample
+ * extraction and LWE key switching.  Key generation builds the evaluation
+ * keys on the GPU from caller-supplied randomness; encryption and decryption
+ * are client-side host routines.
+ *
+ * Conventions (Section 2 of the paper):
+ *  - Z_Q values are uint64 in [0, Q); Q is prime, Q = 1 mod 2N, Q < 2^61.
+ *  - An LWE ciphertext (a_1, ..., a_n, b) is n+1 consecutive uint64, b last;
+ *    phase = b - <a, s>.  Inputs to bootstrapping live in Z_{q'}, q' = 2Nm
+ *    (the output of Algorithm 1's first modulus switch); outputs in Z_Q.
+ *  - An RLWE vector of m rows is [m][2][N] uint64: row r, component 0 = a,
+ *    1 = b, coefficient of x^i at index i; phase_r = b_r - a_r z.
+ *  - A look-up table is t uint32 entries f(0..t-1) in [0, t), negacyclic:
+ *    f(k + t/2) = (t - f(k)) mod t  (Section 2, item (7)).
+ *  - Secrets: s in {-1,0,1}^n (LWE, int8), z in {-1,0,1}^N (RLWE, int8).
+ *
+ * Ownership: key handles are created and freed by the library and own their
+ * device memory.  Every other buffer belongs to the caller.  Device buffers
+ * passed with a stream must stay valid until the stream's work completes.
+ *
+ * Errors: every call validates its arguments on the host and returns a
+ * negative bm_status before launching anything.  Faults detected on the
+ * device (a table that is not negacyclic, a bounded wait that expired) are
+ * recorded in the status word at the start of the caller's workspace and
+ * read back with bm_workspace_status(); no kernel traps.
+ */
+#ifndef BOOTMMPM_H
+#define BOOTMMPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t bm_status;
+#define BM_OK               0
+#define BM_EINVAL          (-1)   /* an argument is out of range or inconsistent */
+#define BM_ENOTPRIME       (-2)   /* Q is not prime or not 1 mod 2N */
+#define BM_ENOMEM          (-3)   /* device allocation failed (key generation) */
+#define BM_ENONNEGACYCLIC  (-4)   /* a look-up table is not negacyclic */
+#define BM_ETIMEDOUT       (-5)   /* a bounded device wait expired */
+#define BM_ECUDA           (-6)   /* a CUDA runtime call failed */
+#define BM_EBUSY           (-7)   /* admission refused (serving loop) */
+#define BM_EWORKSPACE      (-8)   /* the workspace is too small */
+
+/* Evaluation-key parameters (Algorithm 1, REQUIRE block).  The keys do not
+ * depend on m or t (Section 5, items (1)-(2)); one key set serves every job
+ * shape (m, t) with the same N. */
+typedef struct bm_key_params {
+    uint32_t n;         /* LWE dimension */
+    uint32_t N;         /* ring degree, power of two, 256..4096 */
+    uint32_t log2_B;    /* blind-rotation gadget base B = 2^log2_B */
+    uint32_t l_B;       /* gadget digits, B^l_B >= Q, 2 <= l_B <= 8 */
+    uint32_t log2_Bks;  /* key-switching base B_ks = 2^log2_Bks, <= 8 */
+    uint32_t l_ks;      /* key-switching digits of the approximate gadget, <= 16,
+                           B_ks^l_ks < Q */
+    uint64_t Q;         /* prime ring modulus */
+} bm_key_params;
+
+/* Randomness of key generation, all host arrays (C order):
+ *   s        int8   [n]                     LWE secret, entries in {-1,0,1}
+ *   z        int8   [N]                     RLWE secret, entries in {-1,0,1}
+ *   bsk_mask uint64 [n][2][2 l_B][N]        uniform in [0, Q)
+ *   bsk_err  int8   [n][2][2 l_B][N]        errors of the RGSW rows
+ *   ksk_mask uint64 [N][l_ks][B_ks-1][n]    uniform in [0, Q)
+ *   ksk_err  int8   [N][l_ks][B_ks-1]       errors of the LWE rows      */
+typedef struct bm_key_randomness {
+    const int8_t *s;
+    const int8_t *z;
+    const uint64_t *bsk_mask;
+    const int8_t *bsk_err;
+    const uint64_t *ksk_mask;
+    const int8_t *ksk_err;
+} bm_key_randomness;
+
+typedef struct bm_secret_key bm_secret_key;
+typedef struct bm_eval_key bm_eval_key;
+
+/* One bootstrapping job (Definition 1): ciphertext, table, shape, key set. */
+typedef struct bm_job {
+    uint32_t key;       /* index into the key array of the call */
+    uint32_t m;         /* polynomials in the test vector, 1..64 */
+    uint32_t t;         /* plaintext modulus, even, 2 <= t <= 2Nm */
+    uint32_t reserved;  /* must be 0 */
+    uint64_t in_off;    /* element offset of the input LWE_{n,2Nm} (n+1 words) */
+    uint64_t lut_off;   /* element offset of the table (t entries) */
+    uint64_t out_off;   /* element offset of the output (n+1 words, or the
+                           [m][2][N] ACC for bm_blind_rotate) */
+} bm_job;
+
+/* Key generation (Section 2 items (11) and (14); Algorithm 1 REQUIRE).
+ * Builds on device `device`:
+ *   BSK: for k in [n] and s_k+ = max(s_k,0), s_k- = max(-s_k,0), the RGSW
+ *        encryptions under z: row j < l_B = (a + mu B^j, a z + e), row l_B+j =
+ *        (a, a z + e + mu B^j); stored in the NTT domain scaled by N^-1;
+ *   KSK: for i in [N], j in [l_ks], v in [1, B_ks), the LWE encryption under s
+ *        of v z_i g_j, g_j = floor((Q B_ks^j + P/2) / P), P = B_ks^l_ks.
+ * Copies the randomness, so the caller may free it on return.
+ * Returns BM_EINVAL / BM_ENOTPRIME on bad parameters, BM_ENOMEM, BM_ECUDA. */
+bm_status bm_keygen(const bm_key_params *params, const bm_key_randomness *rnd,
+                    int device, bm_secret_key **sk_out, bm_eval_key **ek_out);
+void bm_free_secret_key(bm_secret_key *sk);
+void bm_free_eval_key(bm_eval_key *ek);
+
+/* Device bytes held by an evaluation key (BSK + KSK + tables). */
+size_t bm_eval_key_bytes(const bm_eval_key *ek);
+
+/* LWE_{n,q} encryption on the host (Section 2, item (8)):
+ * ct_i = (a_i, <a_i, s> + msg_i floor(q/t) + e_i) mod q, for `count` messages.
+ * mask: uint64 [count][n] in [0, q); err: int8 [count]; ct_out: [count][n+1]. */
+bm_status bm_encrypt(const bm_secret_key *sk, uint64_t q, uint32_t t,
+                     const uint32_t *msg, const uint64_t *mask, const int8_t *err,
+                     size_t count, uint64_t *ct_out);
+
+/* LWE decryption on the host: msg = floor((phase t + floor(q/2)) / q) mod t.
+ * ct: [count][n+1] in [0, q). */
+bm_status bm_decrypt(const bm_secret_key *sk, uint64_t q, uint32_t t,
+                     const uint64_t *ct, size_t count, uint32_t *msg_out);
+
+/* Bytes of device workspace that bm_bootstrap_batch / bm_blind_rotate need
+ * for these jobs (status word, job table, per-job accumulators). */
+size_t bm_workspace_bytes(const bm_eval_key *const *keys, uint32_t n_keys,
+                          const bm_job *jobs, uint32_t count);
+
+/* Algorithm 1 for `count` jobs in one launch sequence on `stream`
+ * (a cudaStream_t, or NULL for the default stream):
+ *   ACC <- P(b) (0, v_test floor(Q/t))            (test vector Eq. (equ:test-use))
+ *   for k = 1..n: ACC <- CMux(ct_k+, ct_k-; P(-a_k), I, P(a_k)) ACC   (Eq. (cmux:BP))
+ *   ct  <- SampleExtract(row 0 of ACC)            (Eq. (equ-sam-extr))
+ *   ct  <- KeySwitch_{z -> s}(ct)                 (Eq. (equ-key-swi))
+ * The input modulus switch is the identity (inputs are given in Z_{2Nm});
+ * the final switch Q -> q is not applied: outputs are LWE_{n,Q} under s.
+ * d_ct_in (uint64), d_lut (uint32), d_ct_out (uint64): device arrays indexed
+ * by the jobs' offsets.  d_ws: device workspace of ws_bytes bytes, 256-byte
+ * aligned.  Asynchronous; host-side validation errors return before any
+ * launch, device-side ones land in the workspace status word. */
+bm_status bm_bootstrap_batch(const bm_eval_key *const *keys, uint32_t n_keys,
+                             const bm_job *jobs, uint32_t count,
+                             const uint64_t *d_ct_in, const uint32_t *d_lut,
+                             uint64_t *d_ct_out, void *d_ws, size_t ws_bytes,
+                             void *stream);
+
+/* Same computation with host buffers: copies the inputs (h_ct_in, h_lut) to
+ * the workspace, bootstraps, copies the outputs back to h_ct_out, and
+ * synchronises the stream.  The workspace must hold
+ * bm_workspace_bytes(...) + bm_host_staging_bytes(...). */
+size_t bm_host_staging_bytes(const bm_eval_key *const *keys, uint32_t n_keys,
+                             const bm_job *jobs, uint32_t count);
+bm_status bm_bootstrap_batch_host(const bm_eval_key *const *keys, uint32_t n_keys,
+                                  const bm_job *jobs, uint32_t count,
+                                  const uint64_t *h_ct_in, size_t ct_in_words,
+                                  const uint32_t *h_lut, size_t lut_words,
+                                  uint64_t *h_ct_out, size_t ct_out_words,
+                                  void *d_ws, size_t ws_bytes, void *stream);
+
+/* Blind rotation only (Algorithm 1, phase accumulation): writes each job's
+ * final ACC, [m][2][N] uint64, at d_acc_out + job.out_off.  `steps` limits
+ * the CMux loop to its first `steps` iterations (steps >= n runs all). */
+bm_status bm_blind_rotate(const bm_eval_key *const *keys, uint32_t n_keys,
+                          const bm_job *jobs, uint32_t count, uint32_t steps,
+                          const uint64_t *d_ct_in, const uint32_t *d_lut,
+                          uint64_t *d_acc_out, void *d_ws, size_t ws_bytes,
+                          void *stream);
+
+/* Sample extraction (Section 2 item (13), Eq. (equ-sam-extr)): for each of
+ * `count` RLWE ciphertexts (a, b) at d_rlwe + i*2N, writes the LWE_{N,Q}
+ * sample (a_0, -a_{N-1}, ..., -a_1, b_0) at d_lwe_out + i*(N+1). */
+bm_status bm_sample_extract(const bm_eval_key *key, const uint64_t *d_rlwe,
+                            uint32_t count, uint64_t *d_lwe_out, void *stream);
+
+/* LWE key switching z -> s (Section 2 item (11), Eq. (equ-key-swi)) with the
+ * approximate gadget: a~_i = floor((a_i P + floor(Q/2)) / Q) mod P split into
+ * l_ks base-B_ks digits d_ij; out = (0^n, b) - sum_ij KSK(i, j, d_ij).
+ * d_lwe_in: [count][N+1]; d_out: [count][n+1]. */
+bm_status bm_key_switch(const bm_eval_key *key, const uint64_t *d_lwe_in,
+                        uint32_t count, uint64_t *d_out, void *stream);
+
+/* Negacyclic products in R_{N,Q} (Section 2 item (6)) through the library's
+ * NTT: d_out[i] = d_a[i] * d_b[i] for `count` pairs of N coefficients. */
+bm_status bm_poly_mul(const bm_eval_key *key, const uint64_t *d_a,
+                      const uint64_t *d_b, uint32_t count, uint64_t *d_out,
+                      void *stream);
+
+/* Reads (synchronising `stream`) and clears the device status word of a
+ * workspace: BM_OK or the first device-side error recorded. */
+bm_status bm_workspace_status(void *d_ws, void *stream);
+
+/* Throughput probe of the library's Shoup modular multiplication (the
+ * integer-ALU roofline denominator): runs `iters` dependent-chain steps on
+ * every thread of a full-device grid and returns modmuls/s in *rate. */
+bm_status bm_modmul_peak(int device, uint32_t iters, double *rate);
+
+const char *bm_status_str(bm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BOOTMMPM_H */

@@ -1,0 +1,68 @@
+// Internal types shared by the translation units of libbootmmpm.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+#include "modarith.cuh"
+#include "../../include/bootmmpm.h"
+
+#define BM_MAX_L_B 8
+#define BM_MAX_M 64
+
+// Device-resident description of one evaluation key set.  One copy lives in
+// device memory (owned by the bm_eval_key) so jobs can point at it.
+struct KeyDev {
+    const u64 *bsk;    // [n][2][2 l_B][2][N], NTT domain, scaled by N^-1
+    const u64 *ksk;    // [N][l_ks][B_ks - 1][n + 1]
+    const u64 *tw;     // forward twiddles psi^bitrev(k), k in [0, N)
+    const u64 *twsh;   // their Shoup companions
+    const u64 *itw;    // inverse twiddles psi^-bitrev(k)
+    const u64 *itwsh;
+    ModQ mq;
+    u64 ninv, ninv_sh; // N^-1 mod Q and companion
+    u64 ks_pq;         // floor(P 2^64 / Q), P = B_ks^l_ks
+    u32 n, N, logN, log2_B, l_B, log2_Bks, l_ks, pad;
+};
+
+// One job as the kernels see it.
+struct DevJob {
+    const KeyDev *key;
+    u32 m, t, N, n;
+    u64 in_off, lut_off, out_off;
+    u64 acc_off;       // element offset of the job's two ACC buffers in the workspace
+};
+
+// Host-side evaluation key.
+struct bm_eval_key {
+    int device;
+    bm_key_params p;
+    u32 logN;
+    KeyDev host_view;  // same fields as the device copy (pointers are device pointers)
+    KeyDev *d_view;
+    u64 *d_bsk, *d_ksk, *d_tables;
+    size_t bytes;
+};
+
+struct bm_secret_key {
+    bm_key_params p;
+    int8_t *s;
+    int8_t *z;
+};
+
+#define BM_CUDA_TRY(call)                                                   \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) {                                            \
+            fprintf(stderr, "bootmmpm: %s failed: %s (%s:%d)\n", #call,     \
+                    cudaGetErrorString(e_), __FILE__, __LINE__);            \
+            return BM_ECUDA;                                                \
+        }                                                                   \
+    } while (0)
+
+// Workspace header: the device status word sits at offset 0.
+#define BM_WS_HEADER 256
+
+// Host helpers (keygen.cu)
+bm_status bm_check_key_params(const bm_key_params *p);
+u64 host_mulmod(u64 a, u64 b, u64 Q);

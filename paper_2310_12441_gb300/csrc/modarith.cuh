@@ -1,0 +1,71 @@
+// Modular arithmetic in Z_Q, Q < 2^61 prime, for sm_103a.
+//
+// Multiplication by a fixed operand uses Shoup's precomputed-quotient method
+// (V. Shoup, NTL; analysed in D. Harvey, "Faster arithmetic for
+// number-theoretic transforms", J. Symb. Comp. 2014): for w in [0, Q) and
+// w' = floor(w 2^64 / Q), any a in [0, 2^64) gives
+//     a w - floor(a w' / 2^64) Q  in [0, 2Q).
+// Products of two variable operands are accumulated exactly in 128 bits
+// (mad.lo.cc / madc.hi) and reduced once at the end.
+#pragma once
+#include <cstdint>
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+struct ModQ {
+    u64 Q;
+    u64 two_Q;
+    u64 r64;      // 2^64 mod Q
+    u64 r64_sh;   // floor(r64 * 2^64 / Q)
+    u64 one_sh;   // floor(2^64 / Q): Shoup companion of w = 1
+};
+
+__device__ __forceinline__ u64 reduce_2q(u64 x, u64 Q) { return x >= Q ? x - Q : x; }
+
+// a * w mod Q in [0, 2Q), Shoup.
+__device__ __forceinline__ u64 mul_shoup_lazy(u64 a, u64 w, u64 wsh, u64 Q) {
+    u64 q = __umul64hi(a, wsh);
+    return a * w - q * Q;
+}
+
+__device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 wsh, u64 Q) {
+    return reduce_2q(mul_shoup_lazy(a, w, wsh, Q), Q);
+}
+
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 Q) {
+    u64 s = a + b;
+    return s >= Q ? s - Q : s;
+}
+
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 Q) {
+    return a >= b ? a - b : a + Q - b;
+}
+
+// (hi:lo) += a * b, exact 128-bit accumulation.
+__device__ __forceinline__ void mac128(u64 &lo, u64 &hi, u64 a, u64 b) {
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+        "madc.hi.u64 %1, %2, %3, %1;"
+        : "+l"(lo), "+l"(hi)
+        : "l"(a), "l"(b));
+}
+
+// (hi:lo) += a, exact 128-bit accumulation of a 64-bit value.
+__device__ __forceinline__ void add128(u64 &lo, u64 &hi, u64 a) {
+    asm("add.cc.u64 %0, %0, %2;\n\t"
+        "addc.u64 %1, %1, 0;"
+        : "+l"(lo), "+l"(hi)
+        : "l"(a));
+}
+
+// (hi 2^64 + lo) mod Q, any hi, lo < 2^64:  hi * (2^64 mod Q) + lo, each term
+// Shoup-reduced into [0, 2Q), sum < 4Q < 2^63, then two conditional
+// subtractions.
+__device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const ModQ &m) {
+    u64 x = mul_shoup_lazy(hi, m.r64, m.r64_sh, m.Q);
+    u64 y = lo - __umul64hi(lo, m.one_sh) * m.Q;
+    u64 s = x + y;
+    if (s >= m.two_Q) s -= m.two_Q;
+    if (s >= m.Q) s -= m.Q;
+    return s;
+}

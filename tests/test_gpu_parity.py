@@ -1,0 +1,284 @@
+"""Parity of the CUDA path with the oracle, element by element, bit-exact.
+
+All arithmetic is exact modular integer arithmetic, so the tolerance is 0:
+every output word must equal the oracle's.  Every call goes through the C ABI
+(libbootmmpm.so) via the thin binding.
+"""
+import numpy as np
+import pytest
+
+from paper_2310_12441_gb300 import params as P
+from paper_2310_12441_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_12441_gb300 import api as A
+    A.load()
+    return A
+
+
+class KeySet:
+    def __init__(self, api, orc, kp, seed, oracle_keys):
+        self.kp = kp
+        self.rnd = synth.key_randomness(kp, seed)
+        self.sk, self.ek = api.bm_keygen(kp, self.rnd, 0)
+        self.bsk = orc.keygen_bsk(kp, self.rnd, 0, oracle_keys)
+        self.ksk = orc.keygen_ksk(kp, self.rnd)
+
+
+@pytest.fixture(scope="module")
+def toy(api, orc):
+    return KeySet(api, orc, P.KEYS_TOY, 1001, P.KEYS_TOY.n)
+
+
+@pytest.fixture(scope="module")
+def n1024(api, orc):
+    return KeySet(api, orc, P.KEYS_N1024, 1002, 8)
+
+
+@pytest.fixture(scope="module")
+def n2048(api, orc):
+    return KeySet(api, orc, P.KEYS_N2048, 1003, 4)
+
+
+def _encrypt(orc, ks, m, t, count, seed, prefix=None, half=None):
+    kp = ks.kp
+    qp = 2 * kp.N * m
+    msg = synth.messages(t, count, 3000 + seed, half)
+    enc = synth.encryption_randomness(kp.n, qp, kp.sigma, count, 4000 + seed, prefix=prefix)
+    ct = orc.encrypt(kp.n, qp, t, ks.rnd["s"], msg, enc["mask"], enc["err"])
+    return msg, ct
+
+
+def _run_batch(api, keys, jobs, ct_in, luts, out_words):
+    d_in = api.to_device_u64(ct_in.ravel())
+    d_lut = api.to_device_u32(luts.ravel())
+    d_out = torch.zeros(out_words, dtype=torch.int64, device="cuda")
+    ws = api.workspace(api.bm_workspace_bytes(keys, jobs))
+    api.bm_bootstrap_batch(keys, jobs, d_in, d_lut, d_out, ws)
+    torch.cuda.synchronize()
+    assert api.bm_workspace_status(ws) == 0
+    return api.from_device_u64(d_out)
+
+
+def _uniform_jobs(api, count, n, t, m):
+    return api.make_jobs(0, m, t, np.arange(count) * (n + 1), np.arange(count) * t,
+                         np.arange(count) * (n + 1))
+
+
+# --- ring product (NTT / INTT path) --------------------------------------------------
+
+@pytest.mark.parametrize("fixture", ["toy", "n1024", "n2048"])
+def test_poly_mul_matches_schoolbook(api, orc, request, fixture):
+    ks = request.getfixturevalue(fixture)
+    kp = ks.kp
+    rng = np.random.default_rng(kp.N)
+    cnt = 3
+    a = rng.integers(0, kp.Q, (cnt, kp.N), dtype=np.uint64)
+    b = rng.integers(0, kp.Q, (cnt, kp.N), dtype=np.uint64)
+    a[0] = 0; a[0, 1] = 1                      # x * b
+    b[1] = kp.Q - 1                            # all coefficients -1
+    d_out = torch.zeros(cnt * kp.N, dtype=torch.int64, device="cuda")
+    api.bm_poly_mul(ks.ek, api.to_device_u64(a), api.to_device_u64(b), cnt, d_out)
+    got = api.from_device_u64(d_out).reshape(cnt, kp.N)
+    for i in range(cnt):
+        assert np.array_equal(got[i], orc.poly_mul(kp.N, kp.Q, a[i], b[i])), i
+
+
+# --- sample extraction and key switching -----------------------------------------------
+
+@pytest.mark.parametrize("fixture", ["toy", "n1024"])
+def test_sample_extract(api, orc, request, fixture):
+    ks = request.getfixturevalue(fixture)
+    kp = ks.kp
+    rng = np.random.default_rng(3)
+    cnt = 5
+    rl = rng.integers(0, kp.Q, (cnt, 2, kp.N), dtype=np.uint64)
+    rl[0, 0] = 0                                # zero a-part (no negation wrap)
+    d_out = torch.zeros(cnt * (kp.N + 1), dtype=torch.int64, device="cuda")
+    api.bm_sample_extract(ks.ek, api.to_device_u64(rl), cnt, d_out)
+    got = api.from_device_u64(d_out).reshape(cnt, kp.N + 1)
+    for i in range(cnt):
+        assert np.array_equal(got[i], orc.sample_extract(kp.N, kp.Q, rl[i, 0], rl[i, 1]))
+
+
+@pytest.mark.parametrize("fixture", ["toy", "n1024", "n2048"])
+def test_key_switch(api, orc, request, fixture):
+    ks = request.getfixturevalue(fixture)
+    kp = ks.kp
+    rng = np.random.default_rng(5)
+    cnt = 4
+    lwe = rng.integers(0, kp.Q, (cnt, kp.N + 1), dtype=np.uint64)
+    lwe[1, :kp.N] = 0                           # all digits zero: output (0, b)
+    lwe[2, :kp.N] = kp.Q - 1                    # rounding to P wraps to 0
+    d_out = torch.zeros(cnt * (kp.n + 1), dtype=torch.int64, device="cuda")
+    api.bm_key_switch(ks.ek, api.to_device_u64(lwe), cnt, d_out)
+    got = api.from_device_u64(d_out).reshape(cnt, kp.n + 1)
+    for i in range(cnt):
+        assert np.array_equal(got[i], orc.key_switch(kp, lwe[i], ks.ksk)), i
+
+
+# --- blind rotation ----------------------------------------------------------------------
+
+def _blind_rotate_gpu(api, ks, jobs, ct, luts, steps):
+    kp = ks.kp
+    out_words = int(sum(2 * int(j["m"]) * kp.N for j in jobs))
+    jobs = jobs.copy()
+    offs = np.concatenate([[0], np.cumsum([2 * int(j["m"]) * kp.N for j in jobs])[:-1]])
+    jobs["out_off"] = offs
+    d_out = torch.zeros(out_words, dtype=torch.int64, device="cuda")
+    ws = api.workspace(api.bm_workspace_bytes([ks.ek], jobs))
+    api.bm_blind_rotate([ks.ek], jobs, steps, api.to_device_u64(ct.ravel()),
+                        api.to_device_u32(luts.ravel()), d_out, ws)
+    torch.cuda.synchronize()
+    assert api.bm_workspace_status(ws) == 0
+    full = api.from_device_u64(d_out)
+    return [full[o:o + 2 * int(j["m"]) * kp.N].reshape(int(j["m"]), 2, kp.N) for o, j in zip(offs, jobs)]
+
+
+def test_blind_rotate_toy_full(api, orc, toy):
+    kp, m, t = toy.kp, 2, 32
+    msg, ct = _encrypt(orc, toy, m, t, 3, 1)
+    luts, _ = synth.luts(t, 3, 2001)
+    jobs = _uniform_jobs(api, 3, kp.n, t, m)
+    got = _blind_rotate_gpu(api, toy, jobs, ct, luts, 1 << 30)
+    for i in range(3):
+        assert np.array_equal(got[i], orc.blind_rotate(kp, m, t, toy.bsk, ct[i], luts[i]))
+
+
+@pytest.mark.parametrize("steps", [0, 1, 5])
+def test_blind_rotate_steps_equal_truncated_ciphertext(api, orc, n1024, steps):
+    """ACC after the first K CMux steps equals the oracle's full rotation of
+    the same ciphertext with a_k = 0 beyond K (P(0) = I)."""
+    kp, m, t = n1024.kp, 4, 1024
+    msg, ct = _encrypt(orc, n1024, m, t, 2, 2)
+    luts, _ = synth.luts(t, 2, 2002)
+    jobs = _uniform_jobs(api, 2, kp.n, t, m)
+    got = _blind_rotate_gpu(api, n1024, jobs, ct, luts, steps)
+    for i in range(2):
+        tr = ct[i].copy()
+        tr[steps:kp.n] = 0
+        assert np.array_equal(got[i], orc.blind_rotate(kp, m, t, n1024.bsk, tr, luts[i]))
+
+
+def test_blind_rotate_prefix_ciphertexts_n2048(api, orc, n2048):
+    kp, m, t = n2048.kp, 8, 8192
+    msg, ct = _encrypt(orc, n2048, m, t, 2, 3, prefix=4)
+    luts, _ = synth.luts(t, 2, 2003, mix="mixed")
+    jobs = _uniform_jobs(api, 2, kp.n, t, m)
+    got = _blind_rotate_gpu(api, n2048, jobs, ct, luts, 1 << 30)
+    for i in range(2):
+        assert np.array_equal(got[i], orc.blind_rotate(kp, m, t, n2048.bsk, ct[i], luts[i]))
+
+
+def test_blind_rotate_uneven_shapes_one_call(api, orc, n1024):
+    """Jobs with different (m, t) in one call (the uneven-batch sets on the
+    N = 1024 key), prefix ciphertexts so the oracle stays fast."""
+    kp = n1024.kp
+    shapes = [(1, 256), (2, 512), (4, 1024), (2, 512), (1, 256)]
+    cts, luts_l, jobs = [], [], []
+    in_off = lut_off = 0
+    for i, (m, t) in enumerate(shapes):
+        _, ct = _encrypt(orc, n1024, m, t, 1, 10 + i, prefix=6)
+        lut, _ = synth.luts(t, 1, 2010 + i)
+        cts.append(ct[0]); luts_l.append(lut[0])
+        jobs.append((0, m, t, 0, in_off, lut_off, 0))
+        in_off += kp.n + 1; lut_off += t
+    jobs = np.array(jobs, dtype=api.JOB_DTYPE)
+    got = _blind_rotate_gpu(api, n1024, jobs, np.concatenate(cts), np.concatenate(luts_l), 1 << 30)
+    for i, (m, t) in enumerate(shapes):
+        assert np.array_equal(got[i], orc.blind_rotate(kp, m, t, n1024.bsk, cts[i], luts_l[i])), i
+
+
+# --- full bootstrap ------------------------------------------------------------------------
+
+def test_bootstrap_toy_all_messages(api, orc, toy):
+    """Toy workload: all 32 messages, bit-exact with the oracle, and every
+    output decrypts to f(Dec(input))."""
+    kp, m, t = toy.kp, 2, 32
+    msg = np.arange(t, dtype=np.uint32)
+    qp = 2 * kp.N * m
+    enc = synth.encryption_randomness(kp.n, qp, kp.sigma, t, 4001)
+    ct = orc.encrypt(kp.n, qp, t, toy.rnd["s"], msg, enc["mask"], enc["err"])
+    luts, _ = synth.luts(t, t, 2001)
+    jobs = _uniform_jobs(api, t, kp.n, t, m)
+    got = _run_batch(api, [toy.ek], jobs, ct, luts, t * (kp.n + 1)).reshape(t, kp.n + 1)
+    want = orc.bootstrap(kp, m, t, toy.bsk, toy.ksk, ct, luts)
+    assert np.array_equal(got, want)
+    dec_in = orc.decrypt(kp.n, qp, t, toy.rnd["s"], ct)
+    dec_out = api.bm_decrypt(toy.sk, kp.Q, t, got)
+    assert np.array_equal(dec_out, luts[np.arange(t), dec_in])
+
+
+def test_bootstrap_prefix_n1024_bit_exact(api, orc, n1024):
+    kp, m, t = n1024.kp, 4, 1024
+    cnt = 3
+    msg, ct = _encrypt(orc, n1024, m, t, cnt, 21, prefix=8)
+    luts, _ = synth.luts(t, cnt, 2021)
+    jobs = _uniform_jobs(api, cnt, kp.n, t, m)
+    got = _run_batch(api, [n1024.ek], jobs, ct, luts, cnt * (kp.n + 1)).reshape(cnt, kp.n + 1)
+    want = orc.bootstrap(kp, m, t, n1024.bsk, n1024.ksk, ct, luts)
+    assert np.array_equal(got, want)
+
+
+def test_nonnegacyclic_table_sets_status(api, orc, toy):
+    kp, m, t = toy.kp, 2, 32
+    _, ct = _encrypt(orc, toy, m, t, 2, 30)
+    luts, _ = synth.luts(t, 2, 2030)
+    luts[1, t // 2] = (luts[1, t // 2] + 1) % t
+    jobs = _uniform_jobs(api, 2, kp.n, t, m)
+    d_out = torch.zeros(2 * (kp.n + 1), dtype=torch.int64, device="cuda")
+    ws = api.workspace(api.bm_workspace_bytes([toy.ek], jobs))
+    api.bm_bootstrap_batch([toy.ek], jobs, api.to_device_u64(ct.ravel()),
+                           api.to_device_u32(luts.ravel()), d_out, ws)
+    assert api.bm_workspace_status(ws) == -4
+    assert api.bm_workspace_status(ws) == 0          # reading clears it
+
+
+def test_invalid_jobs_rejected_before_launch(api, toy):
+    kp = toy.kp
+    ws = api.workspace(1 << 20)
+    d = torch.zeros(64, dtype=torch.int64, device="cuda")
+    for bad in [dict(m=0), dict(t=3), dict(t=2 * kp.N * 2 + 2), dict(key=1)]:
+        j = api.make_jobs(bad.get("key", 0), bad.get("m", 2), bad.get("t", 32), 0, 0, 0)
+        with pytest.raises(api.BMError) as e:
+            api.bm_bootstrap_batch([toy.ek], j, d, d, d, ws)
+        assert e.value.code == -1
+    j = _uniform_jobs(api, 4, kp.n, 32, 2)
+    small = api.workspace(16)
+    with pytest.raises(api.BMError) as e:
+        api.bm_bootstrap_batch([toy.ek], j, d, d, d, small[:16])
+    assert e.value.code == -8
+
+
+def test_host_buffer_entry_point_matches_device(api, orc, toy):
+    kp, m, t = toy.kp, 2, 32
+    cnt = 4
+    _, ct = _encrypt(orc, toy, m, t, cnt, 40)
+    luts, _ = synth.luts(t, cnt, 2040)
+    jobs = _uniform_jobs(api, cnt, kp.n, t, m)
+    dev = _run_batch(api, [toy.ek], jobs, ct, luts, cnt * (kp.n + 1))
+    host_out = np.zeros(cnt * (kp.n + 1), np.uint64)
+    need = api.bm_workspace_bytes([toy.ek], jobs) + api.bm_host_staging_bytes([toy.ek], jobs)
+    ws = api.workspace(need + 4096)
+    api.bm_bootstrap_batch_host([toy.ek], jobs, np.ascontiguousarray(ct.ravel()),
+                                np.ascontiguousarray(luts.ravel()), host_out, ws)
+    assert np.array_equal(host_out, dev)
+
+
+def test_deterministic_repeat(api, orc, n1024):
+    kp, m, t = n1024.kp, 4, 1024
+    cnt = 8
+    _, ct = _encrypt(orc, n1024, m, t, cnt, 50, prefix=8)
+    luts, _ = synth.luts(t, cnt, 2050)
+    jobs = _uniform_jobs(api, cnt, kp.n, t, m)
+    a = _run_batch(api, [n1024.ek], jobs, ct, luts, cnt * (kp.n + 1))
+    b = _run_batch(api, [n1024.ek], jobs, ct, luts, cnt * (kp.n + 1))
+    assert np.array_equal(a, b)
