@@ -199,6 +199,33 @@ bm_status bm_workspace_status(void *d_ws, void *stream);
  * every thread of a full-device grid and returns modmuls/s in *rate. */
 bm_status bm_modmul_peak(int device, uint32_t iters, double *rate);
 
+/* Bootstrapping for callers that cannot allocate device memory (no
+ * counterpart in the paper; a property of this library's interface).
+ * Such callers include code running inside a host application whose memory
+ * pool already owns the GPU's memory, serving loops in which a cudaMalloc or
+ * cudaFree would stall every stream on the device, and components whose
+ * device footprint must stay fixed after start-up.
+ *
+ * Same computation and arguments as bm_bootstrap_batch, but the job table,
+ * status word and accumulators live in a fixed array of
+ * BM_NOALLOC_SCRATCH_BYTES bytes inside the library (every GPU that loads
+ * the library holds it until the process exits).  The call performs no
+ * device allocation of any kind.  A batch needing more than the array
+ * (bm_workspace_bytes(...) > BM_NOALLOC_SCRATCH_BYTES) is rejected with
+ * BM_EWORKSPACE before anything is launched.
+ *  - The first call on a device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call shares the one array: calls whose work overlaps on the GPU
+ *    (concurrent streams, or threads) race and corrupt each other.  Order
+ *    them on one stream or synchronise between them.
+ *  - d_status (device int32, may be NULL) receives BM_OK or the first
+ *    device-side error of this call, written after the batch on `stream`. */
+#define BM_NOALLOC_SCRATCH_BYTES (16u << 20)
+bm_status bm_bootstrap_batch_noalloc(const bm_eval_key *const *keys, uint32_t n_keys,
+                                     const bm_job *jobs, uint32_t count,
+                                     const uint64_t *d_ct_in, const uint32_t *d_lut,
+                                     uint64_t *d_ct_out, int32_t *d_status, void *stream);
+
 const char *bm_status_str(bm_status s);
 
 #ifdef __cplusplus

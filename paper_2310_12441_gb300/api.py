@@ -26,7 +26,9 @@ SYMBOLS = ["bm_keygen", "bm_free_secret_key", "bm_free_eval_key", "bm_eval_key_b
            "bm_encrypt", "bm_decrypt", "bm_workspace_bytes", "bm_bootstrap_batch",
            "bm_host_staging_bytes", "bm_bootstrap_batch_host", "bm_blind_rotate",
            "bm_sample_extract", "bm_key_switch", "bm_poly_mul", "bm_workspace_status",
-           "bm_modmul_peak", "bm_status_str"]
+           "bm_modmul_peak", "bm_status_str", "bm_bootstrap_batch_noalloc"]
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class BMError(RuntimeError):
@@ -99,6 +101,8 @@ def load(build_if_needed: bool = True) -> C.CDLL:
     L.bm_workspace_status.restype = i32
     L.bm_modmul_peak.argtypes = [C.c_int, u32, C.POINTER(C.c_double)]
     L.bm_modmul_peak.restype = i32
+    L.bm_bootstrap_batch_noalloc.argtypes = [vp, u32, vp, u32, vp, vp, vp, vp, vp]
+    L.bm_bootstrap_batch_noalloc.restype = i32
     L.bm_status_str.argtypes = [i32]
     L.bm_status_str.restype = C.c_char_p
     _lib = L
@@ -221,6 +225,19 @@ def bm_bootstrap_batch(keys, jobs: np.ndarray, d_ct_in, d_lut, d_ct_out, d_ws, s
     _check(load().bm_bootstrap_batch(karr, nk, _ptr(jobs), len(jobs), _ptr(d_ct_in), _ptr(d_lut),
                                      _ptr(d_ct_out), _ptr(d_ws), d_ws.numel() * d_ws.element_size(),
                                      _stream(stream)), "bm_bootstrap_batch")
+
+
+def bm_bootstrap_batch_noalloc(keys, jobs: np.ndarray, d_ct_in, d_lut, d_ct_out, d_status=None,
+                               stream=None):
+    """bm_bootstrap_batch for callers that cannot allocate device memory: the
+    scratch is a fixed array inside the library (NOALLOC_SCRATCH_BYTES), so no
+    workspace is passed.  Calls that overlap on the GPU race on that array."""
+    karr, nk = _keys(keys)
+    jobs = np.ascontiguousarray(jobs, JOB_DTYPE)
+    _check(load().bm_bootstrap_batch_noalloc(karr, nk, _ptr(jobs), len(jobs), _ptr(d_ct_in),
+                                             _ptr(d_lut), _ptr(d_ct_out),
+                                             None if d_status is None else _ptr(d_status),
+                                             _stream(stream)), "bm_bootstrap_batch_noalloc")
 
 
 def bm_bootstrap_batch_host(keys, jobs: np.ndarray, h_ct_in, h_lut, h_ct_out, d_ws, stream=None):

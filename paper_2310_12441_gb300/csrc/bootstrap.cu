@@ -15,6 +15,7 @@
 //   4. reduces, inverse-transforms (N^-1 is folded into the key) and adds
 //      the result to row r of ACC.
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -621,5 +622,75 @@ extern "C" bm_status bm_modmul_peak(int device, uint32_t iters, double *rate) {
     cudaFree(d_out);
     if (err != cudaSuccess) return BM_ECUDA;
     *rate = (double)blocks * threads * 8.0 * iters / (ms * 1e-3);
+    return BM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Bootstrapping without any device allocation.
+//
+// Some callers cannot allocate device memory when they want to bootstrap:
+// code embedded in a host application whose memory pool already holds the
+// GPU's memory, serving loops where a cudaMalloc or cudaFree would stall
+// the whole device, and components that must keep their device footprint
+// fixed after start-up.  For them, the job table, status word and
+// accumulators of a batch live in one fixed array compiled into this
+// library instead of a caller-supplied workspace.
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[BM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices];   // device address of the array, per device
+
+__global__ void k_noalloc_status(const u32 *word, int32_t *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = -(int32_t)(*word);
+}
+}  // namespace
+
+extern "C" bm_status bm_bootstrap_batch_noalloc(const bm_eval_key *const *keys, uint32_t n_keys,
+                                                const bm_job *jobs, uint32_t count,
+                                                const uint64_t *d_ct_in, const uint32_t *d_lut,
+                                                uint64_t *d_ct_out, int32_t *d_status, void *stream) {
+    int dev = 0;
+    bm_status s = validate_jobs(keys, n_keys, jobs, count, &dev);
+    if (s != BM_OK) return s;
+    if (dev < 0 || dev >= kMaxDevices) return BM_EINVAL;
+    Plan pl;
+    make_plan(keys, jobs, count, pl);
+    if (pl.total > BM_NOALLOC_SCRATCH_BYTES) {
+        fprintf(stderr, "bootmmpm: batch needs %zu bytes of scratch, more than the %u built in\n",
+                pl.total, (unsigned)BM_NOALLOC_SCRATCH_BYTES);
+        return BM_EWORKSPACE;
+    }
+    DeviceGuard g(dev);
+    void *scratch = nullptr;
+    {
+        // Host code sees only a stand-in for the array; its device address is
+        // looked up once per device, with that device current.
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                fprintf(stderr, "bootmmpm: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+                return BM_ECUDA;
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // The array keeps the previous call's contents: the status word must
+    // start at zero (job table and accumulators are fully rewritten).
+    BM_CUDA_TRY(cudaMemsetAsync(scratch, 0, BM_WS_HEADER, st));
+    s = bootstrap_impl(keys, n_keys, jobs, count, 0xffffffffu, true, d_ct_in, d_lut, d_ct_out, scratch,
+                       BM_NOALLOC_SCRATCH_BYTES, stream);
+    if (s != BM_OK) return s;
+    if (d_status) {
+        k_noalloc_status<<<1, 32, 0, st>>>((const u32 *)scratch, d_status);
+        BM_CUDA_TRY(cudaGetLastError());
+    }
     return BM_OK;
 }
