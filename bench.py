@@ -269,7 +269,7 @@ def run_gpu(args, w):
                               "kernel": "k_blind_rotate", "kernel_ms": rot_s * 1e3,
                               "modmuls_per_launch": mm}
         # plain form: one ciphertext per launch
-        if args.plain:
+        if args.plain > 0:
             P_ = min(args.plain, count)
             j1 = [jobs[i:i + 1] for i in range(P_)]
             for i in range(2):

@@ -20,13 +20,14 @@
 
 #include "common.cuh"
 #include "ntt.cuh"
+#include "ntt_reg.cuh"
 
 // ---------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------
 
 // Coefficient `c` of x^e * p in R_{N,Q}, e in [0, 2N).
-__device__ __forceinline__ u64 rotated_coeff(const u64 *__restrict__ p, u32 c, u32 e, u32 N, u64 Q) {
+__device__ __forceinline__ u64 rotated_coeff(const u64 *p, u32 c, u32 e, u32 N, u64 Q) {
     u32 j = c + 2 * N - e;
     if (j >= 2 * N) j -= 2 * N;
     if (j < N) return p[j];
@@ -85,95 +86,161 @@ __device__ void acc_init(u64 *__restrict__ acc, const u32 *__restrict__ lut, u64
 }
 
 // ---------------------------------------------------------------------------
-// Blind rotation kernel: one job per block, NPT coefficients per thread.
+// Blind rotation kernel: one job per block of 512 threads.
+//
+// A CMux step handles the m rows one after another.  For row r the 4 l_B
+// digit polynomials ("combos": sign x component x digit) are transformed P at
+// a time (P = 512 / (N/16) polynomials per batch, each by N/16 threads holding
+// 16 coefficients in registers).  The transforms land in shared memory; every
+// thread then multiplies the positions it owns (q = tid + 512 j) with the key
+// rows of the batch's combos and accumulates exactly in 128-bit registers, so
+// the whole row needs a single reduction per position and column.  The
+// reduced row sums go to the job's sum buffer; after the last row, the 2m
+// sums are inverse-transformed (P per batch) and added to the rows of the
+// next ACC buffer.
 // ---------------------------------------------------------------------------
-template <int NPT>
-__global__ void __launch_bounds__(512) k_blind_rotate(const DevJob *__restrict__ jobs, u32 steps_limit,
-                                                      const u64 *__restrict__ ct_in,
-                                                      const u32 *__restrict__ luts,
-                                                      u64 *__restrict__ ws, u32 *status) {
+namespace brk {
+constexpr int kThreads = 512;
+template <int LOGN>
+struct Cfg {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int T = N / 16;                               // threads per polynomial
+    static constexpr int P = kThreads / T;                         // polynomials per batch
+    static constexpr int PPT = N >= kThreads ? N / kThreads : 1;   // positions per thread
+    static constexpr size_t SMEM = 2ull * P * N * 8;               // two regions per polynomial
+};
+}  // namespace brk
+
+template <int LOGN>
+__global__ void __launch_bounds__(brk::kThreads, 1)
+    k_blind_rotate(const DevJob *__restrict__ jobs, u32 steps_limit, const u64 *__restrict__ ct_in,
+                   const u32 *__restrict__ luts, u64 *ws, u32 *status) {
+    using C = brk::Cfg<LOGN>;
+    constexpr int N = C::N;
     extern __shared__ u64 sm[];
     const DevJob J = jobs[blockIdx.x];
     const KeyDev *K = J.key;
-    const u32 N = K->N, logN = K->logN, m = J.m, t = J.t, lB = K->l_B, log2B = K->log2_B, n = K->n;
+    const u32 m = J.m, t = J.t, lB = K->l_B, log2B = K->log2_B, n = K->n;
     const ModQ mq = K->mq;
     const u64 Q = mq.Q;
     const u64 qp = 2ull * N * m;
     const u64 Bmask = (1ull << log2B) - 1;
-    const u64 *tw = K->tw, *twsh = K->twsh, *itw = K->itw, *itwsh = K->itwsh;
-    const u32 tid = threadIdx.x, nth = blockDim.x;
+    const u64 *twp = K->twp, *itwp = K->itwp;
+    const u32 tid = threadIdx.x;
+    const size_t vec = (size_t)m * 2 * N;
     u64 *acc0 = ws + J.acc_off;
-    u64 *acc1 = acc0 + (size_t)m * 2 * N;
+    u64 *acc1 = acc0 + vec;
+    u64 *sums = acc1 + vec;
     const u64 *ct = ct_in + J.in_off;
     const u32 *lut = luts + J.lut_off;
 
     if (!lut_is_negacyclic(lut, t)) {
         if (tid == 0) set_status(status, BM_ENONNEGACYCLIC);
-        for (u32 idx = tid; idx < 2 * m * 2 * N; idx += nth) acc0[idx] = 0;
+        for (u32 idx = tid; idx < 2 * vec; idx += blockDim.x) acc0[idx] = 0;
         return;
     }
     acc_init(acc0, lut, ct[n] % qp, m, t, N, Q);
     __syncthreads();
 
-    u64 *cur = acc0, *nxt = acc1;
-    u64 *dig = sm;   // l_B polynomials of N words
-    const u32 steps = steps_limit < n ? steps_limit : n;
+    const u32 p = tid / C::T;          // polynomial slot within a batch
+    const u32 l = tid % C::T;          // thread within the polynomial
+    ntr::Swap sw{sm + (size_t)p * N, sm + (size_t)(C::P + p) * N, 0};
+    const u32 ncomb = 4 * lB;
     const size_t rgsw = (size_t)2 * lB * 2 * N;
+
+    u64 *cur = acc0, *nxt = acc1;
+    const u32 steps = steps_limit < n ? steps_limit : n;
     for (u32 k = 0; k < steps; k++) {
         const u64 ak = ct[k] % qp;
         const u64 *bsk_k = K->bsk + (size_t)k * 2 * rgsw;
         for (u32 r = 0; r < m; r++) {
-            u64 alo[2][NPT], ahi[2][NPT];
+            u64 lo[2][C::PPT], hi[2][C::PPT];
 #pragma unroll
-            for (int q = 0; q < NPT; q++) alo[0][q] = ahi[0][q] = alo[1][q] = ahi[1][q] = 0;
-            for (u32 sgn = 0; sgn < 2; sgn++) {
-                const u64 c = sgn == 0 ? (qp - ak) % qp : ak;
-                const u32 ea = (u32)(c / m), bb = (u32)(c % m);
-                const u32 src = r >= bb ? r - bb : r + m - bb;
-                u32 e = r >= bb ? ea : ea + 1;
-                if (e >= 2 * N) e -= 2 * N;
-                for (u32 comp = 0; comp < 2; comp++) {
+            for (int j = 0; j < C::PPT; j++) lo[0][j] = hi[0][j] = lo[1][j] = hi[1][j] = 0;
+            for (u32 c0 = 0; c0 < ncomb; c0 += C::P) {
+                // --- this thread's digit polynomial, transformed into shared memory
+                const u32 c = c0 + p;
+                const bool active = c < ncomb;
+                u64 x[16];
+                if (active) {
+                    const u32 sgn = c / (2 * lB), comp = (c / lB) & 1, d = c % lB;
+                    const u64 cv = sgn == 0 ? (qp - ak) % qp : ak;
+                    const u32 ea = (u32)(cv / m), bb = (u32)(cv % m);
+                    const u32 src = r >= bb ? r - bb : r + m - bb;
+                    u32 e = r >= bb ? ea : ea + 1;
+                    if (e >= 2 * N) e -= 2 * N;
                     const u64 *srow = cur + ((size_t)src * 2 + comp) * N;
                     const u64 *orow = cur + ((size_t)r * 2 + comp) * N;
+                    const u32 sh = d * log2B;
 #pragma unroll
-                    for (int q = 0; q < NPT; q++) {
-                        const u32 ci = tid + q * nth;
-                        const u64 D = sub_mod(rotated_coeff(srow, ci, e, N, Q), orow[ci], Q);
-                        for (u32 d = 0; d < lB; d++) dig[d * N + ci] = (D >> (d * log2B)) & Bmask;
+                    for (int i = 0; i < 16; i++) {
+                        const u32 idx = l + C::T * i;
+                        const u64 D = sub_mod(rotated_coeff(srow, idx, e, N, Q), orow[idx], Q);
+                        x[i] = (D >> sh) & Bmask;
                     }
-                    __syncthreads();
-                    cta_ntt_fwd(dig, lB, logN, tw, twsh, Q);
-                    const u64 *brow = bsk_k + (size_t)sgn * rgsw + (size_t)comp * lB * 2 * N;
-                    for (u32 d = 0; d < lB; d++) {
+                }
+                u64 *out = ntr::fwd_to_smem<LOGN>(x, sw, l, active, twp, Q);
+                // regions of the other polynomials of the batch sit at stride N
+                const u64 *slots = out - (size_t)p * N;
+                __syncthreads();
+                // --- multiply-accumulate against the key rows of the batch's combos
 #pragma unroll
-                        for (int q = 0; q < NPT; q++) {
-                            const u32 ci = tid + q * nth;
-                            const u64 x = dig[d * N + ci];
-                            mac128(alo[0][q], ahi[0][q], x, __ldg(brow + (size_t)(2 * d) * N + ci));
-                            mac128(alo[1][q], ahi[1][q], x, __ldg(brow + (size_t)(2 * d + 1) * N + ci));
+                for (int j = 0; j < C::PPT; j++) {
+                    const u32 q = tid + brk::kThreads * j;
+                    if (q < (u32)N) {
+                        const u32 sq = ntr::swz(q);
+#pragma unroll
+                        for (int cc = 0; cc < C::P; cc++) {
+                            const u32 c2 = c0 + cc;
+                            if (c2 < ncomb) {
+                                // combo c = (sign, component, digit) is key row c of the step
+                                const u64 *brow = bsk_k + (size_t)c2 * 2 * N;
+                                const u64 b0 = __ldg(brow + q), b1 = __ldg(brow + N + q);
+                                const u64 xv = slots[(size_t)cc * N + sq];
+                                mac128(lo[0][j], hi[0][j], xv, b0);
+                                mac128(lo[1][j], hi[1][j], xv, b1);
+                            }
                         }
                     }
-                    __syncthreads();
                 }
             }
+            // --- reduced row sums (NTT domain) to the sum buffer
 #pragma unroll
-            for (int q = 0; q < NPT; q++) {
-                const u32 ci = tid + q * nth;
-                dig[ci] = reduce128(alo[0][q], ahi[0][q], mq);
-                dig[N + ci] = reduce128(alo[1][q], ahi[1][q], mq);
-            }
-            __syncthreads();
-            cta_ntt_inv(dig, 2, logN, itw, itwsh, Q);
-#pragma unroll
-            for (int q = 0; q < NPT; q++) {
-                const u32 ci = tid + q * nth;
-                for (u32 comp = 0; comp < 2; comp++) {
-                    const size_t o = ((size_t)r * 2 + comp) * N + ci;
-                    nxt[o] = add_mod(cur[o], dig[comp * N + ci], Q);
+            for (int j = 0; j < C::PPT; j++) {
+                const u32 q = tid + brk::kThreads * j;
+                if (q < (u32)N) {
+                    sums[((size_t)r * 2) * N + q] = reduce128(lo[0][j], hi[0][j], mq);
+                    sums[((size_t)r * 2 + 1) * N + q] = reduce128(lo[1][j], hi[1][j], mq);
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
+        // --- inverse transforms of the 2m row sums, ACC update
+        for (u32 u0 = 0; u0 < 2 * m; u0 += C::P) {
+            const u32 u = u0 + p;
+            const bool active = u < 2 * m;
+            u64 x[16];
+            u64 *in = sw.take();
+            if (active) {
+                const u64 *sp = sums + (size_t)u * N;
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    const u32 idx = l + C::T * i;
+                    in[ntr::swz(idx)] = sp[idx];
+                }
+            }
+            __syncthreads();
+            ntr::inv_from_smem<LOGN>(x, in, sw, l, active, itwp, Q);
+            if (active) {
+                const size_t base = (size_t)u * N;
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    const size_t o = base + l + C::T * i;
+                    nxt[o] = add_mod(cur[o], x[i], Q);
+                }
+            }
+        }
+        __syncthreads();
         u64 *tmp = cur;
         cur = nxt;
         nxt = tmp;
@@ -373,22 +440,20 @@ bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t
         d.lut_off = jobs[i].lut_off;
         d.out_off = jobs[i].out_off;
         d.acc_off = acc_words;
-        acc_words += 2ull * 2 * jobs[i].m * k->p.N;
+        acc_words += 3ull * 2 * jobs[i].m * k->p.N;
     }
     pl.total = off + acc_words * 8;
     return BM_OK;
 }
 
-int npt_for(u32 N) { return N <= 1024 ? 2 : N / 512; }
-
-template <int NPT>
+template <int LOGN>
 bm_status launch_br(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 steps, const uint64_t *ct_in,
-                    const uint32_t *lut, u64 *ws_acc, u32 *status, u32 N, u32 lB, cudaStream_t st) {
-    const u32 threads = N / NPT;
-    const size_t smem = (size_t)lB * N * 8;
-    BM_CUDA_TRY(cudaFuncSetAttribute(k_blind_rotate<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                    const uint32_t *lut, u64 *ws_acc, u32 *status, cudaStream_t st) {
+    using C = brk::Cfg<LOGN>;
+    const size_t smem = C::SMEM;
+    BM_CUDA_TRY(cudaFuncSetAttribute(k_blind_rotate<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    k_blind_rotate<NPT><<<cnt, threads, smem, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc, status);
+    k_blind_rotate<LOGN><<<cnt, brk::kThreads, smem, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc, status);
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
 }
@@ -408,10 +473,12 @@ bm_status run_blind_rotation(const bm_eval_key *const *keys, const bm_job *jobs,
         uint32_t j = i + 1;
         while (j < count && keys[jobs[j].key]->p.N == N) j++;
         bm_status s = BM_OK;
-        switch (npt_for(N)) {
-            case 2: s = launch_br<2>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, N, k->p.l_B, st); break;
-            case 4: s = launch_br<4>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, N, k->p.l_B, st); break;
-            case 8: s = launch_br<8>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, N, k->p.l_B, st); break;
+        switch (N) {
+            case 256: s = launch_br<8>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, st); break;
+            case 512: s = launch_br<9>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, st); break;
+            case 1024: s = launch_br<10>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, st); break;
+            case 2048: s = launch_br<11>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, st); break;
+            case 4096: s = launch_br<12>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, st); break;
             default: return BM_EINVAL;
         }
         if (s != BM_OK) return s;

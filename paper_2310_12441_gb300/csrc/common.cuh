@@ -19,6 +19,8 @@ struct KeyDev {
     const u64 *twsh;   // their Shoup companions
     const u64 *itw;    // inverse twiddles psi^-bitrev(k)
     const u64 *itwsh;
+    const u64 *twp;    // forward (twiddle, companion) pairs, 16-byte aligned
+    const u64 *itwp;   // inverse pairs
     ModQ mq;
     u64 ninv, ninv_sh; // N^-1 mod Q and companion
     u64 ks_pq;         // floor(P 2^64 / Q), P = B_ks^l_ks
@@ -30,7 +32,8 @@ struct DevJob {
     const KeyDev *key;
     u32 m, t, N, n;
     u64 in_off, lut_off, out_off;
-    u64 acc_off;       // element offset of the job's two ACC buffers in the workspace
+    u64 acc_off;       // element offset of the job's three [m][2][N] buffers in the
+                       // workspace: ACC ping-pong and the per-step row sums
 };
 
 // Host-side evaluation key.

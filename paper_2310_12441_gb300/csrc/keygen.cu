@@ -265,8 +265,9 @@ static bm_status keygen_impl(const bm_key_params *params, const bm_key_randomnes
     const u64 psi = find_psi(Q, N);
     if (!psi) return BM_ENOTPRIME;
 
-    // Twiddle tables: fwd, fwd_sh, inv, inv_sh (each N words).
-    std::vector<u64> tab(4 * (size_t)N);
+    // Twiddle tables: fwd, fwd_sh, inv, inv_sh (each N words), then the same
+    // as interleaved (w, w') pairs, forward and inverse (2N words each).
+    std::vector<u64> tab(8 * (size_t)N);
     const u64 psi_inv = host_powmod(psi, Q - 2, Q);
     for (u32 k = 0; k < N; k++) {
         const u32 br = bitrev(k, logN);
@@ -275,6 +276,10 @@ static bm_status keygen_impl(const bm_key_params *params, const bm_key_randomnes
         tab[N + k] = shoup_of(w, Q);
         tab[2 * N + k] = wi;
         tab[3 * N + k] = shoup_of(wi, Q);
+        tab[4 * N + 2 * k] = w;
+        tab[4 * N + 2 * k + 1] = tab[N + k];
+        tab[6 * N + 2 * k] = wi;
+        tab[6 * N + 2 * k + 1] = tab[3 * N + k];
     }
     const size_t bsk_words = (size_t)n * 2 * 2 * lB * 2 * N;
     const u32 B1 = (1u << p.log2_Bks) - 1;
@@ -296,8 +301,10 @@ static bm_status keygen_impl(const bm_key_params *params, const bm_key_randomnes
     K.twsh = ek->d_tables + N;
     K.itw = ek->d_tables + 2 * N;
     K.itwsh = ek->d_tables + 3 * N;
+    K.twp = ek->d_tables + 4 * N;
+    K.itwp = ek->d_tables + 6 * N;
     BM_CUDA_TRY(cudaMemcpy(ek->d_view, &K, sizeof(KeyDev), cudaMemcpyHostToDevice));
-    u64 *d_zhat = ek->d_tables + 4 * (size_t)N;
+    u64 *d_zhat = ek->d_tables + 8 * (size_t)N;
 
     // Secrets on the device.
     DevBuf d_s, d_z;

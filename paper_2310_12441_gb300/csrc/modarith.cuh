@@ -29,6 +29,19 @@ __device__ __forceinline__ u64 mul_shoup_lazy(u64 a, u64 w, u64 wsh, u64 Q) {
     return a * w - q * Q;
 }
 
+// a * w mod Q in [0, 2Q), Shoup with the quotient taken from three of the
+// four 32 x 32-bit partial products of a * w': dropping a_lo * w'_lo and the
+// carries of the middle terms leaves an estimate at most 2 below
+// floor(a w' / 2^64), so a w - q Q lies in [0, 4Q); one conditional
+// subtraction of 2Q restores [0, 2Q).  Needs 4Q < 2^64.
+__device__ __forceinline__ u64 mul_shoup_q3(u64 a, u64 w, u64 wsh, u64 Q, u64 twoQ) {
+    const u32 a0 = (u32)a, a1 = (u32)(a >> 32);
+    const u32 s0 = (u32)wsh, s1 = (u32)(wsh >> 32);
+    const u64 q = (u64)a1 * s1 + __umulhi(a1, s0) + __umulhi(a0, s1);
+    const u64 r = a * w - q * Q;
+    return r >= twoQ ? r - twoQ : r;
+}
+
 __device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 wsh, u64 Q) {
     return reduce_2q(mul_shoup_lazy(a, w, wsh, Q), Q);
 }

@@ -1,0 +1,194 @@
+// Register-resident negacyclic NTT over Z_Q for batches of polynomials.
+//
+// Same transform as ntt.cuh (Cooley-Tukey forward with psi^bitrev twiddles,
+// bit-reversed output; Gentleman-Sande inverse without the N^-1 factor), but
+// each thread holds R = 16 coefficients of one polynomial in registers and
+// performs up to four butterfly stages on them (a radix-16 phase); between
+// phases the block exchanges values through shared memory.  A polynomial of
+// N = 2^LOGN coefficients takes T = N/16 threads and ceil(LOGN/4) phases.
+//
+// Phase layouts: a thread of a phase whose 4-bit field sits at bits
+// [F, F+4) of the coefficient index holds the 16 indices that differ only in
+// that field; its thread number l supplies the other bits (the bits below F
+// first).  Forward phases take the fields from the top down
+// (F = LOGN-4, LOGN-8, ..., 0), inverse phases from the bottom up.  Stage s
+// of the forward transform acts on index bit LOGN-1-s, stage s of the
+// inverse on bit s; a butterfly group is the index shifted right past that
+// bit.
+//
+// Butterflies are Harvey's lazy ones (D. Harvey, "Faster arithmetic for
+// number-theoretic transforms", J. Symb. Comp. 2014): forward values stay in
+// [0, 4Q), inverse values in [0, 2Q); twiddle products use the three-product
+// Shoup quotient of modarith.cuh.  Twiddles come as (w, w') pairs.
+//
+// Shared memory: every polynomial owns two regions of N words and the
+// exchanges alternate between them (Swap), so a region is never rewritten
+// while a slower thread may still read it and each exchange needs a single
+// barrier.  Index idx is stored at word idx ^ ((idx >> 4) & 15), which keeps
+// every phase's accesses (and position-major accesses) free of bank
+// conflicts.
+#pragma once
+#include "modarith.cuh"
+
+namespace ntr {
+
+__device__ __forceinline__ u32 swz(u32 idx) { return idx ^ ((idx >> 4) & 15u); }
+
+template <int F>
+__device__ __forceinline__ u32 fidx(u32 l, u32 i) {
+    return ((l >> F) << (F + 4)) | (i << F) | (l & ((1u << F) - 1u));
+}
+
+// The two shared regions of one polynomial; `next` is the one written next.
+struct Swap {
+    u64 *r0, *r1;
+    int next;
+    __device__ __forceinline__ u64 *take() {
+        u64 *d = next ? r1 : r0;
+        next ^= 1;
+        return d;
+    }
+};
+
+__device__ __forceinline__ void twiddle(const u64 *__restrict__ tp, u32 ti, u64 &W, u64 &Wsh) {
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(tp) + ti);
+    W = v.x;
+    Wsh = v.y;
+}
+
+// Forward phase: NST stages starting at global stage S0, field [F, F+4).
+template <int LOGN, int F, int S0, int NST>
+__device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__restrict__ twp, u64 Q,
+                                          u64 twoQ) {
+    const u32 high = l >> F;
+#pragma unroll
+    for (int st = 0; st < NST; st++) {
+        const int s = S0 + st;
+        const int lb = LOGN - 1 - s - F;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            if (i & (1 << lb)) continue;
+            const int i2 = i | (1 << lb);
+            const u32 g = (high << (3 - lb)) | (u32)(i >> (lb + 1));
+            u64 W, Wsh;
+            twiddle(twp, (1u << s) + g, W, Wsh);
+            u64 X = x[i];
+            X = X >= twoQ ? X - twoQ : X;
+            const u64 T = mul_shoup_q3(x[i2], W, Wsh, Q, twoQ);
+            x[i] = X + T;
+            x[i2] = X - T + twoQ;
+        }
+    }
+}
+
+// Inverse phase: NST stages acting on bits SB, SB+1, ..., field [F, F+4).
+template <int LOGN, int F, int SB, int NST>
+__device__ __forceinline__ void inv_phase(u64 (&x)[16], u32 l, const u64 *__restrict__ itwp, u64 Q,
+                                          u64 twoQ) {
+    const u32 high = l >> F;
+#pragma unroll
+    for (int st = 0; st < NST; st++) {
+        const int b = SB + st;
+        const int lb = b - F;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            if (i & (1 << lb)) continue;
+            const int i2 = i | (1 << lb);
+            const u32 g = (high << (3 - lb)) | (u32)(i >> (lb + 1));
+            u64 W, Wsh;
+            twiddle(itwp, (1u << (LOGN - 1 - b)) + g, W, Wsh);
+            const u64 U = x[i], V = x[i2];
+            u64 u = U + V;
+            u = u >= twoQ ? u - twoQ : u;
+            x[i] = u;
+            x[i2] = mul_shoup_q3(U - V + twoQ, W, Wsh, Q, twoQ);
+        }
+    }
+}
+
+template <int F>
+__device__ __forceinline__ void store_field(const u64 (&x)[16], u64 *reg, u32 l) {
+#pragma unroll
+    for (int i = 0; i < 16; i++) reg[swz(fidx<F>(l, i))] = x[i];
+}
+
+template <int F>
+__device__ __forceinline__ void load_field(u64 (&x)[16], const u64 *reg, u32 l) {
+#pragma unroll
+    for (int i = 0; i < 16; i++) x[i] = reg[swz(fidx<F>(l, i))];
+}
+
+// Forward NTT.  On entry x holds indices l + T i (field [LOGN-4, LOGN)) of
+// this thread's polynomial, values below 4Q.  Returns the region that holds
+// the transform, fully reduced to [0, Q), in bit-reversed positions
+// (swizzled); the caller must __syncthreads() before reading it.  Every
+// thread of the block calls this (it contains barriers); threads with
+// active == false only take part in the barriers.
+template <int LOGN>
+__device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool active,
+                                            const u64 *__restrict__ twp, u64 Q) {
+    constexpr int NPH = (LOGN + 3) / 4;
+    static_assert(LOGN >= 8 && LOGN <= 12, "ring degree 256..4096");
+    const u64 twoQ = 2 * Q;
+    if (active) fwd_phase<LOGN, LOGN - 4, 0, 4>(x, l, twp, Q, twoQ);
+    u64 *r = sw.take();
+    if (active) store_field<LOGN - 4>(x, r, l);
+    __syncthreads();
+    if constexpr (NPH == 3) {
+        if (active) {
+            load_field<LOGN - 8>(x, r, l);
+            fwd_phase<LOGN, LOGN - 8, 4, 4>(x, l, twp, Q, twoQ);
+        }
+        r = sw.take();
+        if (active) store_field<LOGN - 8>(x, r, l);
+        __syncthreads();
+    }
+    if (active) {
+        load_field<0>(x, r, l);
+        fwd_phase<LOGN, 0, 4 * (NPH - 1), LOGN - 4 * (NPH - 1)>(x, l, twp, Q, twoQ);
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            u64 v = x[i];
+            v = v >= twoQ ? v - twoQ : v;
+            x[i] = v >= Q ? v - Q : v;
+        }
+    }
+    r = sw.take();
+    if (active) store_field<0>(x, r, l);
+    return r;
+}
+
+// Inverse NTT (without N^-1).  On entry region `in` holds the bit-reversed
+// transform (swizzled, values below 2Q) and the block has passed a barrier
+// since it was written; `in` must be the region sw wrote last.  On exit x
+// holds natural-order coefficients l + T i, reduced to [0, Q).
+template <int LOGN>
+__device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap &sw, u32 l, bool active,
+                                              const u64 *__restrict__ itwp, u64 Q) {
+    constexpr int NPH = (LOGN + 3) / 4;
+    const u64 twoQ = 2 * Q;
+    if (active) {
+        load_field<0>(x, in, l);
+        inv_phase<LOGN, 0, 0, 4>(x, l, itwp, Q, twoQ);
+    }
+    u64 *r = sw.take();
+    if (active) store_field<0>(x, r, l);
+    __syncthreads();
+    if constexpr (NPH == 3) {
+        if (active) {
+            load_field<4>(x, r, l);
+            inv_phase<LOGN, 4, 4, 4>(x, l, itwp, Q, twoQ);
+        }
+        r = sw.take();
+        if (active) store_field<4>(x, r, l);
+        __syncthreads();
+    }
+    if (active) {
+        load_field<LOGN - 4>(x, r, l);
+        inv_phase<LOGN, LOGN - 4, 4 * (NPH - 1), LOGN - 4 * (NPH - 1)>(x, l, itwp, Q, twoQ);
+#pragma unroll
+        for (int i = 0; i < 16; i++) x[i] = x[i] >= Q ? x[i] - Q : x[i];
+    }
+}
+
+}  // namespace ntr

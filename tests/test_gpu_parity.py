@@ -48,6 +48,11 @@ def n2048(api, orc):
     return KeySet(api, orc, P.KEYS_N2048, 1003, 4)
 
 
+@pytest.fixture(scope="module")
+def n4096(api, orc):
+    return KeySet(api, orc, P.KEYS_N4096, 1002, 3)
+
+
 def _encrypt(orc, ks, m, t, count, seed, prefix=None, half=None):
     kp = ks.kp
     qp = 2 * kp.N * m
@@ -178,11 +183,43 @@ def test_blind_rotate_prefix_ciphertexts_n2048(api, orc, n2048):
         assert np.array_equal(got[i], orc.blind_rotate(kp, m, t, n2048.bsk, ct[i], luts[i]))
 
 
+def test_blind_rotate_single_polynomial_n4096(api, orc, n4096):
+    """The m = 1, N = 4096 layout (same q' = 8192 and t as the N = 1024, m = 4
+    batch), prefix ciphertexts, bit-exact."""
+    kp, m, t = n4096.kp, 1, 1024
+    msg, ct = _encrypt(orc, n4096, m, t, 2, 4, prefix=3)
+    luts, _ = synth.luts(t, 2, 2004)
+    jobs = _uniform_jobs(api, 2, kp.n, t, m)
+    got = _blind_rotate_gpu(api, n4096, jobs, ct, luts, 1 << 30)
+    for i in range(2):
+        assert np.array_equal(got[i], orc.blind_rotate(kp, m, t, n4096.bsk, ct[i], luts[i]))
+
+
+def test_bootstrap_prefix_n4096_bit_exact(api, orc, n4096):
+    kp, m, t = n4096.kp, 1, 1024
+    msg, ct = _encrypt(orc, n4096, m, t, 2, 5, prefix=3)
+    luts, _ = synth.luts(t, 2, 2005)
+    jobs = _uniform_jobs(api, 2, kp.n, t, m)
+    got = _run_batch(api, [n4096.ek], jobs, ct, luts, 2 * (kp.n + 1)).reshape(2, kp.n + 1)
+    assert np.array_equal(got, orc.bootstrap(kp, m, t, n4096.bsk, n4096.ksk, ct, luts))
+
+
+@pytest.mark.parametrize("m,t", [(2, 1 << 11), (4, 1 << 12), (1, 1 << 10)])
+def test_blind_rotate_n2048_other_shapes(api, orc, n2048, m, t):
+    kp = n2048.kp
+    msg, ct = _encrypt(orc, n2048, m, t, 3, 6 + m, prefix=4)
+    luts, _ = synth.luts(t, 3, 2006 + m)
+    jobs = _uniform_jobs(api, 3, kp.n, t, m)
+    got = _blind_rotate_gpu(api, n2048, jobs, ct, luts, 1 << 30)
+    for i in range(3):
+        assert np.array_equal(got[i], orc.blind_rotate(kp, m, t, n2048.bsk, ct[i], luts[i]))
+
+
 def test_blind_rotate_uneven_shapes_one_call(api, orc, n1024):
     """Jobs with different (m, t) in one call (the uneven-batch sets on the
     N = 1024 key), prefix ciphertexts so the oracle stays fast."""
     kp = n1024.kp
-    shapes = [(1, 256), (2, 512), (4, 1024), (2, 512), (1, 256)]
+    shapes = [(1, 256), (2, 512), (4, 1024), (2, 512), (1, 256), (3, 768), (5, 1280)]
     cts, luts_l, jobs = [], [], []
     in_off = lut_off = 0
     for i, (m, t) in enumerate(shapes):
