@@ -111,7 +111,7 @@ struct Cfg {
 };
 }  // namespace brk
 
-template <int LOGN>
+template <int LOGN, bool LAZY>
 __global__ void __launch_bounds__(brk::kThreads, 1)
     k_blind_rotate(const DevJob *__restrict__ jobs, u32 steps_limit, const u64 *__restrict__ ct_in,
                    const u32 *__restrict__ luts, u64 *ws, u32 *status) {
@@ -179,26 +179,44 @@ __global__ void __launch_bounds__(brk::kThreads, 1)
                         x[i] = (D >> sh) & Bmask;
                     }
                 }
-                u64 *out = ntr::fwd_to_smem<LOGN>(x, sw, l, active, twp, Q);
+                u64 *out = ntr::fwd_to_smem<LOGN, LAZY>(x, sw, l, active, twp, Q, mq.one_sh);
                 // regions of the other polynomials of the batch sit at stride N
                 const u64 *slots = out - (size_t)p * N;
                 __syncthreads();
                 // --- multiply-accumulate against the key rows of the batch's combos
+                // (combo c = (sign, component, digit) is key row c of the step)
+                const u64 *bsk_c0 = bsk_k + (size_t)c0 * 2 * N;
+                if (c0 + C::P <= ncomb) {
 #pragma unroll
-                for (int j = 0; j < C::PPT; j++) {
-                    const u32 q = tid + brk::kThreads * j;
-                    if (q < (u32)N) {
-                        const u32 sq = ntr::swz(q);
+                    for (int j = 0; j < C::PPT; j++) {
+                        const u32 q = tid + brk::kThreads * j;
+                        if (q < (u32)N) {
+                            const u32 sq = ntr::swz(q);
+                            u64 b0[C::P], b1[C::P];
 #pragma unroll
-                        for (int cc = 0; cc < C::P; cc++) {
-                            const u32 c2 = c0 + cc;
-                            if (c2 < ncomb) {
-                                // combo c = (sign, component, digit) is key row c of the step
-                                const u64 *brow = bsk_k + (size_t)c2 * 2 * N;
-                                const u64 b0 = __ldg(brow + q), b1 = __ldg(brow + N + q);
+                            for (int cc = 0; cc < C::P; cc++) {
+                                b0[cc] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q);
+                                b1[cc] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q);
+                            }
+#pragma unroll
+                            for (int cc = 0; cc < C::P; cc++) {
                                 const u64 xv = slots[(size_t)cc * N + sq];
-                                mac128(lo[0][j], hi[0][j], xv, b0);
-                                mac128(lo[1][j], hi[1][j], xv, b1);
+                                mac128(lo[0][j], hi[0][j], xv, b0[cc]);
+                                mac128(lo[1][j], hi[1][j], xv, b1[cc]);
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < C::PPT; j++) {
+                        const u32 q = tid + brk::kThreads * j;
+                        if (q < (u32)N) {
+                            const u32 sq = ntr::swz(q);
+                            for (u32 cc = 0; c0 + cc < ncomb; cc++) {
+                                const u64 *brow = bsk_c0 + (size_t)cc * 2 * N;
+                                const u64 xv = slots[(size_t)cc * N + sq];
+                                mac128(lo[0][j], hi[0][j], xv, __ldg(brow + q));
+                                mac128(lo[1][j], hi[1][j], xv, __ldg(brow + N + q));
                             }
                         }
                     }
@@ -446,16 +464,27 @@ bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t
     return BM_OK;
 }
 
-template <int LOGN>
-bm_status launch_br(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 steps, const uint64_t *ct_in,
-                    const uint32_t *lut, u64 *ws_acc, u32 *status, cudaStream_t st) {
+template <int LOGN, bool LAZY>
+bm_status launch_br_v(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 steps, const uint64_t *ct_in,
+                      const uint32_t *lut, u64 *ws_acc, u32 *status, cudaStream_t st) {
     using C = brk::Cfg<LOGN>;
     const size_t smem = C::SMEM;
-    BM_CUDA_TRY(cudaFuncSetAttribute(k_blind_rotate<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    BM_CUDA_TRY(cudaFuncSetAttribute(k_blind_rotate<LOGN, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    k_blind_rotate<LOGN><<<cnt, brk::kThreads, smem, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc, status);
+    k_blind_rotate<LOGN, LAZY><<<cnt, brk::kThreads, smem, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc,
+                                                                status);
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
+}
+
+// The correction-free forward transform needs (1 + 4 log2 N) Q < 2^64.
+template <int LOGN>
+bm_status launch_br(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 steps, const uint64_t *ct_in,
+                    const uint32_t *lut, u64 *ws_acc, u32 *status, u64 Q, cudaStream_t st) {
+    const unsigned __int128 bound = (unsigned __int128)(1 + 4 * LOGN) * Q;
+    if (bound < ((unsigned __int128)1 << 64))
+        return launch_br_v<LOGN, true>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, st);
+    return launch_br_v<LOGN, false>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, st);
 }
 
 // Launches blind rotation for every job; jobs are grouped by ring degree
@@ -471,14 +500,15 @@ bm_status run_blind_rotation(const bm_eval_key *const *keys, const bm_job *jobs,
         const bm_eval_key *k = keys[jobs[i].key];
         const u32 N = k->p.N;
         uint32_t j = i + 1;
-        while (j < count && keys[jobs[j].key]->p.N == N) j++;
+        const u64 Q = k->p.Q;
+        while (j < count && keys[jobs[j].key]->p.N == N && keys[jobs[j].key]->p.Q == Q) j++;
         bm_status s = BM_OK;
         switch (N) {
-            case 256: s = launch_br<8>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, st); break;
-            case 512: s = launch_br<9>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, st); break;
-            case 1024: s = launch_br<10>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, st); break;
-            case 2048: s = launch_br<11>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, st); break;
-            case 4096: s = launch_br<12>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, st); break;
+            case 256: s = launch_br<8>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, st); break;
+            case 512: s = launch_br<9>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, st); break;
+            case 1024: s = launch_br<10>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, st); break;
+            case 2048: s = launch_br<11>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, st); break;
+            case 4096: s = launch_br<12>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, st); break;
             default: return BM_EINVAL;
         }
         if (s != BM_OK) return s;

@@ -42,6 +42,14 @@ __device__ __forceinline__ u64 mul_shoup_q3(u64 a, u64 w, u64 wsh, u64 Q, u64 tw
     return r >= twoQ ? r - twoQ : r;
 }
 
+// Same estimate without the final correction: result in [0, 4Q).
+__device__ __forceinline__ u64 mul_shoup_q3_lazy(u64 a, u64 w, u64 wsh, u64 Q) {
+    const u32 a0 = (u32)a, a1 = (u32)(a >> 32);
+    const u32 s0 = (u32)wsh, s1 = (u32)(wsh >> 32);
+    const u64 q = (u64)a1 * s1 + __umulhi(a1, s0) + __umulhi(a0, s1);
+    return a * w - q * Q;
+}
+
 __device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 wsh, u64 Q) {
     return reduce_2q(mul_shoup_lazy(a, w, wsh, Q), Q);
 }

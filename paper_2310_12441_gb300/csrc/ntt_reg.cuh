@@ -57,7 +57,11 @@ __device__ __forceinline__ void twiddle(const u64 *__restrict__ tp, u32 ti, u64 
 }
 
 // Forward phase: NST stages starting at global stage S0, field [F, F+4).
-template <int LOGN, int F, int S0, int NST>
+// LAZY: no per-stage corrections.  Products lie in [0, 4Q) and the sum and
+// difference X + T, X - T + 4Q each grow the bound by 4Q, so inputs below Q
+// leave the last stage below (1 + 4 LOGN) Q, which the caller guarantees
+// fits in 64 bits.  Otherwise Harvey's [0, 4Q) invariant is kept.
+template <int LOGN, int F, int S0, int NST, bool LAZY>
 __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__restrict__ twp, u64 Q,
                                           u64 twoQ) {
     const u32 high = l >> F;
@@ -72,11 +76,18 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__rest
             const u32 g = (high << (3 - lb)) | (u32)(i >> (lb + 1));
             u64 W, Wsh;
             twiddle(twp, (1u << s) + g, W, Wsh);
-            u64 X = x[i];
-            X = X >= twoQ ? X - twoQ : X;
-            const u64 T = mul_shoup_q3(x[i2], W, Wsh, Q, twoQ);
-            x[i] = X + T;
-            x[i2] = X - T + twoQ;
+            if constexpr (LAZY) {
+                const u64 X = x[i];
+                const u64 T = mul_shoup_q3_lazy(x[i2], W, Wsh, Q);
+                x[i] = X + T;
+                x[i2] = X - T + 2 * twoQ;
+            } else {
+                u64 X = x[i];
+                X = X >= twoQ ? X - twoQ : X;
+                const u64 T = mul_shoup_q3(x[i2], W, Wsh, Q, twoQ);
+                x[i] = X + T;
+                x[i2] = X - T + twoQ;
+            }
         }
     }
 }
@@ -124,20 +135,20 @@ __device__ __forceinline__ void load_field(u64 (&x)[16], const u64 *reg, u32 l) 
 // (swizzled); the caller must __syncthreads() before reading it.  Every
 // thread of the block calls this (it contains barriers); threads with
 // active == false only take part in the barriers.
-template <int LOGN>
+template <int LOGN, bool LAZY>
 __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool active,
-                                            const u64 *__restrict__ twp, u64 Q) {
+                                            const u64 *__restrict__ twp, u64 Q, u64 one_sh) {
     constexpr int NPH = (LOGN + 3) / 4;
     static_assert(LOGN >= 8 && LOGN <= 12, "ring degree 256..4096");
     const u64 twoQ = 2 * Q;
-    if (active) fwd_phase<LOGN, LOGN - 4, 0, 4>(x, l, twp, Q, twoQ);
+    if (active) fwd_phase<LOGN, LOGN - 4, 0, 4, LAZY>(x, l, twp, Q, twoQ);
     u64 *r = sw.take();
     if (active) store_field<LOGN - 4>(x, r, l);
     __syncthreads();
     if constexpr (NPH == 3) {
         if (active) {
             load_field<LOGN - 8>(x, r, l);
-            fwd_phase<LOGN, LOGN - 8, 4, 4>(x, l, twp, Q, twoQ);
+            fwd_phase<LOGN, LOGN - 8, 4, 4, LAZY>(x, l, twp, Q, twoQ);
         }
         r = sw.take();
         if (active) store_field<LOGN - 8>(x, r, l);
@@ -145,11 +156,15 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
     }
     if (active) {
         load_field<0>(x, r, l);
-        fwd_phase<LOGN, 0, 4 * (NPH - 1), LOGN - 4 * (NPH - 1)>(x, l, twp, Q, twoQ);
+        fwd_phase<LOGN, 0, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), LAZY>(x, l, twp, Q, twoQ);
 #pragma unroll
         for (int i = 0; i < 16; i++) {
             u64 v = x[i];
-            v = v >= twoQ ? v - twoQ : v;
+            if constexpr (LAZY) {
+                v = v - __umul64hi(v, one_sh) * Q;     // Shoup with w = 1: [0, 2Q)
+            } else {
+                v = v >= twoQ ? v - twoQ : v;
+            }
             x[i] = v >= Q ? v - Q : v;
         }
     }
