@@ -107,11 +107,12 @@ struct Cfg {
     static constexpr int T = N / 16;                               // threads per polynomial
     static constexpr int P = kThreads / T;                         // polynomials per batch
     static constexpr int PPT = N >= kThreads ? N / kThreads : 1;   // positions per thread
-    static constexpr size_t SMEM = 2ull * P * N * 8;               // two regions per polynomial
+    static constexpr bool DSM = LOGN <= 11;                        // row differences in smem
+    static constexpr size_t SMEM = 2ull * P * N * 8 + (DSM ? 4ull * N * 8 : 0);
 };
 }  // namespace brk
 
-template <int LOGN, bool LAZY>
+template <int LOGN, bool LAZY, bool SMALL0>
 __global__ void __launch_bounds__(brk::kThreads, 1)
     k_blind_rotate(const DevJob *__restrict__ jobs, u32 steps_limit, const u64 *__restrict__ ct_in,
                    const u32 *__restrict__ luts, u64 *ws, u32 *status) {
@@ -145,6 +146,8 @@ __global__ void __launch_bounds__(brk::kThreads, 1)
     const u32 p = tid / C::T;          // polynomial slot within a batch
     const u32 l = tid % C::T;          // thread within the polynomial
     ntr::Swap sw{sm + (size_t)p * N, sm + (size_t)(C::P + p) * N, 0};
+    u64 *dbuf = sm + (size_t)2 * C::P * N;   // [4][N] row differences (DSM only)
+    const u64 qb = Q << log2B;                 // Q * B, used when SMALL0
     const u32 ncomb = 4 * lB;
     const size_t rgsw = (size_t)2 * lB * 2 * N;
 
@@ -157,12 +160,33 @@ __global__ void __launch_bounds__(brk::kThreads, 1)
             u64 lo[2][C::PPT], hi[2][C::PPT];
 #pragma unroll
             for (int j = 0; j < C::PPT; j++) lo[0][j] = hi[0][j] = lo[1][j] = hi[1][j] = 0;
+            if constexpr (C::DSM) {
+                // D_(sign, comp) = P(c) ACC - ACC for row r, c = -a_k / a_k
+                for (u32 w = tid; w < 4u * N; w += brk::kThreads) {
+                    const u32 pair = w / N, idx = w % N;
+                    const u32 sgn = pair >> 1, comp = pair & 1;
+                    const u64 cv = sgn == 0 ? (qp - ak) % qp : ak;
+                    const u32 ea = (u32)(cv / m), bb = (u32)(cv % m);
+                    const u32 src = r >= bb ? r - bb : r + m - bb;
+                    u32 e = r >= bb ? ea : ea + 1;
+                    if (e >= 2 * N) e -= 2 * N;
+                    const u64 *srow = cur + ((size_t)src * 2 + comp) * N;
+                    const u64 *orow = cur + ((size_t)r * 2 + comp) * N;
+                    dbuf[w] = sub_mod(rotated_coeff(srow, idx, e, N, Q), orow[idx], Q);
+                }
+                __syncthreads();
+            }
             for (u32 c0 = 0; c0 < ncomb; c0 += C::P) {
                 // --- this thread's digit polynomial, transformed into shared memory
                 const u32 c = c0 + p;
                 const bool active = c < ncomb;
                 u64 x[16];
-                if (active) {
+                if (active && C::DSM) {
+                    const u32 pair = c / lB, sh = (c % lB) * log2B;
+                    const u64 *dp = dbuf + (size_t)pair * N;
+#pragma unroll
+                    for (int i = 0; i < 16; i++) x[i] = (dp[l + C::T * i] >> sh) & Bmask;
+                } else if (active) {
                     const u32 sgn = c / (2 * lB), comp = (c / lB) & 1, d = c % lB;
                     const u64 cv = sgn == 0 ? (qp - ak) % qp : ak;
                     const u32 ea = (u32)(cv / m), bb = (u32)(cv % m);
@@ -179,7 +203,7 @@ __global__ void __launch_bounds__(brk::kThreads, 1)
                         x[i] = (D >> sh) & Bmask;
                     }
                 }
-                u64 *out = ntr::fwd_to_smem<LOGN, LAZY>(x, sw, l, active, twp, Q, mq.one_sh);
+                u64 *out = ntr::fwd_to_smem<LOGN, LAZY, SMALL0>(x, sw, l, active, twp, Q, mq.one_sh, qb);
                 // regions of the other polynomials of the batch sit at stride N
                 const u64 *slots = out - (size_t)p * N;
                 __syncthreads();
@@ -464,27 +488,33 @@ bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t
     return BM_OK;
 }
 
-template <int LOGN, bool LAZY>
+template <int LOGN, bool LAZY, bool SMALL0>
 bm_status launch_br_v(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 steps, const uint64_t *ct_in,
                       const uint32_t *lut, u64 *ws_acc, u32 *status, cudaStream_t st) {
     using C = brk::Cfg<LOGN>;
     const size_t smem = C::SMEM;
-    BM_CUDA_TRY(cudaFuncSetAttribute(k_blind_rotate<LOGN, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    k_blind_rotate<LOGN, LAZY><<<cnt, brk::kThreads, smem, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc,
-                                                                status);
+    auto kern = k_blind_rotate<LOGN, LAZY, SMALL0>;
+    BM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<cnt, brk::kThreads, smem, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc, status);
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
 }
 
-// The correction-free forward transform needs (1 + 4 log2 N) Q < 2^64.
+// The correction-free forward transform needs (1 + 4 log2 N) Q < 2^64; its
+// exact first stage additionally needs B + Q B + 4 Q (log2 N - 1) < 2^64.
 template <int LOGN>
 bm_status launch_br(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 steps, const uint64_t *ct_in,
-                    const uint32_t *lut, u64 *ws_acc, u32 *status, u64 Q, cudaStream_t st) {
-    const unsigned __int128 bound = (unsigned __int128)(1 + 4 * LOGN) * Q;
-    if (bound < ((unsigned __int128)1 << 64))
-        return launch_br_v<LOGN, true>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, st);
-    return launch_br_v<LOGN, false>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, st);
+                    const uint32_t *lut, u64 *ws_acc, u32 *status, u64 Q, u32 log2B, cudaStream_t st) {
+    typedef unsigned __int128 u128;
+    const u128 lim = (u128)1 << 64;
+    const u128 lazy = (u128)(1 + 4 * LOGN) * Q;
+    const u128 B = (u128)1 << log2B;
+    const u128 small0 = B + (u128)Q * B + (u128)4 * Q * (LOGN - 1);
+    if (lazy < lim && small0 < lim && log2B <= 31)
+        return launch_br_v<LOGN, true, true>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, st);
+    if (lazy < lim)
+        return launch_br_v<LOGN, true, false>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, st);
+    return launch_br_v<LOGN, false, false>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, st);
 }
 
 // Launches blind rotation for every job; jobs are grouped by ring degree
@@ -501,14 +531,17 @@ bm_status run_blind_rotation(const bm_eval_key *const *keys, const bm_job *jobs,
         const u32 N = k->p.N;
         uint32_t j = i + 1;
         const u64 Q = k->p.Q;
-        while (j < count && keys[jobs[j].key]->p.N == N && keys[jobs[j].key]->p.Q == Q) j++;
+        const u32 log2B = k->p.log2_B;
+        while (j < count && keys[jobs[j].key]->p.N == N && keys[jobs[j].key]->p.Q == Q &&
+               keys[jobs[j].key]->p.log2_B == log2B)
+            j++;
         bm_status s = BM_OK;
         switch (N) {
-            case 256: s = launch_br<8>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, st); break;
-            case 512: s = launch_br<9>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, st); break;
-            case 1024: s = launch_br<10>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, st); break;
-            case 2048: s = launch_br<11>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, st); break;
-            case 4096: s = launch_br<12>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, st); break;
+            case 256: s = launch_br<8>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, log2B, st); break;
+            case 512: s = launch_br<9>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, log2B, st); break;
+            case 1024: s = launch_br<10>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, log2B, st); break;
+            case 2048: s = launch_br<11>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, log2B, st); break;
+            case 4096: s = launch_br<12>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, log2B, st); break;
             default: return BM_EINVAL;
         }
         if (s != BM_OK) return s;

@@ -61,9 +61,13 @@ __device__ __forceinline__ void twiddle(const u64 *__restrict__ tp, u32 ti, u64 
 // difference X + T, X - T + 4Q each grow the bound by 4Q, so inputs below Q
 // leave the last stage below (1 + 4 LOGN) Q, which the caller guarantees
 // fits in 64 bits.  Otherwise Harvey's [0, 4Q) invariant is kept.
-template <int LOGN, int F, int S0, int NST, bool LAZY>
+// SMALL0 (with LAZY): the first stage's inputs are digits below B < 2^32, so
+// W * Y is formed exactly (a 64 x 32-bit product) and left unreduced:
+// X + W Y and X - W Y + Q B, both below B + Q B.  The caller guarantees
+// B + Q B + 4 Q (LOGN - 1) < 2^64.
+template <int LOGN, int F, int S0, int NST, bool LAZY, bool SMALL0 = false>
 __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__restrict__ twp, u64 Q,
-                                          u64 twoQ) {
+                                          u64 twoQ, u64 qb = 0) {
     const u32 high = l >> F;
 #pragma unroll
     for (int st = 0; st < NST; st++) {
@@ -76,6 +80,16 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__rest
             const u32 g = (high << (3 - lb)) | (u32)(i >> (lb + 1));
             u64 W, Wsh;
             twiddle(twp, (1u << s) + g, W, Wsh);
+            if constexpr (LAZY && SMALL0 && S0 == 0) {
+                if (st == 0) {
+                    const u32 y = (u32)x[i2];
+                    const u64 T = (u64)(u32)W * y + ((u64)((u32)(W >> 32) * y) << 32);
+                    const u64 X = x[i];
+                    x[i] = X + T;
+                    x[i2] = X - T + qb;
+                    continue;
+                }
+            }
             if constexpr (LAZY) {
                 const u64 X = x[i];
                 const u64 T = mul_shoup_q3_lazy(x[i2], W, Wsh, Q);
@@ -135,13 +149,13 @@ __device__ __forceinline__ void load_field(u64 (&x)[16], const u64 *reg, u32 l) 
 // (swizzled); the caller must __syncthreads() before reading it.  Every
 // thread of the block calls this (it contains barriers); threads with
 // active == false only take part in the barriers.
-template <int LOGN, bool LAZY>
+template <int LOGN, bool LAZY, bool SMALL0 = false>
 __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool active,
-                                            const u64 *__restrict__ twp, u64 Q, u64 one_sh) {
+                                            const u64 *__restrict__ twp, u64 Q, u64 one_sh, u64 qb = 0) {
     constexpr int NPH = (LOGN + 3) / 4;
     static_assert(LOGN >= 8 && LOGN <= 12, "ring degree 256..4096");
     const u64 twoQ = 2 * Q;
-    if (active) fwd_phase<LOGN, LOGN - 4, 0, 4, LAZY>(x, l, twp, Q, twoQ);
+    if (active) fwd_phase<LOGN, LOGN - 4, 0, 4, LAZY, SMALL0>(x, l, twp, Q, twoQ, qb);
     u64 *r = sw.take();
     if (active) store_field<LOGN - 4>(x, r, l);
     __syncthreads();
