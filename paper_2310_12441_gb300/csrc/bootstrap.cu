@@ -100,9 +100,13 @@ __device__ void acc_init(u64 *__restrict__ acc, const u32 *__restrict__ lut, u64
 // next ACC buffer.
 // ---------------------------------------------------------------------------
 namespace brk {
-constexpr int kThreads = 512;
+// Up to N = 1024 two blocks of 256 threads share an SM (two jobs whose
+// barriers and memory phases overlap each other's arithmetic); larger rings
+// use one block of 512 threads.
 template <int LOGN>
 struct Cfg {
+    static constexpr int kThreads = LOGN <= 10 ? 256 : 512;
+    static constexpr int kBlocksPerSM = 512 / kThreads;
     static constexpr int N = 1 << LOGN;
     static constexpr int T = N / 16;                               // threads per polynomial
     static constexpr int P = kThreads / T;                         // polynomials per batch
@@ -113,7 +117,7 @@ struct Cfg {
 }  // namespace brk
 
 template <int LOGN, bool LAZY, bool SMALL0>
-__global__ void __launch_bounds__(brk::kThreads, 1)
+__global__ void __launch_bounds__(brk::Cfg<LOGN>::kThreads, brk::Cfg<LOGN>::kBlocksPerSM)
     k_blind_rotate(const DevJob *__restrict__ jobs, u32 steps_limit, const u64 *__restrict__ ct_in,
                    const u32 *__restrict__ luts, u64 *ws, u32 *status) {
     using C = brk::Cfg<LOGN>;
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(brk::kThreads, 1)
             for (int j = 0; j < C::PPT; j++) lo[0][j] = hi[0][j] = lo[1][j] = hi[1][j] = 0;
             if constexpr (C::DSM) {
                 // D_(sign, comp) = P(c) ACC - ACC for row r, c = -a_k / a_k
-                for (u32 w = tid; w < 4u * N; w += brk::kThreads) {
+                for (u32 w = tid; w < 4u * N; w += C::kThreads) {
                     const u32 pair = w / N, idx = w % N;
                     const u32 sgn = pair >> 1, comp = pair & 1;
                     const u64 cv = sgn == 0 ? (qp - ak) % qp : ak;
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(brk::kThreads, 1)
                 if (c0 + C::P <= ncomb) {
 #pragma unroll
                     for (int j = 0; j < C::PPT; j++) {
-                        const u32 q = tid + brk::kThreads * j;
+                        const u32 q = tid + C::kThreads * j;
                         if (q < (u32)N) {
                             const u32 sq = ntr::swz(q);
                             u64 b0[C::P], b1[C::P];
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(brk::kThreads, 1)
                 } else {
 #pragma unroll
                     for (int j = 0; j < C::PPT; j++) {
-                        const u32 q = tid + brk::kThreads * j;
+                        const u32 q = tid + C::kThreads * j;
                         if (q < (u32)N) {
                             const u32 sq = ntr::swz(q);
                             for (u32 cc = 0; c0 + cc < ncomb; cc++) {
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(brk::kThreads, 1)
             // --- reduced row sums (NTT domain) to the sum buffer
 #pragma unroll
             for (int j = 0; j < C::PPT; j++) {
-                const u32 q = tid + brk::kThreads * j;
+                const u32 q = tid + C::kThreads * j;
                 if (q < (u32)N) {
                     sums[((size_t)r * 2) * N + q] = reduce128(lo[0][j], hi[0][j], mq);
                     sums[((size_t)r * 2 + 1) * N + q] = reduce128(lo[1][j], hi[1][j], mq);
@@ -495,7 +499,7 @@ bm_status launch_br_v(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 st
     const size_t smem = C::SMEM;
     auto kern = k_blind_rotate<LOGN, LAZY, SMALL0>;
     BM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<cnt, brk::kThreads, smem, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc, status);
+    kern<<<cnt, C::kThreads, smem, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc, status);
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
 }
