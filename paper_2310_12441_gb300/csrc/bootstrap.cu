@@ -116,10 +116,10 @@ struct Cfg {
 };
 }  // namespace brk
 
-template <int LOGN, bool LAZY, bool SMALL0>
+template <int LOGN, bool LAZY, bool SMALL0, bool QLOW1>
 __global__ void __launch_bounds__(brk::Cfg<LOGN>::kThreads, brk::Cfg<LOGN>::kBlocksPerSM)
     k_blind_rotate(const DevJob *__restrict__ jobs, u32 steps_limit, const u64 *__restrict__ ct_in,
-                   const u32 *__restrict__ luts, u64 *ws, u32 *status) {
+                   const u32 *__restrict__ luts, u64 *ws, u32 *status, u32 lbits, bool fold_each) {
     using C = brk::Cfg<LOGN>;
     constexpr int N = C::N;
     extern __shared__ u64 sm[];
@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(brk::Cfg<LOGN>::kThreads, brk::Cfg<LOGN>::kBlo
     ntr::Swap sw{sm + (size_t)p * N, sm + (size_t)(C::P + p) * N, 0};
     u64 *dbuf = sm + (size_t)2 * C::P * N;   // [4][N] row differences (DSM only)
     const u64 qb = Q << log2B;                 // Q * B, used when SMALL0
+    const u64 lmask = (1ull << lbits) - 1;     // Karatsuba limb mask
     const u32 ncomb = 4 * lB;
     const size_t rgsw = (size_t)2 * lB * 2 * N;
 
@@ -207,45 +208,71 @@ __global__ void __launch_bounds__(brk::Cfg<LOGN>::kThreads, brk::Cfg<LOGN>::kBlo
                         x[i] = (D >> sh) & Bmask;
                     }
                 }
-                u64 *out = ntr::fwd_to_smem<LOGN, LAZY, SMALL0>(x, sw, l, active, twp, Q, mq.one_sh, qb);
+                u64 *out = ntr::fwd_to_smem<LOGN, LAZY, SMALL0, QLOW1>(x, sw, l, active, twp, Q, mq.one_sh, qb);
                 // regions of the other polynomials of the batch sit at stride N
                 const u64 *slots = out - (size_t)p * N;
                 __syncthreads();
                 // --- multiply-accumulate against the key rows of the batch's combos
-                // (combo c = (sign, component, digit) is key row c of the step)
+                // (combo c = (sign, component, digit) is key row c of the step).
+                // Karatsuba on half-width limbs x = x1 2^lbits + x0: the limb
+                // products x1 b1, x0 b0 and (x0 + x1)(b0 + b1) are summed over
+                // the batch in 64-bit registers, then folded into the 128-bit
+                // row sums as hi 2^(2 lbits) + (mid - hi - lo) 2^lbits + lo.
                 const u64 *bsk_c0 = bsk_k + (size_t)c0 * 2 * N;
-                if (c0 + C::P <= ncomb) {
+                const u32 nc = ncomb - c0 < (u32)C::P ? ncomb - c0 : (u32)C::P;
+                auto fold = [&](int j, u64 (&kh)[2], u64 (&kl)[2], u64 (&km)[2]) {
+#pragma unroll
+                    for (int col = 0; col < 2; col++) {
+                        add128(lo[col][j], hi[col][j], kl[col]);
+                        add128_shl(lo[col][j], hi[col][j], km[col] - kh[col] - kl[col], lbits);
+                        add128_shl(lo[col][j], hi[col][j], kh[col], 2 * lbits);
+                        kh[col] = kl[col] = km[col] = 0;
+                    }
+                };
+                auto kara = [&](u64 xv, u64 bv, u64 &kh, u64 &kl, u64 &km) {
+                    const u32 x0 = (u32)(xv & lmask), x1 = (u32)(xv >> lbits);
+                    const u32 b0 = (u32)(bv & lmask), b1 = (u32)(bv >> lbits);
+                    kh += (u64)x1 * b1;
+                    kl += (u64)x0 * b0;
+                    km += (u64)(x0 + x1) * (b0 + b1);
+                };
+                if (nc == (u32)C::P && !fold_each) {
+                    // full batch: every key word of a position is requested first
 #pragma unroll
                     for (int j = 0; j < C::PPT; j++) {
                         const u32 q = tid + C::kThreads * j;
                         if (q < (u32)N) {
                             const u32 sq = ntr::swz(q);
-                            u64 b0[C::P], b1[C::P];
+                            u64 bv[C::P][2];
 #pragma unroll
                             for (int cc = 0; cc < C::P; cc++) {
-                                b0[cc] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q);
-                                b1[cc] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q);
+                                bv[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q);
+                                bv[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q);
                             }
+                            u64 kh[2] = {0, 0}, kl[2] = {0, 0}, km[2] = {0, 0};
 #pragma unroll
                             for (int cc = 0; cc < C::P; cc++) {
                                 const u64 xv = slots[(size_t)cc * N + sq];
-                                mac128(lo[0][j], hi[0][j], xv, b0[cc]);
-                                mac128(lo[1][j], hi[1][j], xv, b1[cc]);
+                                kara(xv, bv[cc][0], kh[0], kl[0], km[0]);
+                                kara(xv, bv[cc][1], kh[1], kl[1], km[1]);
                             }
+                            fold(j, kh, kl, km);
                         }
                     }
                 } else {
-#pragma unroll
                     for (int j = 0; j < C::PPT; j++) {
                         const u32 q = tid + C::kThreads * j;
                         if (q < (u32)N) {
                             const u32 sq = ntr::swz(q);
-                            for (u32 cc = 0; c0 + cc < ncomb; cc++) {
-                                const u64 *brow = bsk_c0 + (size_t)cc * 2 * N;
+                            u64 kh[2] = {0, 0}, kl[2] = {0, 0}, km[2] = {0, 0};
+                            for (u32 cc = 0; cc < nc; cc++) {
                                 const u64 xv = slots[(size_t)cc * N + sq];
-                                mac128(lo[0][j], hi[0][j], xv, __ldg(brow + q));
-                                mac128(lo[1][j], hi[1][j], xv, __ldg(brow + N + q));
+                                const u64 *brow = bsk_c0 + (size_t)cc * 2 * N + q;
+                                kara(xv, __ldg(brow), kh[0], kl[0], km[0]);
+                                kara(xv, __ldg(brow + N), kh[1], kl[1], km[1]);
+                                if (fold_each) fold(j, kh, kl, km);
                             }
+                            fold(j, kh, kl, km);
                         }
                     }
                 }
@@ -276,7 +303,7 @@ __global__ void __launch_bounds__(brk::Cfg<LOGN>::kThreads, brk::Cfg<LOGN>::kBlo
                 }
             }
             __syncthreads();
-            ntr::inv_from_smem<LOGN>(x, in, sw, l, active, itwp, Q);
+            ntr::inv_from_smem<LOGN, QLOW1>(x, in, sw, l, active, itwp, Q);
             if (active) {
                 const size_t base = (size_t)u * N;
 #pragma unroll
@@ -492,33 +519,48 @@ bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t
     return BM_OK;
 }
 
-template <int LOGN, bool LAZY, bool SMALL0>
+template <int LOGN, bool LAZY, bool SMALL0, bool QLOW1>
 bm_status launch_br_v(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 steps, const uint64_t *ct_in,
-                      const uint32_t *lut, u64 *ws_acc, u32 *status, cudaStream_t st) {
+                      const uint32_t *lut, u64 *ws_acc, u32 *status, u32 lbits, bool fold_each,
+                      cudaStream_t st) {
     using C = brk::Cfg<LOGN>;
     const size_t smem = C::SMEM;
-    auto kern = k_blind_rotate<LOGN, LAZY, SMALL0>;
+    auto kern = k_blind_rotate<LOGN, LAZY, SMALL0, QLOW1>;
     BM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<cnt, C::kThreads, smem, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc, status);
+    kern<<<cnt, C::kThreads, smem, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc, status, lbits, fold_each);
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
 }
 
-// The correction-free forward transform needs (1 + 4 log2 N) Q < 2^64; its
-// exact first stage additionally needs B + Q B + 4 Q (log2 N - 1) < 2^64.
+// Variant choice for one key set:
+//  - the correction-free forward transform needs (1 + 4 log2 N) Q < 2^64, its
+//    exact first stage B + Q B + 4 Q (log2 N - 1) < 2^64;
+//  - Q = c 2^32 + 1 selects the one-multiply q Q;
+//  - the Karatsuba limbs have lbits = ceil(bits(Q - 1) / 2) bits; a batch's P
+//    limb products fit 64 bits when P (2^(lbits+1) - 1)^2 < 2^64, otherwise
+//    they are folded after every combo.
 template <int LOGN>
 bm_status launch_br(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 steps, const uint64_t *ct_in,
                     const uint32_t *lut, u64 *ws_acc, u32 *status, u64 Q, u32 log2B, cudaStream_t st) {
     typedef unsigned __int128 u128;
+    using C = brk::Cfg<LOGN>;
     const u128 lim = (u128)1 << 64;
-    const u128 lazy = (u128)(1 + 4 * LOGN) * Q;
+    const bool lazy = (u128)(1 + 4 * LOGN) * Q < lim;
     const u128 B = (u128)1 << log2B;
-    const u128 small0 = B + (u128)Q * B + (u128)4 * Q * (LOGN - 1);
-    if (lazy < lim && small0 < lim && log2B <= 31)
-        return launch_br_v<LOGN, true, true>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, st);
-    if (lazy < lim)
-        return launch_br_v<LOGN, true, false>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, st);
-    return launch_br_v<LOGN, false, false>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, st);
+    const bool small0 = lazy && log2B <= 31 && B + (u128)Q * B + (u128)4 * Q * (LOGN - 1) < lim;
+    const bool qlow1 = (Q & 0xffffffffull) == 1;
+    u32 qbits = 0;
+    while (qbits < 64 && ((Q - 1) >> qbits)) qbits++;
+    const u32 lbits = (qbits + 1) / 2;
+    const u128 limb = ((u128)1 << (lbits + 1)) - 1;
+    const bool fold_each = (u128)C::P * limb * limb >= lim;
+#define BM_LAUNCH(LZ, S0, QL) \
+    return launch_br_v<LOGN, LZ, S0, QL>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, lbits, fold_each, st)
+    if (small0 && qlow1) BM_LAUNCH(true, true, true);
+    if (small0) BM_LAUNCH(true, true, false);
+    if (qlow1) BM_LAUNCH(false, false, true);
+    BM_LAUNCH(false, false, false);
+#undef BM_LAUNCH
 }
 
 // Launches blind rotation for every job; jobs are grouped by ring degree

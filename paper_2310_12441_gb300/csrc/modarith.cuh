@@ -50,6 +50,33 @@ __device__ __forceinline__ u64 mul_shoup_q3_lazy(u64 a, u64 w, u64 wsh, u64 Q) {
     return a * w - q * Q;
 }
 
+// q * Q mod 2^64; when Q = c 2^32 + 1 (QLOW1), q Q = q + (q mod 2^32) c 2^32
+// modulo 2^64, one 32-bit multiply.
+template <bool QLOW1>
+__device__ __forceinline__ u64 times_q(u64 q, u64 Q) {
+    if constexpr (QLOW1) {
+        return q + ((u64)((u32)q * (u32)(Q >> 32)) << 32);
+    } else {
+        return q * Q;
+    }
+}
+
+// Three-product Shoup (see mul_shoup_q3) without the final correction, for
+// either kind of modulus: result in [0, 4Q).
+template <bool QLOW1>
+__device__ __forceinline__ u64 shoup3_lazy(u64 a, u64 w, u64 wsh, u64 Q) {
+    const u32 a0 = (u32)a, a1 = (u32)(a >> 32);
+    const u32 s0 = (u32)wsh, s1 = (u32)(wsh >> 32);
+    const u64 q = (u64)a1 * s1 + __umulhi(a1, s0) + __umulhi(a0, s1);
+    return a * w - times_q<QLOW1>(q, Q);
+}
+
+template <bool QLOW1>
+__device__ __forceinline__ u64 shoup3(u64 a, u64 w, u64 wsh, u64 Q, u64 twoQ) {
+    const u64 r = shoup3_lazy<QLOW1>(a, w, wsh, Q);
+    return r >= twoQ ? r - twoQ : r;
+}
+
 __device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 wsh, u64 Q) {
     return reduce_2q(mul_shoup_lazy(a, w, wsh, Q), Q);
 }
@@ -77,6 +104,12 @@ __device__ __forceinline__ void add128(u64 &lo, u64 &hi, u64 a) {
         "addc.u64 %1, %1, 0;"
         : "+l"(lo), "+l"(hi)
         : "l"(a));
+}
+
+// (hi:lo) += v << sh for 0 < sh < 64.
+__device__ __forceinline__ void add128_shl(u64 &lo, u64 &hi, u64 v, u32 sh) {
+    add128(lo, hi, v << sh);
+    hi += v >> (64 - sh);
 }
 
 // (hi 2^64 + lo) mod Q, any hi, lo < 2^64:  hi * (2^64 mod Q) + lo, each term

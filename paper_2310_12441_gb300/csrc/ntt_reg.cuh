@@ -19,7 +19,7 @@
 // Butterflies are Harvey's lazy ones (D. Harvey, "Faster arithmetic for
 // number-theoretic transforms", J. Symb. Comp. 2014): forward values stay in
 // [0, 4Q), inverse values in [0, 2Q); twiddle products use the three-product
-// Shoup quotient of modarith.cuh.  Twiddles come as (w, w') pairs.
+// Shoup quotient of modarith.cuh (with a one-multiply q Q when Q = c 2^32 + 1).  Twiddles come as (w, w') pairs.
 //
 // Shared memory: every polynomial owns two regions of N words and the
 // exchanges alternate between them (Swap), so a region is never rewritten
@@ -65,7 +65,7 @@ __device__ __forceinline__ void twiddle(const u64 *__restrict__ tp, u32 ti, u64 
 // W * Y is formed exactly (a 64 x 32-bit product) and left unreduced:
 // X + W Y and X - W Y + Q B, both below B + Q B.  The caller guarantees
 // B + Q B + 4 Q (LOGN - 1) < 2^64.
-template <int LOGN, int F, int S0, int NST, bool LAZY, bool SMALL0 = false>
+template <int LOGN, int F, int S0, int NST, bool LAZY, bool SMALL0 = false, bool QLOW1 = false>
 __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__restrict__ twp, u64 Q,
                                           u64 twoQ, u64 qb = 0) {
     const u32 high = l >> F;
@@ -92,13 +92,13 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__rest
             }
             if constexpr (LAZY) {
                 const u64 X = x[i];
-                const u64 T = mul_shoup_q3_lazy(x[i2], W, Wsh, Q);
+                const u64 T = shoup3_lazy<QLOW1>(x[i2], W, Wsh, Q);
                 x[i] = X + T;
                 x[i2] = X - T + 2 * twoQ;
             } else {
                 u64 X = x[i];
                 X = X >= twoQ ? X - twoQ : X;
-                const u64 T = mul_shoup_q3(x[i2], W, Wsh, Q, twoQ);
+                const u64 T = shoup3<QLOW1>(x[i2], W, Wsh, Q, twoQ);
                 x[i] = X + T;
                 x[i2] = X - T + twoQ;
             }
@@ -107,7 +107,7 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__rest
 }
 
 // Inverse phase: NST stages acting on bits SB, SB+1, ..., field [F, F+4).
-template <int LOGN, int F, int SB, int NST>
+template <int LOGN, int F, int SB, int NST, bool QLOW1 = false>
 __device__ __forceinline__ void inv_phase(u64 (&x)[16], u32 l, const u64 *__restrict__ itwp, u64 Q,
                                           u64 twoQ) {
     const u32 high = l >> F;
@@ -126,7 +126,7 @@ __device__ __forceinline__ void inv_phase(u64 (&x)[16], u32 l, const u64 *__rest
             u64 u = U + V;
             u = u >= twoQ ? u - twoQ : u;
             x[i] = u;
-            x[i2] = mul_shoup_q3(U - V + twoQ, W, Wsh, Q, twoQ);
+            x[i2] = shoup3<QLOW1>(U - V + twoQ, W, Wsh, Q, twoQ);
         }
     }
 }
@@ -149,20 +149,20 @@ __device__ __forceinline__ void load_field(u64 (&x)[16], const u64 *reg, u32 l) 
 // (swizzled); the caller must __syncthreads() before reading it.  Every
 // thread of the block calls this (it contains barriers); threads with
 // active == false only take part in the barriers.
-template <int LOGN, bool LAZY, bool SMALL0 = false>
+template <int LOGN, bool LAZY, bool SMALL0 = false, bool QLOW1 = false>
 __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool active,
                                             const u64 *__restrict__ twp, u64 Q, u64 one_sh, u64 qb = 0) {
     constexpr int NPH = (LOGN + 3) / 4;
     static_assert(LOGN >= 8 && LOGN <= 12, "ring degree 256..4096");
     const u64 twoQ = 2 * Q;
-    if (active) fwd_phase<LOGN, LOGN - 4, 0, 4, LAZY, SMALL0>(x, l, twp, Q, twoQ, qb);
+    if (active) fwd_phase<LOGN, LOGN - 4, 0, 4, LAZY, SMALL0, QLOW1>(x, l, twp, Q, twoQ, qb);
     u64 *r = sw.take();
     if (active) store_field<LOGN - 4>(x, r, l);
     __syncthreads();
     if constexpr (NPH == 3) {
         if (active) {
             load_field<LOGN - 8>(x, r, l);
-            fwd_phase<LOGN, LOGN - 8, 4, 4, LAZY>(x, l, twp, Q, twoQ);
+            fwd_phase<LOGN, LOGN - 8, 4, 4, LAZY, false, QLOW1>(x, l, twp, Q, twoQ);
         }
         r = sw.take();
         if (active) store_field<LOGN - 8>(x, r, l);
@@ -170,7 +170,7 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
     }
     if (active) {
         load_field<0>(x, r, l);
-        fwd_phase<LOGN, 0, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), LAZY>(x, l, twp, Q, twoQ);
+        fwd_phase<LOGN, 0, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), LAZY, false, QLOW1>(x, l, twp, Q, twoQ);
 #pragma unroll
         for (int i = 0; i < 16; i++) {
             u64 v = x[i];
@@ -191,14 +191,14 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
 // transform (swizzled, values below 2Q) and the block has passed a barrier
 // since it was written; `in` must be the region sw wrote last.  On exit x
 // holds natural-order coefficients l + T i, reduced to [0, Q).
-template <int LOGN>
+template <int LOGN, bool QLOW1 = false>
 __device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap &sw, u32 l, bool active,
                                               const u64 *__restrict__ itwp, u64 Q) {
     constexpr int NPH = (LOGN + 3) / 4;
     const u64 twoQ = 2 * Q;
     if (active) {
         load_field<0>(x, in, l);
-        inv_phase<LOGN, 0, 0, 4>(x, l, itwp, Q, twoQ);
+        inv_phase<LOGN, 0, 0, 4, QLOW1>(x, l, itwp, Q, twoQ);
     }
     u64 *r = sw.take();
     if (active) store_field<0>(x, r, l);
@@ -206,7 +206,7 @@ __device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap 
     if constexpr (NPH == 3) {
         if (active) {
             load_field<4>(x, r, l);
-            inv_phase<LOGN, 4, 4, 4>(x, l, itwp, Q, twoQ);
+            inv_phase<LOGN, 4, 4, 4, QLOW1>(x, l, itwp, Q, twoQ);
         }
         r = sw.take();
         if (active) store_field<4>(x, r, l);
@@ -214,7 +214,7 @@ __device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap 
     }
     if (active) {
         load_field<LOGN - 4>(x, r, l);
-        inv_phase<LOGN, LOGN - 4, 4 * (NPH - 1), LOGN - 4 * (NPH - 1)>(x, l, itwp, Q, twoQ);
+        inv_phase<LOGN, LOGN - 4, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), QLOW1>(x, l, itwp, Q, twoQ);
 #pragma unroll
         for (int i = 0; i < 16; i++) x[i] = x[i] >= Q ? x[i] - Q : x[i];
     }

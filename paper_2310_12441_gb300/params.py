@@ -8,8 +8,11 @@ number m of polynomials in the test vector nor on the plaintext modulus t
 with the same N.  A *job shape* is (m, t); the input ciphertext modulus is
 q' = 2*N*m (Algorithm 1, modulus switch), so Delta = q'/t.
 
-All moduli Q below are the largest primes under 2^k with Q = 1 mod 2N
-(needed for a negacyclic NTT of length N).
+Moduli: Q is prime with Q = 1 mod 2N (a negacyclic NTT of length N exists).
+Above 2^32 we take the largest prime below 2^k of the form c 2^32 + 1: then
+q Q mod 2^64 = q + ((q mod 2^32) c mod 2^32) 2^32, which saves multiplies in
+every modular reduction of the NTT.  The toy modulus lies below 2^32 and is
+the largest prime below 2^30 that is 1 mod 512.
 """
 from __future__ import annotations
 
@@ -78,11 +81,11 @@ class Workload:
 # Key sets -----------------------------------------------------------------
 KEYS_TOY = KeyParams(n=64, N=256, Q=1073738753, log2_B=6, l_B=5,
                      log2_Bks=4, l_ks=7, secret="binary")
-KEYS_N1024 = KeyParams(n=630, N=1024, Q=18014398509404161, log2_B=9, l_B=6,
+KEYS_N1024 = KeyParams(n=630, N=1024, Q=18014359854776321, log2_B=9, l_B=6,
                        log2_Bks=4, l_ks=7)
-KEYS_N4096 = KeyParams(n=630, N=4096, Q=18014398509309953, log2_B=9, l_B=6,
+KEYS_N4096 = KeyParams(n=630, N=4096, Q=18014359854776321, log2_B=9, l_B=6,
                        log2_Bks=4, l_ks=7)
-KEYS_N2048 = KeyParams(n=750, N=2048, Q=1152921504606830593, log2_B=10, l_B=6,
+KEYS_N2048 = KeyParams(n=750, N=2048, Q=1152921092289986561, log2_B=10, l_B=6,
                        log2_Bks=4, l_ks=7)
 
 # Workloads ------------------------------------------------------------------

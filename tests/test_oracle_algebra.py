@@ -268,3 +268,19 @@ def test_decompose(orc):
             d = orc.decompose(int(x), log2_B, l_B)
             assert all(int(dj) < (1 << log2_B) for dj in d)
             assert sum(int(dj) << (log2_B * j) for j, dj in enumerate(d)) == int(x)
+
+
+def test_workload_moduli():
+    """Every modulus is prime, 1 mod 2N, within its bound; above 2^32 it is
+    the largest such prime of the form c 2^32 + 1."""
+    import sympy
+    from paper_2310_12441_gb300 import params as P
+    for kp, bits in [(P.KEYS_TOY, 30), (P.KEYS_N1024, 54), (P.KEYS_N4096, 54), (P.KEYS_N2048, 60)]:
+        Q = kp.Q
+        assert sympy.isprime(Q) and (Q - 1) % (2 * kp.N) == 0 and Q < 1 << bits
+        kp.validate()
+        if bits > 32:
+            assert Q & 0xFFFFFFFF == 1
+            c = Q >> 32
+            for c2 in range(c + 1, ((1 << bits) - 1) >> 32):
+                assert not sympy.isprime((c2 << 32) + 1)
