@@ -190,6 +190,29 @@ bm_status bm_poly_mul(const bm_eval_key *key, const uint64_t *d_a,
                       const uint64_t *d_b, uint32_t count, uint64_t *d_out,
                       void *stream);
 
+/* Reusable batch (native executor around Algorithm 1): the job table is
+ * built, ordered and uploaded to the workspace once; every bm_batch_run then
+ * only launches kernels on the bound buffers.  Flags:
+ *   BM_BATCH_PERSISTENT  one persistent blind-rotation launch for all jobs of
+ *                        ring degree 1024..4096 (one 512-thread block per SM
+ *                        pulls jobs from a counter, longest first), so uneven
+ *                        mixes of key sets and shapes run as one launch;
+ *   BM_BATCH_GRAPH       the first run records the launches in a CUDA graph
+ *                        on `stream` (which must not be the legacy default
+ *                        stream) and later runs replay it.
+ * The buffers and the workspace stay bound to the batch until bm_batch_free;
+ * runs of one batch must not overlap on the GPU (they share the workspace). */
+typedef struct bm_batch bm_batch;
+#define BM_BATCH_PERSISTENT 1u
+#define BM_BATCH_GRAPH 2u
+bm_status bm_batch_create(const bm_eval_key *const *keys, uint32_t n_keys,
+                          const bm_job *jobs, uint32_t count,
+                          const uint64_t *d_ct_in, const uint32_t *d_lut,
+                          uint64_t *d_ct_out, void *d_ws, size_t ws_bytes,
+                          uint32_t flags, bm_batch **out);
+bm_status bm_batch_run(bm_batch *batch, void *stream);
+void bm_batch_free(bm_batch *batch);
+
 /* Reads (synchronising `stream`) and clears the device status word of a
  * workspace: BM_OK or the first device-side error recorded. */
 bm_status bm_workspace_status(void *d_ws, void *stream);

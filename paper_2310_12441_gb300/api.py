@@ -26,7 +26,11 @@ SYMBOLS = ["bm_keygen", "bm_free_secret_key", "bm_free_eval_key", "bm_eval_key_b
            "bm_encrypt", "bm_decrypt", "bm_workspace_bytes", "bm_bootstrap_batch",
            "bm_host_staging_bytes", "bm_bootstrap_batch_host", "bm_blind_rotate",
            "bm_sample_extract", "bm_key_switch", "bm_poly_mul", "bm_workspace_status",
-           "bm_modmul_peak", "bm_status_str", "bm_bootstrap_batch_noalloc"]
+           "bm_modmul_peak", "bm_status_str", "bm_bootstrap_batch_noalloc",
+           "bm_batch_create", "bm_batch_run", "bm_batch_free"]
+
+BATCH_PERSISTENT = 1
+BATCH_GRAPH = 2
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -103,6 +107,11 @@ def load(build_if_needed: bool = True) -> C.CDLL:
     L.bm_modmul_peak.restype = i32
     L.bm_bootstrap_batch_noalloc.argtypes = [vp, u32, vp, u32, vp, vp, vp, vp, vp]
     L.bm_bootstrap_batch_noalloc.restype = i32
+    L.bm_batch_create.argtypes = [vp, u32, vp, u32, vp, vp, vp, vp, sz, u32, C.POINTER(vp)]
+    L.bm_batch_create.restype = i32
+    L.bm_batch_run.argtypes = [vp, vp]
+    L.bm_batch_run.restype = i32
+    L.bm_batch_free.argtypes = [vp]
     L.bm_status_str.argtypes = [i32]
     L.bm_status_str.restype = C.c_char_p
     _lib = L
@@ -238,6 +247,32 @@ def bm_bootstrap_batch_noalloc(keys, jobs: np.ndarray, d_ct_in, d_lut, d_ct_out,
                                              _ptr(d_lut), _ptr(d_ct_out),
                                              None if d_status is None else _ptr(d_status),
                                              _stream(stream)), "bm_bootstrap_batch_noalloc")
+
+
+class Batch:
+    """A reusable batch (bm_batch_create): buffers stay bound until free()."""
+
+    def __init__(self, keys, jobs: np.ndarray, d_ct_in, d_lut, d_ct_out, d_ws, flags: int = 0):
+        karr, nk = _keys(keys)
+        self._keys = keys          # keep the key handles alive
+        self._bufs = (d_ct_in, d_lut, d_ct_out, d_ws)
+        jobs = np.ascontiguousarray(jobs, JOB_DTYPE)
+        h = C.c_void_p()
+        _check(load().bm_batch_create(karr, nk, _ptr(jobs), len(jobs), _ptr(d_ct_in), _ptr(d_lut),
+                                      _ptr(d_ct_out), _ptr(d_ws), d_ws.numel() * d_ws.element_size(),
+                                      flags, C.byref(h)), "bm_batch_create")
+        self.handle = h.value
+
+    def run(self, stream=None):
+        _check(load().bm_batch_run(self.handle, _stream(stream)), "bm_batch_run")
+
+    def free(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bm_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.free()
 
 
 def bm_bootstrap_batch_host(keys, jobs: np.ndarray, h_ct_in, h_lut, h_ct_out, d_ws, stream=None):

@@ -14,6 +14,8 @@
 //      registers (Section 2 item (14), summed over both CMux terms);
 //   4. reduces, inverse-transforms (N^-1 is folded into the key) and adds
 //      the result to row r of ACC.
+#include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -22,303 +24,7 @@
 #include "ntt.cuh"
 #include "ntt_reg.cuh"
 
-// ---------------------------------------------------------------------------
-// Device helpers
-// ---------------------------------------------------------------------------
-
-// Coefficient `c` of x^e * p in R_{N,Q}, e in [0, 2N).
-__device__ __forceinline__ u64 rotated_coeff(const u64 *p, u32 c, u32 e, u32 N, u64 Q) {
-    u32 j = c + 2 * N - e;
-    if (j >= 2 * N) j -= 2 * N;
-    if (j < N) return p[j];
-    const u64 v = p[j - N];
-    return v ? Q - v : 0;
-}
-
-__device__ __forceinline__ void set_status(u32 *status, bm_status code) {
-    atomicCAS(status, 0u, (u32)(-code));
-}
-
-// Negacyclic table check: entries in [0, t) and f(k + t/2) = -f(k) mod t.
-__device__ bool lut_is_negacyclic(const u32 *__restrict__ lut, u32 t) {
-    __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
-    for (u32 k = threadIdx.x; k < t / 2; k += blockDim.x) {
-        const u32 a = lut[k], b = lut[k + t / 2];
-        if (a >= t || b >= t || b != (t - a) % t) bad = 1;
-    }
-    __syncthreads();
-    const bool ok = bad == 0;
-    __syncthreads();
-    return ok;
-}
-
-// ACC <- P(b) (0, v_test floor(Q/t)), v_test of Eq. (equ:test-use):
-// row i, coefficient a of v_test is f'(-(a m + i) mod 2Nm), with the
-// negacyclic extension f'(u) = f(floor((u t + Nm) / 2Nm) mod t).
-__device__ void acc_init(u64 *__restrict__ acc, const u32 *__restrict__ lut, u64 b, u32 m, u32 t,
-                         u32 N, u64 Q) {
-    const u64 qp = 2ull * N * m;
-    const u64 dq = Q / t;
-    const u32 ea = (u32)(b / m), bb = (u32)(b % m);
-    for (u32 idx = threadIdx.x; idx < m * 2 * N; idx += blockDim.x) {
-        const u32 c = idx % N;
-        const u32 comp = (idx / N) & 1;
-        const u32 i = idx / (2 * N);
-        u64 val = 0;
-        if (comp == 1) {
-            const u32 src = i >= bb ? i - bb : i + m - bb;
-            u32 e = i >= bb ? ea : ea + 1;
-            if (e >= 2 * N) e -= 2 * N;
-            u32 j = c + 2 * N - e;
-            if (j >= 2 * N) j -= 2 * N;
-            const bool neg = j >= N;
-            if (neg) j -= N;
-            const u64 w = ((u64)j * m + src) % qp;
-            const u64 u = (qp - w) % qp;
-            const u32 fi = (u32)(((u * t + qp / 2) / qp) % t);
-            const u64 v = (u64)lut[fi] * dq;     // < t * floor(Q/t) <= Q
-            val = neg ? (v ? Q - v : 0) : v;
-        }
-        acc[idx] = val;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Blind rotation kernel: one job per block of 512 threads.
-//
-// A CMux step handles the m rows one after another.  For row r the 4 l_B
-// digit polynomials ("combos": sign x component x digit) are transformed P at
-// a time (P = 512 / (N/16) polynomials per batch, each by N/16 threads holding
-// 16 coefficients in registers).  The transforms land in shared memory; every
-// thread then multiplies the positions it owns (q = tid + 512 j) with the key
-// rows of the batch's combos and accumulates exactly in 128-bit registers, so
-// the whole row needs a single reduction per position and column.  The
-// reduced row sums go to the job's sum buffer; after the last row, the 2m
-// sums are inverse-transformed (P per batch) and added to the rows of the
-// next ACC buffer.
-// ---------------------------------------------------------------------------
-namespace brk {
-// Up to N = 1024 two blocks of 256 threads share an SM (two jobs whose
-// barriers and memory phases overlap each other's arithmetic); larger rings
-// use one block of 512 threads.
-template <int LOGN>
-struct Cfg {
-    static constexpr int kThreads = LOGN <= 10 ? 256 : 512;
-    static constexpr int kBlocksPerSM = 512 / kThreads;
-    static constexpr int N = 1 << LOGN;
-    static constexpr int T = N / 16;                               // threads per polynomial
-    static constexpr int P = kThreads / T;                         // polynomials per batch
-    static constexpr int PPT = N >= kThreads ? N / kThreads : 1;   // positions per thread
-    static constexpr bool DSM = LOGN <= 11;                        // row differences in smem
-    static constexpr size_t SMEM = 2ull * P * N * 8 + (DSM ? 4ull * N * 8 : 0);
-};
-}  // namespace brk
-
-template <int LOGN, bool LAZY, bool SMALL0, bool QLOW1>
-__global__ void __launch_bounds__(brk::Cfg<LOGN>::kThreads, brk::Cfg<LOGN>::kBlocksPerSM)
-    k_blind_rotate(const DevJob *__restrict__ jobs, u32 steps_limit, const u64 *__restrict__ ct_in,
-                   const u32 *__restrict__ luts, u64 *ws, u32 *status, u32 lbits, bool fold_each) {
-    using C = brk::Cfg<LOGN>;
-    constexpr int N = C::N;
-    extern __shared__ u64 sm[];
-    const DevJob J = jobs[blockIdx.x];
-    const KeyDev *K = J.key;
-    const u32 m = J.m, t = J.t, lB = K->l_B, log2B = K->log2_B, n = K->n;
-    const ModQ mq = K->mq;
-    const u64 Q = mq.Q;
-    const u64 qp = 2ull * N * m;
-    const u64 Bmask = (1ull << log2B) - 1;
-    const u64 *twp = K->twp, *itwp = K->itwp;
-    const u32 tid = threadIdx.x;
-    const size_t vec = (size_t)m * 2 * N;
-    u64 *acc0 = ws + J.acc_off;
-    u64 *acc1 = acc0 + vec;
-    u64 *sums = acc1 + vec;
-    const u64 *ct = ct_in + J.in_off;
-    const u32 *lut = luts + J.lut_off;
-
-    if (!lut_is_negacyclic(lut, t)) {
-        if (tid == 0) set_status(status, BM_ENONNEGACYCLIC);
-        for (u32 idx = tid; idx < 2 * vec; idx += blockDim.x) acc0[idx] = 0;
-        return;
-    }
-    acc_init(acc0, lut, ct[n] % qp, m, t, N, Q);
-    __syncthreads();
-
-    const u32 p = tid / C::T;          // polynomial slot within a batch
-    const u32 l = tid % C::T;          // thread within the polynomial
-    ntr::Swap sw{sm + (size_t)p * N, sm + (size_t)(C::P + p) * N, 0};
-    u64 *dbuf = sm + (size_t)2 * C::P * N;   // [4][N] row differences (DSM only)
-    const u64 qb = Q << log2B;                 // Q * B, used when SMALL0
-    const u64 lmask = (1ull << lbits) - 1;     // Karatsuba limb mask
-    const u32 ncomb = 4 * lB;
-    const size_t rgsw = (size_t)2 * lB * 2 * N;
-
-    u64 *cur = acc0, *nxt = acc1;
-    const u32 steps = steps_limit < n ? steps_limit : n;
-    for (u32 k = 0; k < steps; k++) {
-        const u64 ak = ct[k] % qp;
-        const u64 *bsk_k = K->bsk + (size_t)k * 2 * rgsw;
-        for (u32 r = 0; r < m; r++) {
-            u64 lo[2][C::PPT], hi[2][C::PPT];
-#pragma unroll
-            for (int j = 0; j < C::PPT; j++) lo[0][j] = hi[0][j] = lo[1][j] = hi[1][j] = 0;
-            if constexpr (C::DSM) {
-                // D_(sign, comp) = P(c) ACC - ACC for row r, c = -a_k / a_k
-                for (u32 w = tid; w < 4u * N; w += C::kThreads) {
-                    const u32 pair = w / N, idx = w % N;
-                    const u32 sgn = pair >> 1, comp = pair & 1;
-                    const u64 cv = sgn == 0 ? (qp - ak) % qp : ak;
-                    const u32 ea = (u32)(cv / m), bb = (u32)(cv % m);
-                    const u32 src = r >= bb ? r - bb : r + m - bb;
-                    u32 e = r >= bb ? ea : ea + 1;
-                    if (e >= 2 * N) e -= 2 * N;
-                    const u64 *srow = cur + ((size_t)src * 2 + comp) * N;
-                    const u64 *orow = cur + ((size_t)r * 2 + comp) * N;
-                    dbuf[w] = sub_mod(rotated_coeff(srow, idx, e, N, Q), orow[idx], Q);
-                }
-                __syncthreads();
-            }
-            for (u32 c0 = 0; c0 < ncomb; c0 += C::P) {
-                // --- this thread's digit polynomial, transformed into shared memory
-                const u32 c = c0 + p;
-                const bool active = c < ncomb;
-                u64 x[16];
-                if (active && C::DSM) {
-                    const u32 pair = c / lB, sh = (c % lB) * log2B;
-                    const u64 *dp = dbuf + (size_t)pair * N;
-#pragma unroll
-                    for (int i = 0; i < 16; i++) x[i] = (dp[l + C::T * i] >> sh) & Bmask;
-                } else if (active) {
-                    const u32 sgn = c / (2 * lB), comp = (c / lB) & 1, d = c % lB;
-                    const u64 cv = sgn == 0 ? (qp - ak) % qp : ak;
-                    const u32 ea = (u32)(cv / m), bb = (u32)(cv % m);
-                    const u32 src = r >= bb ? r - bb : r + m - bb;
-                    u32 e = r >= bb ? ea : ea + 1;
-                    if (e >= 2 * N) e -= 2 * N;
-                    const u64 *srow = cur + ((size_t)src * 2 + comp) * N;
-                    const u64 *orow = cur + ((size_t)r * 2 + comp) * N;
-                    const u32 sh = d * log2B;
-#pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        const u32 idx = l + C::T * i;
-                        const u64 D = sub_mod(rotated_coeff(srow, idx, e, N, Q), orow[idx], Q);
-                        x[i] = (D >> sh) & Bmask;
-                    }
-                }
-                u64 *out = ntr::fwd_to_smem<LOGN, LAZY, SMALL0, QLOW1>(x, sw, l, active, twp, Q, mq.one_sh, qb);
-                // regions of the other polynomials of the batch sit at stride N
-                const u64 *slots = out - (size_t)p * N;
-                __syncthreads();
-                // --- multiply-accumulate against the key rows of the batch's combos
-                // (combo c = (sign, component, digit) is key row c of the step).
-                // Karatsuba on half-width limbs x = x1 2^lbits + x0: the limb
-                // products x1 b1, x0 b0 and (x0 + x1)(b0 + b1) are summed over
-                // the batch in 64-bit registers, then folded into the 128-bit
-                // row sums as hi 2^(2 lbits) + (mid - hi - lo) 2^lbits + lo.
-                const u64 *bsk_c0 = bsk_k + (size_t)c0 * 2 * N;
-                const u32 nc = ncomb - c0 < (u32)C::P ? ncomb - c0 : (u32)C::P;
-                auto fold = [&](int j, u64 (&kh)[2], u64 (&kl)[2], u64 (&km)[2]) {
-#pragma unroll
-                    for (int col = 0; col < 2; col++) {
-                        add128(lo[col][j], hi[col][j], kl[col]);
-                        add128_shl(lo[col][j], hi[col][j], km[col] - kh[col] - kl[col], lbits);
-                        add128_shl(lo[col][j], hi[col][j], kh[col], 2 * lbits);
-                        kh[col] = kl[col] = km[col] = 0;
-                    }
-                };
-                auto kara = [&](u64 xv, u64 bv, u64 &kh, u64 &kl, u64 &km) {
-                    const u32 x0 = (u32)(xv & lmask), x1 = (u32)(xv >> lbits);
-                    const u32 b0 = (u32)(bv & lmask), b1 = (u32)(bv >> lbits);
-                    kh += (u64)x1 * b1;
-                    kl += (u64)x0 * b0;
-                    km += (u64)(x0 + x1) * (b0 + b1);
-                };
-                if (nc == (u32)C::P && !fold_each) {
-                    // full batch: every key word of a position is requested first
-#pragma unroll
-                    for (int j = 0; j < C::PPT; j++) {
-                        const u32 q = tid + C::kThreads * j;
-                        if (q < (u32)N) {
-                            const u32 sq = ntr::swz(q);
-                            u64 bv[C::P][2];
-#pragma unroll
-                            for (int cc = 0; cc < C::P; cc++) {
-                                bv[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q);
-                                bv[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q);
-                            }
-                            u64 kh[2] = {0, 0}, kl[2] = {0, 0}, km[2] = {0, 0};
-#pragma unroll
-                            for (int cc = 0; cc < C::P; cc++) {
-                                const u64 xv = slots[(size_t)cc * N + sq];
-                                kara(xv, bv[cc][0], kh[0], kl[0], km[0]);
-                                kara(xv, bv[cc][1], kh[1], kl[1], km[1]);
-                            }
-                            fold(j, kh, kl, km);
-                        }
-                    }
-                } else {
-                    for (int j = 0; j < C::PPT; j++) {
-                        const u32 q = tid + C::kThreads * j;
-                        if (q < (u32)N) {
-                            const u32 sq = ntr::swz(q);
-                            u64 kh[2] = {0, 0}, kl[2] = {0, 0}, km[2] = {0, 0};
-                            for (u32 cc = 0; cc < nc; cc++) {
-                                const u64 xv = slots[(size_t)cc * N + sq];
-                                const u64 *brow = bsk_c0 + (size_t)cc * 2 * N + q;
-                                kara(xv, __ldg(brow), kh[0], kl[0], km[0]);
-                                kara(xv, __ldg(brow + N), kh[1], kl[1], km[1]);
-                                if (fold_each) fold(j, kh, kl, km);
-                            }
-                            fold(j, kh, kl, km);
-                        }
-                    }
-                }
-            }
-            // --- reduced row sums (NTT domain) to the sum buffer
-#pragma unroll
-            for (int j = 0; j < C::PPT; j++) {
-                const u32 q = tid + C::kThreads * j;
-                if (q < (u32)N) {
-                    sums[((size_t)r * 2) * N + q] = reduce128(lo[0][j], hi[0][j], mq);
-                    sums[((size_t)r * 2 + 1) * N + q] = reduce128(lo[1][j], hi[1][j], mq);
-                }
-            }
-        }
-        __syncthreads();
-        // --- inverse transforms of the 2m row sums, ACC update
-        for (u32 u0 = 0; u0 < 2 * m; u0 += C::P) {
-            const u32 u = u0 + p;
-            const bool active = u < 2 * m;
-            u64 x[16];
-            u64 *in = sw.take();
-            if (active) {
-                const u64 *sp = sums + (size_t)u * N;
-#pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const u32 idx = l + C::T * i;
-                    in[ntr::swz(idx)] = sp[idx];
-                }
-            }
-            __syncthreads();
-            ntr::inv_from_smem<LOGN, QLOW1>(x, in, sw, l, active, itwp, Q);
-            if (active) {
-                const size_t base = (size_t)u * N;
-#pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const size_t o = base + l + C::T * i;
-                    nxt[o] = add_mod(cur[o], x[i], Q);
-                }
-            }
-        }
-        __syncthreads();
-        u64 *tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-    }
-}
+#include "blind_rotate.cuh"
 
 // ---------------------------------------------------------------------------
 // Sample extraction + key switching
@@ -495,7 +201,41 @@ bm_status validate_jobs(const bm_eval_key *const *keys, uint32_t n_keys, const b
     return BM_OK;
 }
 
-bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t count, Plan &pl) {
+// Arithmetic variant of a key set (BR_V_* flags):
+//  - BR_V_LAZY: the correction-free forward transform needs
+//    (1 + 4 log2 N) Q < 2^64 and its exact first stage
+//    B + Q B + 4 Q (log2 N - 1) < 2^64 with B < 2^32;
+//  - BR_V_QLOW1: Q = c 2^32 + 1.
+u32 choose_variant(const bm_key_params &p) {
+    typedef unsigned __int128 u128;
+    u32 logN = 0;
+    while ((1u << logN) < p.N) logN++;
+    const u128 lim = (u128)1 << 64, Q = p.Q, B = (u128)1 << p.log2_B;
+    u32 v = 0;
+    if ((1 + 4 * (u128)logN) * Q < lim && p.log2_B <= 31 && B + Q * B + 4 * Q * (logN - 1) < lim)
+        v |= BR_V_LAZY;
+    if ((p.Q & 0xffffffffull) == 1) v |= BR_V_QLOW1;
+    return v;
+}
+
+u32 limb_bits(u64 Q) {
+    u32 bits = 0;
+    while (bits < 64 && ((Q - 1) >> bits)) bits++;
+    return (bits + 1) / 2;
+}
+
+// Work of one job in butterfly units (n m N log2 N), for longest-first order.
+double job_cost(const DevJob &d) {
+    double lg = 0;
+    while ((1u << (u32)lg) < d.N) lg += 1;
+    return (double)d.n * d.m * d.N * lg;
+}
+
+// order_by_cost: the device job table lists the longest jobs first (the
+// persistent kernel then pulls them in that order); outputs still go to the
+// jobs' own offsets.
+bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t count, Plan &pl,
+                    bool order_by_cost = false) {
     pl.jobs_off = BM_WS_HEADER;
     size_t off = align_up(pl.jobs_off + sizeof(DevJob) * (size_t)count, 256);
     pl.acc_off_bytes = off;
@@ -513,86 +253,147 @@ bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t
         d.lut_off = jobs[i].lut_off;
         d.out_off = jobs[i].out_off;
         d.acc_off = acc_words;
+        d.variant = choose_variant(k->p);
+        d.lbits = limb_bits(k->p.Q);
         acc_words += 3ull * 2 * jobs[i].m * k->p.N;
     }
+    if (order_by_cost)
+        std::stable_sort(pl.dj.begin(), pl.dj.end(),
+                         [](const DevJob &a, const DevJob &b) { return job_cost(a) > job_cost(b); });
     pl.total = off + acc_words * 8;
     return BM_OK;
 }
 
+// One block per job.  Up to N = 1024 two blocks of 256 threads share an SM
+// (two jobs whose barriers and memory phases overlap each other's
+// arithmetic); larger rings use one block of 512 threads.
+template <int LOGN>
+constexpr int group_threads() { return LOGN <= 10 ? 256 : 512; }
+
+template <int LOGN, bool LAZY, bool SMALL0, bool QLOW1>
+__global__ void __launch_bounds__(group_threads<LOGN>(), 512 / group_threads<LOGN>())
+    k_blind_rotate(const DevJob *__restrict__ jobs, u32 steps_limit, const u64 *__restrict__ ct_in,
+                   const u32 *__restrict__ luts, u64 *ws, u32 *status) {
+    extern __shared__ u64 sm[];
+    brk::br_job<LOGN, group_threads<LOGN>(), LAZY, SMALL0, QLOW1>(jobs[blockIdx.x], steps_limit, ct_in, luts,
+                                                                   ws, status, sm);
+}
+
+// Sets the dynamic shared-memory limit of a kernel once per device.
+template <typename K>
+bm_status ensure_smem(K kern, size_t smem, std::atomic<uint64_t> &done) {
+    int dev = 0;
+    BM_CUDA_TRY(cudaGetDevice(&dev));
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(done.load() & bit)) {
+        BM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        done.fetch_or(bit);
+    }
+    return BM_OK;
+}
+
+// dry: only set the kernel's attributes (done before a CUDA-graph capture).
 template <int LOGN, bool LAZY, bool SMALL0, bool QLOW1>
 bm_status launch_br_v(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 steps, const uint64_t *ct_in,
-                      const uint32_t *lut, u64 *ws_acc, u32 *status, u32 lbits, bool fold_each,
-                      cudaStream_t st) {
-    using C = brk::Cfg<LOGN>;
-    const size_t smem = C::SMEM;
+                      const uint32_t *lut, u64 *ws_acc, u32 *status, cudaStream_t st, bool dry) {
+    using C = brk::Cfg<LOGN, group_threads<LOGN>()>;
+    static std::atomic<uint64_t> attr_done{0};
     auto kern = k_blind_rotate<LOGN, LAZY, SMALL0, QLOW1>;
-    BM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<cnt, C::kThreads, smem, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc, status, lbits, fold_each);
+    bm_status s = ensure_smem(kern, C::SMEM, attr_done);
+    if (s != BM_OK || dry) return s;
+    kern<<<cnt, C::kThreads, C::SMEM, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc, status);
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
 }
 
-// Variant choice for one key set:
-//  - the correction-free forward transform needs (1 + 4 log2 N) Q < 2^64, its
-//    exact first stage B + Q B + 4 Q (log2 N - 1) < 2^64;
-//  - Q = c 2^32 + 1 selects the one-multiply q Q;
-//  - the Karatsuba limbs have lbits = ceil(bits(Q - 1) / 2) bits; a batch's P
-//    limb products fit 64 bits when P (2^(lbits+1) - 1)^2 < 2^64, otherwise
-//    they are folded after every combo.
 template <int LOGN>
 bm_status launch_br(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 steps, const uint64_t *ct_in,
-                    const uint32_t *lut, u64 *ws_acc, u32 *status, u64 Q, u32 log2B, cudaStream_t st) {
-    typedef unsigned __int128 u128;
-    using C = brk::Cfg<LOGN>;
-    const u128 lim = (u128)1 << 64;
-    const bool lazy = (u128)(1 + 4 * LOGN) * Q < lim;
-    const u128 B = (u128)1 << log2B;
-    const bool small0 = lazy && log2B <= 31 && B + (u128)Q * B + (u128)4 * Q * (LOGN - 1) < lim;
-    const bool qlow1 = (Q & 0xffffffffull) == 1;
-    u32 qbits = 0;
-    while (qbits < 64 && ((Q - 1) >> qbits)) qbits++;
-    const u32 lbits = (qbits + 1) / 2;
-    const u128 limb = ((u128)1 << (lbits + 1)) - 1;
-    const bool fold_each = (u128)C::P * limb * limb >= lim;
+                    const uint32_t *lut, u64 *ws_acc, u32 *status, u32 variant, cudaStream_t st, bool dry) {
 #define BM_LAUNCH(LZ, S0, QL) \
-    return launch_br_v<LOGN, LZ, S0, QL>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, lbits, fold_each, st)
-    if (small0 && qlow1) BM_LAUNCH(true, true, true);
-    if (small0) BM_LAUNCH(true, true, false);
-    if (qlow1) BM_LAUNCH(false, false, true);
-    BM_LAUNCH(false, false, false);
+    return launch_br_v<LOGN, LZ, S0, QL>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, st, dry)
+    switch (variant) {
+        case BR_V_LAZY | BR_V_QLOW1: BM_LAUNCH(true, true, true);
+        case BR_V_LAZY: BM_LAUNCH(true, true, false);
+        case BR_V_QLOW1: BM_LAUNCH(false, false, true);
+        default: BM_LAUNCH(false, false, false);
+    }
 #undef BM_LAUNCH
 }
 
-// Launches blind rotation for every job; jobs are grouped by ring degree
-// (one launch per run of equal N in job order).
-bm_status run_blind_rotation(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t count,
-                             u32 steps, const Plan &pl, const uint64_t *d_ct_in, const uint32_t *d_lut,
-                             char *ws, cudaStream_t st) {
+// Blind rotation of jobs [first, last) of the plan, one block per job, one
+// launch per run of equal ring degree and variant.
+bm_status run_groups(const Plan &pl, uint32_t first, uint32_t last, u32 steps, const uint64_t *d_ct_in,
+                     const uint32_t *d_lut, char *ws, cudaStream_t st, bool dry) {
     const DevJob *d_jobs = (const DevJob *)(ws + pl.jobs_off);
     u64 *ws_acc = (u64 *)(ws + pl.acc_off_bytes);
     u32 *status = (u32 *)ws;
-    uint32_t i = 0;
-    while (i < count) {
-        const bm_eval_key *k = keys[jobs[i].key];
-        const u32 N = k->p.N;
+    uint32_t i = first;
+    while (i < last) {
+        const u32 N = pl.dj[i].N;
+        const u32 variant = pl.dj[i].variant;
         uint32_t j = i + 1;
-        const u64 Q = k->p.Q;
-        const u32 log2B = k->p.log2_B;
-        while (j < count && keys[jobs[j].key]->p.N == N && keys[jobs[j].key]->p.Q == Q &&
-               keys[jobs[j].key]->p.log2_B == log2B)
-            j++;
+        while (j < last && pl.dj[j].N == N && pl.dj[j].variant == variant) j++;
         bm_status s = BM_OK;
+#define BM_GRP(L) s = launch_br<L>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, variant, st, dry)
         switch (N) {
-            case 256: s = launch_br<8>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, log2B, st); break;
-            case 512: s = launch_br<9>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, log2B, st); break;
-            case 1024: s = launch_br<10>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, log2B, st); break;
-            case 2048: s = launch_br<11>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, log2B, st); break;
-            case 4096: s = launch_br<12>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, Q, log2B, st); break;
+            case 256: BM_GRP(8); break;
+            case 512: BM_GRP(9); break;
+            case 1024: BM_GRP(10); break;
+            case 2048: BM_GRP(11); break;
+            case 4096: BM_GRP(12); break;
             default: return BM_EINVAL;
         }
+#undef BM_GRP
         if (s != BM_OK) return s;
         i = j;
     }
+    return BM_OK;
+}
+
+// Number of leading plan jobs that the persistent kernel handles (ring
+// degree 1024..4096); make_plan(order_by_cost) puts them first.
+uint32_t persistent_prefix(const Plan &pl) {
+    uint32_t n = 0;
+    while (n < pl.dj.size() && pl.dj[n].N >= 1024 && pl.dj[n].N <= 4096) n++;
+    return n;
+}
+
+struct KsShape {
+    u32 threads;
+    size_t smem;
+};
+
+KsShape ks_shape(const bm_eval_key *const *keys, uint32_t n_keys) {
+    u32 maxN = 0, maxn = 0, maxlks = 0;
+    for (uint32_t i = 0; i < n_keys; i++) {
+        maxN = keys[i]->p.N > maxN ? keys[i]->p.N : maxN;
+        maxn = keys[i]->p.n > maxn ? keys[i]->p.n : maxn;
+        maxlks = keys[i]->p.l_ks > maxlks ? keys[i]->p.l_ks : maxlks;
+    }
+    const u32 threads = (maxn + 1 + 7) / 8 < 128 ? 128 : ((maxn + 1 + 7) / 8 + 31) / 32 * 32;
+    return {threads, (size_t)maxN * maxlks};
+}
+
+// Every launch of one batch (the plan is already in the workspace).
+bm_status launch_all(const Plan &pl, uint32_t n_persistent, const KsShape &ks, int device, u32 steps, bool do_ks,
+                     const uint64_t *d_ct_in, const uint32_t *d_lut, uint64_t *d_out, char *ws,
+                     cudaStream_t st) {
+    const uint32_t count = (uint32_t)pl.dj.size();
+    const DevJob *d_jobs = (const DevJob *)(ws + pl.jobs_off);
+    u64 *ws_acc = (u64 *)(ws + pl.acc_off_bytes);
+    bm_status s;
+    if (n_persistent) {
+        s = bm_launch_persistent_br(d_jobs, n_persistent, steps, d_ct_in, d_lut, ws_acc, (u32 *)ws,
+                                    (u32 *)ws + BM_WS_COUNTER_WORD, device, st);
+        if (s != BM_OK) return s;
+    }
+    if ((s = run_groups(pl, n_persistent, count, steps, d_ct_in, d_lut, ws, st, false)) != BM_OK) return s;
+    if (do_ks) {
+        k_extract_keyswitch<<<count, ks.threads, ks.smem, st>>>(d_jobs, steps, ws_acc, d_out);
+    } else {
+        k_copy_acc<<<count, 256, 0, st>>>(d_jobs, steps, ws_acc, d_out);
+    }
+    BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
 }
 
@@ -644,24 +445,7 @@ static bm_status bootstrap_impl(const bm_eval_key *const *keys, uint32_t n_keys,
     cudaStream_t st = (cudaStream_t)stream;
     char *ws = (char *)d_ws;
     if ((s = upload_plan(pl, ws, st)) != BM_OK) return s;
-    if ((s = run_blind_rotation(keys, jobs, count, steps, pl, d_ct_in, d_lut, ws, st)) != BM_OK) return s;
-    const DevJob *d_jobs = (const DevJob *)(ws + pl.jobs_off);
-    const u64 *ws_acc = (const u64 *)(ws + pl.acc_off_bytes);
-    if (do_ks) {
-        u32 maxN = 0, maxn = 0, maxlks = 0;
-        for (uint32_t i = 0; i < n_keys; i++) {
-            maxN = keys[i]->p.N > maxN ? keys[i]->p.N : maxN;
-            maxn = keys[i]->p.n > maxn ? keys[i]->p.n : maxn;
-            maxlks = keys[i]->p.l_ks > maxlks ? keys[i]->p.l_ks : maxlks;
-        }
-        const u32 threads = (maxn + 1 + 7) / 8 < 128 ? 128 : ((maxn + 1 + 7) / 8 + 31) / 32 * 32;
-        const size_t smem = (size_t)maxN * maxlks;
-        k_extract_keyswitch<<<count, threads, smem, st>>>(d_jobs, steps, ws_acc, d_out);
-    } else {
-        k_copy_acc<<<count, 256, 0, st>>>(d_jobs, steps, ws_acc, d_out);
-    }
-    BM_CUDA_TRY(cudaGetLastError());
-    return BM_OK;
+    return launch_all(pl, 0, ks_shape(keys, n_keys), dev, steps, do_ks, d_ct_in, d_lut, d_out, ws, st);
 }
 
 extern "C" bm_status bm_bootstrap_batch(const bm_eval_key *const *keys, uint32_t n_keys, const bm_job *jobs,
@@ -799,6 +583,100 @@ extern "C" bm_status bm_modmul_peak(int device, uint32_t iters, double *rate) {
     if (err != cudaSuccess) return BM_ECUDA;
     *rate = (double)blocks * threads * 8.0 * iters / (ms * 1e-3);
     return BM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Reusable batches: the plan is built and uploaded once; runs only launch.
+// ---------------------------------------------------------------------------
+
+struct bm_batch {
+    int device;
+    uint32_t flags, n_persistent;
+    Plan pl;
+    KsShape ks;
+    const uint64_t *d_ct_in;
+    const uint32_t *d_lut;
+    uint64_t *d_out;
+    char *ws;
+    cudaGraphExec_t exec;
+};
+
+extern "C" bm_status bm_batch_create(const bm_eval_key *const *keys, uint32_t n_keys, const bm_job *jobs,
+                                     uint32_t count, const uint64_t *d_ct_in, const uint32_t *d_lut,
+                                     uint64_t *d_ct_out, void *d_ws, size_t ws_bytes, uint32_t flags,
+                                     bm_batch **out) {
+    if (!out || (flags & ~(BM_BATCH_PERSISTENT | BM_BATCH_GRAPH))) return BM_EINVAL;
+    int dev = 0;
+    bm_status s = validate_jobs(keys, n_keys, jobs, count, &dev);
+    if (s != BM_OK) return s;
+    if (!count || !d_ct_in || !d_lut || !d_ct_out || !d_ws || ((uintptr_t)d_ws & 255)) return BM_EINVAL;
+    bm_batch *b = new (std::nothrow) bm_batch();
+    if (!b) return BM_ENOMEM;
+    b->device = dev;
+    b->flags = flags;
+    make_plan(keys, jobs, count, b->pl, (flags & BM_BATCH_PERSISTENT) != 0);
+    if (ws_bytes < b->pl.total) {
+        delete b;
+        return BM_EWORKSPACE;
+    }
+    b->n_persistent = (flags & BM_BATCH_PERSISTENT) ? persistent_prefix(b->pl) : 0;
+    b->ks = ks_shape(keys, n_keys);
+    b->d_ct_in = d_ct_in;
+    b->d_lut = d_lut;
+    b->d_out = d_ct_out;
+    b->ws = (char *)d_ws;
+    b->exec = nullptr;
+    DeviceGuard g(dev);
+    cudaError_t e = cudaMemcpy(b->ws + b->pl.jobs_off, b->pl.dj.data(), sizeof(DevJob) * count,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->ws, 0, BM_WS_HEADER);
+    // kernel attributes are set now, outside any later stream capture
+    if (e == cudaSuccess && run_groups(b->pl, b->n_persistent, count, 0, nullptr, nullptr, b->ws, nullptr,
+                                       true) != BM_OK)
+        e = cudaErrorUnknown;
+    if (e == cudaSuccess && b->n_persistent && bm_prepare_persistent_br(dev) != BM_OK) e = cudaErrorUnknown;
+    if (e != cudaSuccess) {
+        delete b;
+        return BM_ECUDA;
+    }
+    *out = b;
+    return BM_OK;
+}
+
+extern "C" bm_status bm_batch_run(bm_batch *b, void *stream) {
+    if (!b) return BM_EINVAL;
+    DeviceGuard g(b->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!(b->flags & BM_BATCH_GRAPH))
+        return launch_all(b->pl, b->n_persistent, b->ks, b->device, 0xffffffffu, true, b->d_ct_in, b->d_lut,
+                          b->d_out, b->ws, st);
+    if (!st) return BM_EINVAL;   // the legacy default stream cannot be captured
+    if (!b->exec) {
+        cudaGraph_t graph = nullptr;
+        BM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        bm_status s = launch_all(b->pl, b->n_persistent, b->ks, b->device, 0xffffffffu, true, b->d_ct_in,
+                                 b->d_lut, b->d_out, b->ws, st);
+        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (s != BM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess) return BM_ECUDA;
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            return BM_ECUDA;
+        }
+    }
+    BM_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+    return BM_OK;
+}
+
+extern "C" void bm_batch_free(bm_batch *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    delete b;
 }
 
 // ---------------------------------------------------------------------------

@@ -34,7 +34,16 @@ struct DevJob {
     u64 in_off, lut_off, out_off;
     u64 acc_off;       // element offset of the job's three [m][2][N] buffers in the
                        // workspace: ACC ping-pong and the per-step row sums
+    u32 variant;       // arithmetic variant of the key's modulus (BR_V_* flags)
+    u32 lbits;         // Karatsuba limb width, ceil(bits(Q - 1) / 2)
 };
+
+// Arithmetic variants of the blind rotation, chosen per key set on the host.
+#define BR_V_QLOW1 1u   // Q = c 2^32 + 1: one-multiply q Q
+#define BR_V_LAZY 2u    // correction-free forward NTT with an exact first stage
+
+// Workspace header: [0] status word, [1] job counter of the persistent kernel.
+#define BM_WS_COUNTER_WORD 1
 
 // Host-side evaluation key.
 struct bm_eval_key {
@@ -65,6 +74,14 @@ struct bm_secret_key {
 
 // Workspace header: the device status word sits at offset 0.
 #define BM_WS_HEADER 256
+
+// Persistent blind rotation of all jobs (persistent.cu): one block per SM
+// pulls jobs from a counter in the workspace header.
+bm_status bm_launch_persistent_br(const DevJob *d_jobs, uint32_t count, uint32_t steps,
+                                  const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc,
+                                  u32 *status, u32 *counter, int device, cudaStream_t st);
+size_t bm_persistent_smem();
+bm_status bm_prepare_persistent_br(int device);
 
 // Host helpers (keygen.cu)
 bm_status bm_check_key_params(const bm_key_params *p);

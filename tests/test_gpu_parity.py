@@ -319,3 +319,66 @@ def test_deterministic_repeat(api, orc, n1024):
     a = _run_batch(api, [n1024.ek], jobs, ct, luts, cnt * (kp.n + 1))
     b = _run_batch(api, [n1024.ek], jobs, ct, luts, cnt * (kp.n + 1))
     assert np.array_equal(a, b)
+
+
+# --- reusable batches: persistent launch over mixed key sets, graph replay ---------------
+
+def _mixed_batch(api, orc, ksets, shapes, seed, prefix):
+    """Jobs over several key sets; returns jobs, inputs, tables and the oracle outputs."""
+    cts, luts_l, jobs, want = [], [], [], []
+    in_off = lut_off = out_off = 0
+    for i, (ki, m, t) in enumerate(shapes):
+        ks = ksets[ki]
+        kp = ks.kp
+        _, ct = _encrypt(orc, ks, m, t, 1, seed + i, prefix=prefix)
+        lut, _ = synth.luts(t, 1, seed + 100 + i)
+        cts.append(ct[0]); luts_l.append(lut[0])
+        jobs.append((ki, m, t, 0, in_off, lut_off, out_off))
+        want.append(orc.bootstrap(kp, m, t, ks.bsk, ks.ksk, ct, lut)[0])
+        in_off += kp.n + 1; lut_off += t; out_off += kp.n + 1
+    return (np.array(jobs, dtype=api.JOB_DTYPE), np.concatenate(cts), np.concatenate(luts_l),
+            want, out_off)
+
+
+def test_batch_persistent_mixed_key_sets_bit_exact(api, orc, n1024, n2048):
+    """Six parameter sets over the two key sets in one persistent launch."""
+    shapes = [(0, 1, 256), (1, 8, 8192), (0, 2, 512), (1, 2, 2048), (0, 4, 1024), (1, 4, 4096),
+              (0, 4, 1024), (1, 2, 2048), (0, 1, 256)]
+    jobs, ct, luts, want, out_words = _mixed_batch(api, orc, [n1024, n2048], shapes, 60, prefix=4)
+    keys = [n1024.ek, n2048.ek]
+    d_in, d_lut = api.to_device_u64(ct), api.to_device_u32(luts)
+    d_out = torch.zeros(out_words, dtype=torch.int64, device="cuda")
+    ws = api.workspace(api.bm_workspace_bytes(keys, jobs))
+    b = api.Batch(keys, jobs, d_in, d_lut, d_out, ws, api.BATCH_PERSISTENT)
+    b.run()
+    torch.cuda.synchronize()
+    assert api.bm_workspace_status(ws) == 0
+    got = api.from_device_u64(d_out)
+    for j, w in zip(jobs, want):
+        o = int(j["out_off"])
+        assert np.array_equal(got[o:o + len(w)], w), j
+    b.free()
+
+
+@pytest.mark.parametrize("flags", ["graph", "persistent+graph"])
+def test_batch_graph_replay_matches_direct_path(api, orc, n1024, flags):
+    kp, m, t = n1024.kp, 4, 1024
+    cnt = 6
+    _, ct = _encrypt(orc, n1024, m, t, cnt, 70)
+    luts, _ = synth.luts(t, cnt, 2070)
+    jobs = _uniform_jobs(api, cnt, kp.n, t, m)
+    ref = _run_batch(api, [n1024.ek], jobs, ct, luts, cnt * (kp.n + 1))
+    d_in, d_lut = api.to_device_u64(ct.ravel()), api.to_device_u32(luts.ravel())
+    d_out = torch.zeros(cnt * (kp.n + 1), dtype=torch.int64, device="cuda")
+    ws = api.workspace(api.bm_workspace_bytes([n1024.ek], jobs))
+    fl = api.BATCH_GRAPH | (api.BATCH_PERSISTENT if "persistent" in flags else 0)
+    s = torch.cuda.Stream()
+    b = api.Batch([n1024.ek], jobs, d_in, d_lut, d_out, ws, fl)
+    for _ in range(2):
+        d_out.zero_()
+        torch.cuda.synchronize()
+        b.run(s)
+        s.synchronize()
+        assert np.array_equal(api.from_device_u64(d_out), ref)
+    assert api.bm_workspace_status(ws) == 0
+    b.free()
