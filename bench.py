@@ -310,6 +310,142 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Suite: the other workloads (one JSON line each; not the headline)
+# ---------------------------------------------------------------------------
+
+def _timed(fn, stream, reps, flush):
+    import torch
+    ts = []
+    for _ in range(reps):
+        flush.fill_(3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def _run_batch_rate(api, wl, keysets, batch, stream, flush, reps=3, flags=None):
+    import torch
+    dev = stream.device
+    d_in = api.to_device_u64(batch.ct_in, dev)
+    d_lut = api.to_device_u32(batch.luts, dev)
+    d_out = torch.zeros(batch.out_words, dtype=torch.int64, device=dev)
+    keys = [k.ek for k in keysets]
+    ws = api.workspace(api.bm_workspace_bytes(keys, batch.jobs), dev)
+    if flags is None:
+        fn = lambda: api.bm_bootstrap_batch(keys, batch.jobs, d_in, d_lut, d_out, ws, stream)
+    else:
+        b = api.Batch(keys, batch.jobs, d_in, d_lut, d_out, ws, flags)
+        fn = lambda: b.run(stream)
+    fn()
+    stream.synchronize()
+    ms = _timed(fn, stream, reps, flush)
+    out = api.from_device_u64(d_out)
+    bad = wl.check_outputs(keysets, batch, out)
+    return ms, bad, out
+
+
+def run_suite(args):
+    import torch
+    from paper_2310_12441_gb300 import api, autotune, serve
+    from paper_2310_12441_gb300 import workload as wl
+    from paper_2310_12441_gb300.params import JobShape
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    api.load()
+    lines = []
+
+    def emit(d):
+        d.setdefault("suite", True)
+        lines.append(d)
+        print(json.dumps(d), flush=True)
+
+    ks1024 = wl.make_keyset(P.KEYS_N1024, 1002)
+    # (1) same inputs, m = 4 / N = 1024 versus m = 1 / N = 4096
+    if "layouts" in args.suite:
+        ks4096 = wl.make_keyset(P.KEYS_N4096, 1002)
+        cnt = args.count or 4096
+        b4 = wl.make_batch([ks1024], [(0, JobShape(4, 1024), cnt)], 2, interleave=False)
+        ms4, bad4, _ = _run_batch_rate(api, wl, [ks1024], b4, stream, flush)
+        b1 = wl.make_batch([ks4096], [(0, JobShape(1, 1024), cnt)], 2, interleave=False)
+        same = bool(np.array_equal(b1.ct_in, b4.ct_in) and np.array_equal(b1.luts, b4.luts))
+        ms1, bad1, _ = _run_batch_rate(api, wl, [ks4096], b1, stream, flush)
+        emit({"workload": "same 4096 inputs: BootMMPM m=4 N=1024 vs single polynomial m=1 N=4096",
+              "inputs_identical": same,
+              "m4_N1024": {"bootstraps_per_s": cnt / ms4 * 1e3, "decrypt_failures": bad4},
+              "m1_N4096": {"bootstraps_per_s": cnt / ms1 * 1e3, "decrypt_failures": bad1},
+              "speedup_m4_over_m1": ms1 / ms4,
+              "key_bytes": {"N1024": ks1024.ek.nbytes, "N4096": ks4096.ek.nbytes}})
+        del ks4096
+    # (2) large plaintext t = 2^13, m = 8, N = 2048, random / identity tables 50/50
+    ks2048 = wl.make_keyset(P.KEYS_N2048, 1003)
+    if "large" in args.suite:
+        cnt = 2048
+        b3 = wl.make_batch([ks2048], [(0, JobShape(8, 8192), cnt)], 3, lut_mix="mixed", interleave=False)
+        ms, bad, _ = _run_batch_rate(api, wl, [ks2048], b3, stream, flush)
+        emit({"workload": P.LARGE_N2048.name, "bootstraps_per_s": cnt / ms * 1e3, "ms": ms,
+              "decrypt_failures": bad, "count": cnt})
+    # (3) uneven mix, 8192 jobs over six sets, Zipf(1.2) counts
+    if "uneven" in args.suite:
+        counts = synth.zipf_counts(8192, len(P.UNEVEN_SETS), 1.2, 5)
+        ksets = [ks1024, ks2048]
+        groups = [(0 if kp is P.KEYS_N1024 else 1, shape, int(c))
+                  for (name, kp, shape), c in zip(P.UNEVEN_SETS, counts)]
+        bu = wl.make_batch(ksets, groups, 4)
+        d_in = api.to_device_u64(bu.ct_in, dev)
+        d_lut = api.to_device_u32(bu.luts, dev)
+        d_out = torch.zeros(bu.out_words, dtype=torch.int64, device=dev)
+        ws = api.workspace(api.bm_workspace_bytes([k.ek for k in ksets], bu.jobs), dev)
+        best, tms = autotune.tune(ksets, bu.jobs, d_in, d_lut, d_out, ws, stream, use_cache=False)
+        res = {}
+        for name, fl in autotune.CANDIDATES.items():
+            ms, bad, _ = _run_batch_rate(api, wl, ksets, bu, stream, flush, flags=fl)
+            res[name] = {"bootstraps_per_s": len(bu.jobs) / ms * 1e3, "ms": ms, "decrypt_failures": bad}
+        emit({"workload": "uneven 8192 jobs, sets S1..S6, Zipf 1.2",
+              "counts": {n: int(c) for (n, _, _), c in zip(P.UNEVEN_SETS, counts)},
+              "autotune_choice": best, "autotune_ms": tms, "modes": res})
+    # (4) served stream over the t = 2^13, m = 8, N = 2048 set
+    if "served" in args.suite:
+        poolsz = 1024
+        bp = wl.make_batch([ks2048], [(0, JobShape(8, 8192), poolsz)], 9, lut_mix="mixed", interleave=False)
+        W = P.KEYS_N2048.n + 1
+        pool = [(0, 8, 8192, bp.ct_in[i * W:(i + 1) * W], bp.luts[i * 8192:(i + 1) * 8192])
+                for i in range(poolsz)]
+        cap = None
+        for rate in [float(r) for r in args.rates.split(",")]:
+            if rate < 1 and cap is not None:
+                rate_abs = rate * cap
+            else:
+                rate_abs = rate
+            srv = serve.Server([ks2048], max_batch=args.max_batch, streams=3)
+            r = serve.run_open_loop(srv, pool, rate_abs, args.serve_seconds, 11)
+            reqs = r.pop("requests")
+            if cap is None:
+                cap = r["throughput"]
+            r["workload"] = "served t=2^13 m=8 N=2048"
+            r["capacity_estimate"] = cap
+            emit(r)
+    # (5) decryption failures over >= 1e5 bootstraps of the headline workload
+    if "failures" in args.suite:
+        total, bad_total = 0, 0
+        cnt = 4096
+        it = 0
+        while total < args.fail_count:
+            b = wl.make_batch([ks1024], [(0, JobShape(4, 1024), cnt)], 500 + it, interleave=False)
+            _, bad, _ = _run_batch_rate(api, wl, [ks1024], b, stream, flush, reps=1)
+            total += cnt
+            bad_total += bad
+            it += 1
+        emit({"workload": P.BATCH_N1024.name, "bootstraps": total, "decrypt_failures": bad_total})
+    return lines
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -321,8 +457,16 @@ def main():
     ap.add_argument("--plain", type=int, default=64, help="ciphertexts timed in the plain form")
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--suite", default="", help="comma list: layouts,large,uneven,served,failures")
+    ap.add_argument("--rates", default="2000,0.25,0.5,0.9", help="served: req/s, or fractions of capacity")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--max-batch", type=int, default=512)
+    ap.add_argument("--fail-count", type=int, default=100000)
     args = ap.parse_args()
     w = P.WORKLOADS[args.workload]
+    if args.suite:
+        run_suite(args)
+        return
     if args.impl == "reference":
         run_reference(args, w)
     else:

@@ -231,9 +231,9 @@ double job_cost(const DevJob &d) {
     return (double)d.n * d.m * d.N * lg;
 }
 
-// order_by_cost: the device job table lists the longest jobs first (the
-// persistent kernel then pulls them in that order); outputs still go to the
-// jobs' own offsets.
+// The device job table is reordered (outputs still go to the jobs' own
+// offsets): by ring degree and variant for one-block-per-job launches, or,
+// with order_by_cost, longest first for the persistent kernel.
 bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t count, Plan &pl,
                     bool order_by_cost = false) {
     pl.jobs_off = BM_WS_HEADER;
@@ -257,9 +257,21 @@ bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t
         d.lbits = limb_bits(k->p.Q);
         acc_words += 3ull * 2 * jobs[i].m * k->p.N;
     }
-    if (order_by_cost)
-        std::stable_sort(pl.dj.begin(), pl.dj.end(),
-                         [](const DevJob &a, const DevJob &b) { return job_cost(a) > job_cost(b); });
+    if (order_by_cost) {
+        // jobs of ring degree 1024..4096 first (the persistent kernel's share),
+        // longest first; the rest grouped by degree and variant
+        std::stable_sort(pl.dj.begin(), pl.dj.end(), [](const DevJob &a, const DevJob &b) {
+            const bool pa = a.N >= 1024 && a.N <= 4096, pb = b.N >= 1024 && b.N <= 4096;
+            if (pa != pb) return pa;
+            if (pa) return job_cost(a) > job_cost(b);
+            return a.N != b.N ? a.N < b.N : a.variant < b.variant;
+        });
+    } else {
+        // one launch per run of equal degree and variant: group them
+        std::stable_sort(pl.dj.begin(), pl.dj.end(), [](const DevJob &a, const DevJob &b) {
+            return a.N != b.N ? a.N < b.N : a.variant < b.variant;
+        });
+    }
     pl.total = off + acc_words * 8;
     return BM_OK;
 }
