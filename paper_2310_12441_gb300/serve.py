@@ -53,7 +53,7 @@ class Stats:
 
 class Server:
     def __init__(self, keysets: list[KeySet], max_batch: int = 512, streams: int = 3,
-                 queue_cap: int = 20000, mem_cap_bytes: int = 120 << 30, device: int = 0,
+                 queue_cap: int = 2048, mem_cap_bytes: int = 120 << 30, device: int = 0,
                  keep_outputs: bool = False):
         import torch
         self.torch = torch
