@@ -136,10 +136,10 @@ def run_reference(args, w):
     if rank != 0:
         return
     vals = []
-    for _ in range(args.warmup):
-        pass
+    for s in range(args.warmup):                  # untimed: loads the library, warms caches
+        oracle_rate(w, steps_sample=1, seed=100 + s)
     for s in range(args.steps):
-        r, cores, sample = oracle_rate(w, steps_sample=4, seed=s)
+        r, cores, sample = oracle_rate(w, steps_sample=args.cpu_steps, seed=s)
         vals.append(r)
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "bootstraps/s",
@@ -455,7 +455,8 @@ def main():
     ap.add_argument("--workload", default=P.BATCH_N1024.name, choices=sorted(P.WORKLOADS))
     ap.add_argument("--count", type=int, default=0, help="override the batch size")
     ap.add_argument("--plain", type=int, default=64, help="ciphertexts timed in the plain form")
-    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--cpu-steps", type=int, default=16,
+                    help="CMux steps per ciphertext in the bounded oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--suite", default="", help="comma list: layouts,large,uneven,served,failures")
     ap.add_argument("--rates", default="2000,0.25,0.5,0.9", help="served: req/s, or fractions of capacity")

@@ -171,6 +171,7 @@ class Server:
                     return
                 free = [s for s in self.slabs if not s["busy"]]
                 if not free or not self.q:
+                    self.lock.wait(0.05)
                     continue
                 slab = free[0]
                 take = min(len(self.q), self.max_batch)
