@@ -86,6 +86,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(local_ms: float, count_per_rank: int, steps: int, world: int, dist=None, device=None):
+    """Whole-job rate over replicas: every rank bootstraps its own batch
+    (weak scaling); the job takes as long as the slowest rank, so the total
+    time is the maximum over ranks and the rate counts all ranks' work."""
+    total_ms = float(local_ms)
+    if world > 1 and dist is not None:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, count_per_rank * world * steps / (total_ms * 1e-3)
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -228,12 +241,7 @@ def run_gpu(args, w):
     if world > 1:
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = float(sum(ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = count * world * args.steps / (total_ms * 1e-3)
+    total_ms, value = aggregate(float(sum(ms)), count, args.steps, world, dist if world > 1 else None, dev)
 
     # kernel-level timing of the blind rotation alone (same jobs, same launch
     # configuration; bm_blind_rotate adds one ACC copy of m*2*N words per job)
