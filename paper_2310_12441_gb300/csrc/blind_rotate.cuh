@@ -92,26 +92,44 @@ struct Cfg {
     static constexpr int T = N / 16;                               // threads per polynomial
     static constexpr int P = kThreads / T;                         // polynomials per batch
     static constexpr int PPT = N >= kThreads ? N / kThreads : 1;   // positions per thread
-    static constexpr bool DSM = LOGN <= 11;                        // row differences in smem
-    static constexpr size_t SMEM = 2ull * P * N * 8 + (DSM ? 4ull * N * 8 : 0);
+    // rows per batch (every key word the multiply-accumulate loads would serve G
+    // rows; G = 2 measured 17% slower on GB300: the extra accumulators cost more
+    // registers than the halved key loads save)
+    static constexpr int G = 1;
+    static constexpr int CPB = P / G;                              // combos per batch
+    static constexpr size_t REGIONS = 2ull * P * N * 8;            // two regions per polynomial
+    static constexpr bool DSM = REGIONS + 4ull * G * N * 8 <= 200 * 1024;   // row differences in smem
+    static constexpr size_t SMEM = REGIONS + (DSM ? 4ull * G * N * 8 : 0);
 };
 
 // Blind rotation of one job by the whole block (all threads must call it).
 // sm: C::SMEM bytes of shared memory.  Variant flags: see choose_variant().
+//
+// A CMux step handles the m rows G at a time.  For a group of rows, the
+// 4 l_B digit polynomials per row ("combos": sign x component x digit) are
+// transformed P at a time, CPB combos of every row of the group per batch
+// (each polynomial by N/16 threads holding 16 coefficients in registers).
+// The transforms land in shared memory; every thread then multiplies the
+// positions it owns (q = tid + THREADS j) with the key rows of the batch's
+// combos (Karatsuba on half-width limbs, exact 128-bit row sums), so the
+// whole row needs a single reduction per position and column.  The reduced
+// row sums go to the job's sum buffer; after the last row the 2m sums are
+// inverse-transformed (P per batch) and added to the rows of the next ACC
+// buffer.
 template <int LOGN, int THREADS, bool LAZY, bool SMALL0, bool QLOW1>
 __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u64 *__restrict__ ct_in,
                                        const u32 *__restrict__ luts, u64 *ws, u32 *status, u64 *sm) {
     using C = Cfg<LOGN, THREADS>;
-    constexpr int N = C::N;
+    constexpr int N = C::N, G = C::G, CPB = C::CPB;
     const KeyDev *K = J.key;
     const u32 lbits = J.lbits;
-    // a batch's C::P limb products must fit 64 bits, else fold after each one
-    const bool fold_each = (unsigned __int128)C::P * ((2ull << lbits) - 1) * ((2ull << lbits) - 1) >=
+    // a batch's CPB limb products must fit 64 bits, else fold after each one
+    const bool fold_each = (unsigned __int128)CPB * ((2ull << lbits) - 1) * ((2ull << lbits) - 1) >=
                            ((unsigned __int128)1 << 64);
     const u32 m = J.m, t = J.t, lB = K->l_B, log2B = K->log2_B, n = K->n;
     const ModQ mq = K->mq;
     const u64 Q = mq.Q;
-    const u64 qp = 2ull * N * m;
+    const u32 qp = 2u * N * m;                 // 2Nm < 2^20
     const u64 Bmask = (1ull << log2B) - 1;
     const u64 *twp = K->twp, *itwp = K->itwp;
     const u32 tid = threadIdx.x;
@@ -132,141 +150,165 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
 
     const u32 p = tid / C::T;          // polynomial slot within a batch
     const u32 l = tid % C::T;          // thread within the polynomial
+    const u32 pc = p / G, pg = p % G;  // its combo within the batch and row within the group
     ntr::Swap sw{sm + (size_t)p * N, sm + (size_t)(C::P + p) * N, 0};
-    u64 *dbuf = sm + (size_t)2 * C::P * N;   // [4][N] row differences (DSM only)
+    u64 *dbuf = sm + (size_t)2 * C::P * N;     // [G][4][N] row differences (DSM only)
     const u64 qb = Q << log2B;                 // Q * B, used when SMALL0
     const u64 lmask = (1ull << lbits) - 1;     // Karatsuba limb mask
     const u32 ncomb = 4 * lB;
     const size_t rgsw = (size_t)2 * lB * 2 * N;
 
+    auto kara = [&](u64 xv, u64 bv, u64 &kh, u64 &kl, u64 &km) {
+        const u32 x0 = (u32)(xv & lmask), x1 = (u32)(xv >> lbits);
+        const u32 b0 = (u32)(bv & lmask), b1 = (u32)(bv >> lbits);
+        kh += (u64)x1 * b1;
+        kl += (u64)x0 * b0;
+        km += (u64)(x0 + x1) * (b0 + b1);
+    };
+
     u64 *cur = acc0, *nxt = acc1;
     const u32 steps = steps_limit < n ? steps_limit : n;
     for (u32 k = 0; k < steps; k++) {
-        const u64 ak = ct[k] % qp;
+        const u32 ak = (u32)(ct[k] % qp);
         const u64 *bsk_k = K->bsk + (size_t)k * 2 * rgsw;
-        for (u32 r = 0; r < m; r++) {
-            u64 lo[2][C::PPT], hi[2][C::PPT];
+        for (u32 r0 = 0; r0 < m; r0 += G) {
+            u64 lo[G][2][C::PPT], hi[G][2][C::PPT];
 #pragma unroll
-            for (int j = 0; j < C::PPT; j++) lo[0][j] = hi[0][j] = lo[1][j] = hi[1][j] = 0;
+            for (int g = 0; g < G; g++)
+#pragma unroll
+                for (int j = 0; j < C::PPT; j++) lo[g][0][j] = hi[g][0][j] = lo[g][1][j] = hi[g][1][j] = 0;
+            // source row and monomial exponent of P(c) for rows r0 + g,
+            // c = -a_k (sign 0) and c = a_k (sign 1), Eq. (ex1:BPc)
+            u32 rsrc[G][2], rexp[G][2];
+#pragma unroll
+            for (int g = 0; g < G; g++)
+#pragma unroll
+                for (int sg = 0; sg < 2; sg++) {
+                    const u32 r = r0 + g;
+                    const u32 cv = sg == 0 ? (ak ? qp - ak : 0u) : ak;
+                    const u32 ea = cv / m, bb = cv % m;
+                    rsrc[g][sg] = r >= bb ? r - bb : r + m - bb;
+                    const u32 e = r >= bb ? ea : ea + 1;
+                    rexp[g][sg] = e >= 2 * N ? e - 2 * N : e;
+                }
             if constexpr (C::DSM) {
-                // D_(sign, comp) = P(c) ACC - ACC for row r, c = -a_k / a_k
-                for (u32 w = tid; w < 4u * N; w += C::kThreads) {
-                    const u32 pair = w / N, idx = w % N;
-                    const u32 sgn = pair >> 1, comp = pair & 1;
-                    const u64 cv = sgn == 0 ? (qp - ak) % qp : ak;
-                    const u32 ea = (u32)(cv / m), bb = (u32)(cv % m);
-                    const u32 src = r >= bb ? r - bb : r + m - bb;
-                    u32 e = r >= bb ? ea : ea + 1;
-                    if (e >= 2 * N) e -= 2 * N;
-                    const u64 *srow = cur + ((size_t)src * 2 + comp) * N;
-                    const u64 *orow = cur + ((size_t)r * 2 + comp) * N;
-                    dbuf[w] = sub_mod(rotated_coeff(srow, idx, e, N, Q), orow[idx], Q);
+                // D_(row, sign, comp) = P(c) ACC - ACC
+                for (u32 w = tid; w < 4u * G * N; w += C::kThreads) {
+                    const u32 g = w / (4 * N), pair = (w / N) & 3, idx = w % N;
+                    const u32 r = r0 + g;
+                    if (r < m) {
+                        const u32 sgn = pair >> 1, comp = pair & 1;
+                        const u64 *srow = cur + ((size_t)rsrc[g][sgn] * 2 + comp) * N;
+                        const u64 *orow = cur + ((size_t)r * 2 + comp) * N;
+                        dbuf[w] = sub_mod(rotated_coeff(srow, idx, rexp[g][sgn], N, Q), orow[idx], Q);
+                    }
                 }
                 __syncthreads();
             }
-            for (u32 c0 = 0; c0 < ncomb; c0 += C::P) {
+            for (u32 c0 = 0; c0 < ncomb; c0 += CPB) {
                 // --- this thread's digit polynomial, transformed into shared memory
-                const u32 c = c0 + p;
-                const bool active = c < ncomb;
+                const u32 c = c0 + pc, r = r0 + pg;
+                const bool active = pc < (u32)CPB && c < ncomb && r < m;
                 u64 x[16];
-                if (active && C::DSM) {
+                if (active) {
                     const u32 pair = c / lB, sh = (c % lB) * log2B;
-                    const u64 *dp = dbuf + (size_t)pair * N;
+                    if constexpr (C::DSM) {
+                        const u64 *dp = dbuf + ((size_t)pg * 4 + pair) * N;
 #pragma unroll
-                    for (int i = 0; i < 16; i++) x[i] = (dp[l + C::T * i] >> sh) & Bmask;
-                } else if (active) {
-                    const u32 sgn = c / (2 * lB), comp = (c / lB) & 1, d = c % lB;
-                    const u64 cv = sgn == 0 ? (qp - ak) % qp : ak;
-                    const u32 ea = (u32)(cv / m), bb = (u32)(cv % m);
-                    const u32 src = r >= bb ? r - bb : r + m - bb;
-                    u32 e = r >= bb ? ea : ea + 1;
-                    if (e >= 2 * N) e -= 2 * N;
-                    const u64 *srow = cur + ((size_t)src * 2 + comp) * N;
-                    const u64 *orow = cur + ((size_t)r * 2 + comp) * N;
-                    const u32 sh = d * log2B;
+                        for (int i = 0; i < 16; i++) x[i] = (dp[l + C::T * i] >> sh) & Bmask;
+                    } else {
+                        const u32 sgn = pair >> 1, comp = pair & 1;
+                        const u64 *srow = cur + ((size_t)rsrc[pg][sgn] * 2 + comp) * N;
+                        const u64 *orow = cur + ((size_t)r * 2 + comp) * N;
 #pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        const u32 idx = l + C::T * i;
-                        const u64 D = sub_mod(rotated_coeff(srow, idx, e, N, Q), orow[idx], Q);
-                        x[i] = (D >> sh) & Bmask;
+                        for (int i = 0; i < 16; i++) {
+                            const u32 idx = l + C::T * i;
+                            const u64 D = sub_mod(rotated_coeff(srow, idx, rexp[pg][sgn], N, Q), orow[idx], Q);
+                            x[i] = (D >> sh) & Bmask;
+                        }
                     }
                 }
                 u64 *out = ntr::fwd_to_smem<LOGN, LAZY, SMALL0, QLOW1>(x, sw, l, active, twp, Q, mq.one_sh, qb);
-                // regions of the other polynomials of the batch sit at stride N
+                // regions of the other polynomials of the batch sit at stride N;
+                // polynomial cc G + g holds combo c0 + cc of row r0 + g
                 const u64 *slots = out - (size_t)p * N;
                 __syncthreads();
                 // --- multiply-accumulate against the key rows of the batch's combos
                 // (combo c = (sign, component, digit) is key row c of the step).
-                // Karatsuba on half-width limbs x = x1 2^lbits + x0: the limb
-                // products x1 b1, x0 b0 and (x0 + x1)(b0 + b1) are summed over
-                // the batch in 64-bit registers, then folded into the 128-bit
-                // row sums as hi 2^(2 lbits) + (mid - hi - lo) 2^lbits + lo.
+                // Limb products x1 b1, x0 b0 and (x0 + x1)(b0 + b1) are summed over
+                // the batch in 64-bit registers, then folded into the 128-bit row
+                // sums as hi 2^(2 lbits) + (mid - hi - lo) 2^lbits + lo.
                 const u64 *bsk_c0 = bsk_k + (size_t)c0 * 2 * N;
-                const u32 nc = ncomb - c0 < (u32)C::P ? ncomb - c0 : (u32)C::P;
-                auto fold = [&](int j, u64 (&kh)[2], u64 (&kl)[2], u64 (&km)[2]) {
+                const u32 nc = ncomb - c0 < (u32)CPB ? ncomb - c0 : (u32)CPB;
 #pragma unroll
-                    for (int col = 0; col < 2; col++) {
-                        add128(lo[col][j], hi[col][j], kl[col]);
-                        add128_shl(lo[col][j], hi[col][j], km[col] - kh[col] - kl[col], lbits);
-                        add128_shl(lo[col][j], hi[col][j], kh[col], 2 * lbits);
-                        kh[col] = kl[col] = km[col] = 0;
-                    }
-                };
-                auto kara = [&](u64 xv, u64 bv, u64 &kh, u64 &kl, u64 &km) {
-                    const u32 x0 = (u32)(xv & lmask), x1 = (u32)(xv >> lbits);
-                    const u32 b0 = (u32)(bv & lmask), b1 = (u32)(bv >> lbits);
-                    kh += (u64)x1 * b1;
-                    kl += (u64)x0 * b0;
-                    km += (u64)(x0 + x1) * (b0 + b1);
-                };
-                if (nc == (u32)C::P && !fold_each) {
-                    // full batch: every key word of a position is requested first
+                for (int j = 0; j < C::PPT; j++) {
+                    const u32 q = tid + C::kThreads * j;
+                    if (q < (u32)N) {
+                        const u32 sq = ntr::swz(q);
+                        u64 kh[G][2], kl[G][2], km[G][2];
 #pragma unroll
-                    for (int j = 0; j < C::PPT; j++) {
-                        const u32 q = tid + C::kThreads * j;
-                        if (q < (u32)N) {
-                            const u32 sq = ntr::swz(q);
-                            u64 bv[C::P][2];
+                        for (int g = 0; g < G; g++) kh[g][0] = kl[g][0] = km[g][0] = kh[g][1] = kl[g][1] = km[g][1] = 0;
+                        auto fold = [&]() {
 #pragma unroll
-                            for (int cc = 0; cc < C::P; cc++) {
+                            for (int g = 0; g < G; g++)
+#pragma unroll
+                                for (int col = 0; col < 2; col++) {
+                                    add128(lo[g][col][j], hi[g][col][j], kl[g][col]);
+                                    add128_shl(lo[g][col][j], hi[g][col][j], km[g][col] - kh[g][col] - kl[g][col], lbits);
+                                    add128_shl(lo[g][col][j], hi[g][col][j], kh[g][col], 2 * lbits);
+                                    kh[g][col] = kl[g][col] = km[g][col] = 0;
+                                }
+                        };
+                        if (nc == (u32)CPB && !fold_each) {
+                            // full batch: the position's key words are requested first
+                            u64 bv[CPB][2];
+#pragma unroll
+                            for (int cc = 0; cc < CPB; cc++) {
                                 bv[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q);
                                 bv[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q);
                             }
-                            u64 kh[2] = {0, 0}, kl[2] = {0, 0}, km[2] = {0, 0};
 #pragma unroll
-                            for (int cc = 0; cc < C::P; cc++) {
-                                const u64 xv = slots[(size_t)cc * N + sq];
-                                kara(xv, bv[cc][0], kh[0], kl[0], km[0]);
-                                kara(xv, bv[cc][1], kh[1], kl[1], km[1]);
-                            }
-                            fold(j, kh, kl, km);
-                        }
-                    }
-                } else {
-                    for (int j = 0; j < C::PPT; j++) {
-                        const u32 q = tid + C::kThreads * j;
-                        if (q < (u32)N) {
-                            const u32 sq = ntr::swz(q);
-                            u64 kh[2] = {0, 0}, kl[2] = {0, 0}, km[2] = {0, 0};
+                            for (int cc = 0; cc < CPB; cc++)
+#pragma unroll
+                                for (int g = 0; g < G; g++) {
+                                    if (G == 1 || r0 + g < m) {
+                                        const u64 xv = slots[(size_t)(cc * G + g) * N + sq];
+                                        kara(xv, bv[cc][0], kh[g][0], kl[g][0], km[g][0]);
+                                        kara(xv, bv[cc][1], kh[g][1], kl[g][1], km[g][1]);
+                                    }
+                                }
+                        } else {
                             for (u32 cc = 0; cc < nc; cc++) {
-                                const u64 xv = slots[(size_t)cc * N + sq];
                                 const u64 *brow = bsk_c0 + (size_t)cc * 2 * N + q;
-                                kara(xv, __ldg(brow), kh[0], kl[0], km[0]);
-                                kara(xv, __ldg(brow + N), kh[1], kl[1], km[1]);
-                                if (fold_each) fold(j, kh, kl, km);
+                                const u64 b0 = __ldg(brow), b1 = __ldg(brow + N);
+#pragma unroll
+                                for (int g = 0; g < G; g++) {
+                                    if (G == 1 || r0 + g < m) {
+                                        const u64 xv = slots[(size_t)(cc * G + g) * N + sq];
+                                        kara(xv, b0, kh[g][0], kl[g][0], km[g][0]);
+                                        kara(xv, b1, kh[g][1], kl[g][1], km[g][1]);
+                                    }
+                                }
+                                if (fold_each) fold();
                             }
-                            fold(j, kh, kl, km);
                         }
+                        fold();
                     }
                 }
             }
             // --- reduced row sums (NTT domain) to the sum buffer
 #pragma unroll
-            for (int j = 0; j < C::PPT; j++) {
-                const u32 q = tid + C::kThreads * j;
-                if (q < (u32)N) {
-                    sums[((size_t)r * 2) * N + q] = reduce128(lo[0][j], hi[0][j], mq);
-                    sums[((size_t)r * 2 + 1) * N + q] = reduce128(lo[1][j], hi[1][j], mq);
+            for (int g = 0; g < G; g++) {
+                const u32 r = r0 + g;
+                if (G == 1 || r < m) {
+#pragma unroll
+                    for (int j = 0; j < C::PPT; j++) {
+                        const u32 q = tid + C::kThreads * j;
+                        if (q < (u32)N) {
+                            sums[((size_t)r * 2) * N + q] = reduce128(lo[g][0][j], hi[g][0][j], mq);
+                            sums[((size_t)r * 2 + 1) * N + q] = reduce128(lo[g][1][j], hi[g][1][j], mq);
+                        }
+                    }
                 }
             }
         }

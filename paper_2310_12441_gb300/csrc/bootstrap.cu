@@ -276,11 +276,9 @@ bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t
     return BM_OK;
 }
 
-// One block per job.  Up to N = 1024 two blocks of 256 threads share an SM
-// (two jobs whose barriers and memory phases overlap each other's
-// arithmetic); larger rings use one block of 512 threads.
+// One block of 512 threads per job.
 template <int LOGN>
-__host__ __device__ constexpr int group_threads() { return LOGN <= 10 ? 256 : 512; }
+__host__ __device__ constexpr int group_threads() { return 512; }
 
 template <int LOGN, bool LAZY, bool SMALL0, bool QLOW1>
 __global__ void __launch_bounds__(group_threads<LOGN>(), 512 / group_threads<LOGN>())
