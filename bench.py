@@ -35,6 +35,23 @@ from paper_2310_12441_gb300 import synth  # noqa: E402
 METRIC = "bootstraps/s on 1 GB300 (batched, bit-exact)"
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# blind-rotation kernel per job, from one ncu capture of a 152-job launch
+# of this workload (profiles/k_blind_rotate_n630_N1024_m4.md), valid while
+# the kernel sources hash to the captured version.
+KERNEL_SOURCES = ["blind_rotate.cuh", "ntt_reg.cuh", "modarith.cuh", "common.cuh", "bootstrap.cu"]
+CAPTURED_TRAFFIC = {"hash": "44e344ddbb778d79", "bytes_per_job": (262.189568e6 + 1.082509e9) / 152}
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2310_12441_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def modmuls_per_bootstrap(kp, m):
     """Algorithmic 64-bit modular multiplications of one bootstrap: per CMux
     step and row, 4 l_B forward and 2 inverse negacyclic NTTs of (N/2) log2 N
@@ -271,9 +288,12 @@ def run_gpu(args, w):
         peak = api.bm_modmul_peak(local, 1 << 14)
         mm = modmuls_per_bootstrap(kp, m) * count
         rot_s = float(np.mean(rot_ms)) * 1e-3
+        traffic = None
+        if w is P.BATCH_N1024 and kernel_hash() == CAPTURED_TRAFFIC["hash"]:
+            traffic = CAPTURED_TRAFFIC["bytes_per_job"] * count
         result["roofline"] = {"bound": "alu", "achieved": mm / rot_s / 1e9,
                               "peak": peak / 1e9, "unit": "Gmodmul/s",
-                              "frac": (mm / rot_s) / peak, "traffic": None,
+                              "frac": (mm / rot_s) / peak, "traffic": traffic,
                               "kernel": "k_blind_rotate", "kernel_ms": rot_s * 1e3,
                               "modmuls_per_launch": mm}
         # plain form: one ciphertext per launch

@@ -2,8 +2,7 @@
 
 Candidates (all bit-identical in their results):
   * "grouped":    one launch per run of equal ring degree and variant, one
-                  block per job (256 threads for N <= 1024, two blocks per SM;
-                  512 threads above);
+                  512-thread block per job;
   * "persistent": one launch for every job of degree 1024..4096, one
                   512-thread block per SM pulling jobs longest first.
 Both are recorded in a CUDA graph and replayed.  The tuner times each
