@@ -213,6 +213,34 @@ bm_status bm_batch_create(const bm_eval_key *const *keys, uint32_t n_keys,
 bm_status bm_batch_run(bm_batch *batch, void *stream);
 void bm_batch_free(bm_batch *batch);
 
+/* Modulus switch (Section 2 item (9)) of `words` consecutive words, on the
+ * device of the current context: out = floor((x q_to + floor(q_from/2)) /
+ * q_from) mod q_to, x in [0, q_from) (larger words are first reduced).  Used
+ * before bootstrapping (q -> 2Nm, Algorithm 1's first line) and after it
+ * (Q -> q, Algorithm 1's last line); in place is allowed. */
+bm_status bm_mod_switch(const uint64_t *d_in, uint64_t *d_out, size_t words,
+                        uint64_t q_from, uint64_t q_to, void *stream);
+
+/* Any function f: Z_t -> Z_t, negacyclic or not, by the two-round method of
+ * Section 4 (last part; Eqs. (rel:mp), (rel:sign)).  Each input is an
+ * LWE_{n,q} encryption of m in [0, t) under plaintext modulus 2t (its top bit
+ * may be unknown: any x in Z_{2t} is read as m = x mod t).  Round 1
+ * bootstraps mp (-t/2 on [-t/2, t/2), t/2 elsewhere) to extract the top bit,
+ * using sign(x) t = mp(x) + t/2; that is switched back to q and subtracted,
+ * leaving y in [-t/2, t/2) with y = m mod t; round 2 bootstraps the
+ * negacyclic extension F of f from [-t/2, t/2).  Each bootstrap switches
+ * q -> 2Nm first and Q -> q after (Algorithm 1's modulus switches).
+ * Outputs: LWE_{n,q} encryptions of f(m) under plaintext modulus 2t.
+ * d_f: count tables of t uint32 entries in [0, t); d_ct_in / d_ct_out:
+ * [count][n+1] words mod q; needs 2t <= 2Nm, 2t <= q < Q, and a workspace of
+ * bm_arbitrary_workspace_bytes(key, m, t, count) bytes. */
+size_t bm_arbitrary_workspace_bytes(const bm_eval_key *key, uint32_t m, uint32_t t,
+                                    uint32_t count);
+bm_status bm_bootstrap_arbitrary(const bm_eval_key *key, uint32_t m, uint32_t t,
+                                 uint64_t q, const uint32_t *d_f, uint32_t count,
+                                 const uint64_t *d_ct_in, uint64_t *d_ct_out,
+                                 void *d_ws, size_t ws_bytes, void *stream);
+
 /* Reads (synchronising `stream`) and clears the device status word of a
  * workspace: BM_OK or the first device-side error recorded. */
 bm_status bm_workspace_status(void *d_ws, void *stream);

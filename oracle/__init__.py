@@ -62,6 +62,11 @@ def lib():
         L.orc_lwe_phase.restype = C.c_uint64
         L.orc_decrypt.argtypes = [C.c_uint32, C.c_uint64, C.c_uint32, i8p, u64p, C.c_size_t, u32p]
         L.orc_rlwe_phase.argtypes = [C.c_uint32, C.c_uint64, i8p, u64p, u64p, u64p]
+        L.orc_mod_switch.argtypes = [u64p, C.c_size_t, C.c_uint64, C.c_uint64, u64p]
+        L.orc_two_round_tables.argtypes = [C.c_uint32, u32p, u32p, u32p]
+        L.orc_bootstrap_arbitrary.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_uint32, C.c_uint64,
+                                              u64p, C.c_uint32, u64p, u64p, u32p, C.c_size_t, u64p]
+        L.orc_bootstrap_arbitrary.restype = C.c_int
         L.orc_bootstrap.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_uint32, u64p, C.c_uint32,
                                     u64p, u64p, u32p, C.c_size_t, u64p]
         L.orc_bootstrap.restype = C.c_int
@@ -235,6 +240,14 @@ def rlwe_phase(N: int, Q: int, z, a, b) -> np.ndarray:
     return out
 
 
+def mod_switch(ct, q_from: int, q_to: int) -> np.ndarray:
+    """Section 2 (9) on every word of ct (any shape)."""
+    ct, pc = _p(ct, np.uint64, u64p)
+    out = np.empty_like(ct)
+    lib().orc_mod_switch(pc, ct.size, q_from, q_to, out.ctypes.data_as(u64p))
+    return out
+
+
 def bootstrap(kp, m: int, t: int, bsk, ksk, ct_in, luts) -> np.ndarray:
     """Algorithm 1 (modulus switches excluded) for count ciphertexts."""
     bsk, pb = _p(bsk, np.uint64, u64p)
@@ -246,6 +259,31 @@ def bootstrap(kp, m: int, t: int, bsk, ksk, ct_in, luts) -> np.ndarray:
     prm = _params(kp)
     rc = lib().orc_bootstrap(C.byref(prm), m, t, pb, bsk.shape[0], pk, pc, pl, count,
                              out.ctypes.data_as(u64p))
+    if rc != 0:
+        raise ValueError("ciphertext uses a bootstrapping key that was not provided")
+    return out
+
+
+def two_round_tables(t: int, f) -> tuple[np.ndarray, np.ndarray]:
+    """mp and the negacyclic extension F of f (both over Z_{2t})."""
+    f, pf = _p(f, np.uint32, u32p)
+    mp = np.empty(2 * t, np.uint32)
+    F = np.empty(2 * t, np.uint32)
+    lib().orc_two_round_tables(t, pf, mp.ctypes.data_as(u32p), F.ctypes.data_as(u32p))
+    return mp, F
+
+
+def bootstrap_arbitrary(kp, m: int, t: int, q: int, bsk, ksk, ct_in, f) -> np.ndarray:
+    """Two-round bootstrap of any f: Z_t -> Z_t (one table of t entries per
+    ciphertext); inputs and outputs in LWE_{n,q}, plaintext modulus 2t."""
+    bsk, pb = _p(bsk, np.uint64, u64p)
+    ksk, pk = _p(ksk, np.uint64, u64p)
+    ct_in, pc = _p(np.atleast_2d(ct_in), np.uint64, u64p)
+    f, pf = _p(np.atleast_2d(f), np.uint32, u32p)
+    out = np.empty_like(ct_in)
+    prm = _params(kp)
+    rc = lib().orc_bootstrap_arbitrary(C.byref(prm), m, t, q, pb, bsk.shape[0], pk, pc, pf,
+                                       ct_in.shape[0], out.ctypes.data_as(u64p))
     if rc != 0:
         raise ValueError("ciphertext uses a bootstrapping key that was not provided")
     return out

@@ -460,6 +460,19 @@ void orc_rlwe_phase(uint32_t N, u64 Q, const int8_t *z, const u64 *a, const u64 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Modulus switch (Section 2, (9)): x -> round(x q_to / q_from), rounding    */
+/* half up, i.e. floor((x q_to + floor(q_from / 2)) / q_from) mod q_to,      */
+/* applied to every word of the given ciphertexts.                           */
+/* ------------------------------------------------------------------------ */
+void orc_mod_switch(const u64 *in, size_t words, u64 q_from, u64 q_to, u64 *out)
+{
+    for (size_t i = 0; i < words; i++) {
+        u128 x = (u128)(in[i] % q_from) * q_to + q_from / 2;
+        out[i] = (u64)((x / q_from) % q_to);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Algorithm 1 end to end (modulus switch q -> 2Nm is the identity here:    */
 /* inputs are given in Z_{2Nm}; the final Q -> q switch is not applied).    */
 /* ------------------------------------------------------------------------ */
@@ -487,4 +500,68 @@ int orc_bootstrap(const orc_params *p, uint32_t m, uint32_t t, const u64 *bsk,
         free(acc); free(lwe);
     }
     return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Arbitrary f: Z_t -> Z_t by two rounds (Section 4, last part): the input   */
+/* encrypts m in [0, t) under plaintext modulus 2t; its unknown top bit is   */
+/* extracted with the negacyclic mp (mp(x) = -t/2 on [-t/2, t/2), t/2 on     */
+/* the rest of [-t, t)), using sign(x) t = mp(x) + t/2 (Eq. (rel:sign));     */
+/* subtracting sign(x) t leaves y in [-t/2, t/2) with y = m mod t, and a    */
+/* second bootstrap with the negacyclic extension F of f from [-t/2, t/2)    */
+/* (F(y) = f(y mod t) there, F(y + t) = -F(y)) gives f(m).                   */
+/* Inputs and outputs are LWE_{n,q}; bootstraps run at q' = 2Nm, plaintext   */
+/* modulus 2t.                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Tables over Z_{2t}: mp[x] and F[y] (per job, from f's t entries). */
+void orc_two_round_tables(uint32_t t, const uint32_t *f, uint32_t *mp, uint32_t *F)
+{
+    uint32_t T = 2 * t;
+    for (uint32_t x = 0; x < T; x++) {
+        /* x in [-t/2, t/2) mod 2t  <=>  x < t/2 or x >= 3t/2 */
+        int lower = x < t / 2 || x >= 3 * t / 2;
+        mp[x] = lower ? T - t / 2 : t / 2;
+    }
+    for (uint32_t y = 0; y < T; y++) {
+        if (y < t / 2) F[y] = f[y] % T;
+        else if (y >= 3 * t / 2) F[y] = f[y - t] % T;          /* y - 2t in [-t/2, 0): y mod t = y - t */
+        else {                                                   /* F(y) = -F(y - t) */
+            uint32_t z = (y + t) % T;                            /* (y - t) mod 2t: [0, t/2) or [3t/2, 2t) */
+            uint32_t v = z < t / 2 ? f[z] : f[z - t];
+            F[y] = (T - v % T) % T;
+        }
+    }
+}
+
+int orc_bootstrap_arbitrary(const orc_params *p, uint32_t m, uint32_t t, u64 q, const u64 *bsk,
+                            uint32_t n_keys, const u64 *ksk, const u64 *ct_in, const uint32_t *f,
+                            size_t count, u64 *ct_out)
+{
+    uint32_t n = p->n, T = 2 * t;
+    u64 qp = 2ull * p->N * m;
+    size_t W = (size_t)count * (n + 1);
+    u64 *a = malloc(sizeof(u64) * W), *b = malloc(sizeof(u64) * W);
+    uint32_t *mp = malloc(sizeof(uint32_t) * T * count), *F = malloc(sizeof(uint32_t) * T * count);
+    for (size_t i = 0; i < count; i++)
+        orc_two_round_tables(t, f + i * t, mp + i * T, F + i * T);
+    int rc = 0;
+    /* round 1: mp */
+    orc_mod_switch(ct_in, W, q, qp, a);
+    rc |= orc_bootstrap(p, m, T, bsk, n_keys, ksk, a, mp, count, b);
+    orc_mod_switch(b, W, p->Q, q, b);
+    /* y = x - (mp(x) + t/2) at modulus q, plaintext scale floor(q / 2t) */
+    u64 half = (u64)(t / 2) * (q / T) % q;
+    for (size_t i = 0; i < count; i++)
+        for (uint32_t c = 0; c <= n; c++) {
+            size_t k = i * (n + 1) + c;
+            u64 v = sub_mod(ct_in[k] % q, b[k], q);
+            a[k] = c == n ? sub_mod(v, half, q) : v;
+        }
+    /* round 2: F */
+    orc_mod_switch(a, W, q, qp, a);
+    rc |= orc_bootstrap(p, m, T, bsk, n_keys, ksk, a, F, count, b);
+    orc_mod_switch(b, W, p->Q, q, ct_out);
+    free(a); free(b); free(mp); free(F);
+    return rc ? -1 : 0;
 }

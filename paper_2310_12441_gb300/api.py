@@ -27,7 +27,8 @@ SYMBOLS = ["bm_keygen", "bm_free_secret_key", "bm_free_eval_key", "bm_eval_key_b
            "bm_host_staging_bytes", "bm_bootstrap_batch_host", "bm_blind_rotate",
            "bm_sample_extract", "bm_key_switch", "bm_poly_mul", "bm_workspace_status",
            "bm_modmul_peak", "bm_status_str", "bm_bootstrap_batch_noalloc",
-           "bm_batch_create", "bm_batch_run", "bm_batch_free"]
+           "bm_batch_create", "bm_batch_run", "bm_batch_free", "bm_mod_switch",
+           "bm_arbitrary_workspace_bytes", "bm_bootstrap_arbitrary"]
 
 BATCH_PERSISTENT = 1
 BATCH_GRAPH = 2
@@ -112,6 +113,12 @@ def load(build_if_needed: bool = True) -> C.CDLL:
     L.bm_batch_run.argtypes = [vp, vp]
     L.bm_batch_run.restype = i32
     L.bm_batch_free.argtypes = [vp]
+    L.bm_mod_switch.argtypes = [vp, vp, sz, C.c_uint64, C.c_uint64, vp]
+    L.bm_mod_switch.restype = i32
+    L.bm_arbitrary_workspace_bytes.argtypes = [vp, u32, u32, u32]
+    L.bm_arbitrary_workspace_bytes.restype = sz
+    L.bm_bootstrap_arbitrary.argtypes = [vp, u32, u32, C.c_uint64, vp, u32, vp, vp, vp, sz, vp]
+    L.bm_bootstrap_arbitrary.restype = i32
     L.bm_status_str.argtypes = [i32]
     L.bm_status_str.restype = C.c_char_p
     _lib = L
@@ -311,6 +318,24 @@ def bm_key_switch(key: EvalKey, d_lwe_in, count: int, d_out, stream=None):
 def bm_poly_mul(key: EvalKey, d_a, d_b, count: int, d_out, stream=None):
     _check(load().bm_poly_mul(key.handle, _ptr(d_a), _ptr(d_b), count, _ptr(d_out), _stream(stream)),
            "bm_poly_mul")
+
+
+def bm_mod_switch(d_in, d_out, q_from: int, q_to: int, stream=None):
+    """Section 2 (9) on every word of d_in (device tensor) into d_out."""
+    _check(load().bm_mod_switch(_ptr(d_in), _ptr(d_out), d_in.numel(), q_from, q_to, _stream(stream)),
+           "bm_mod_switch")
+
+
+def bm_arbitrary_workspace_bytes(key: EvalKey, m: int, t: int, count: int) -> int:
+    return int(load().bm_arbitrary_workspace_bytes(key.handle, m, t, count))
+
+
+def bm_bootstrap_arbitrary(key: EvalKey, m: int, t: int, q: int, d_f, count: int, d_ct_in, d_ct_out,
+                           d_ws, stream=None):
+    """Two-round bootstrap of any f: Z_t -> Z_t (tables d_f, t entries each)."""
+    _check(load().bm_bootstrap_arbitrary(key.handle, m, t, q, _ptr(d_f), count, _ptr(d_ct_in),
+                                         _ptr(d_ct_out), _ptr(d_ws), d_ws.numel() * d_ws.element_size(),
+                                         _stream(stream)), "bm_bootstrap_arbitrary")
 
 
 def bm_workspace_status(d_ws, stream=None) -> int:

@@ -153,6 +153,57 @@ __global__ void k_poly_mul(const KeyDev *Kp, const u64 *__restrict__ a, const u6
     for (u32 i = threadIdx.x; i < N; i += blockDim.x) out[off + i] = sm[i];
 }
 
+// Modulus switch (Section 2 (9)) of every word: round half up.
+__global__ void k_mod_switch(const u64 *__restrict__ in, u64 *__restrict__ out, size_t words, u64 q_from,
+                             u64 q_to) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned __int128 x = (unsigned __int128)(in[i] % q_from) * q_to + q_from / 2;
+        out[i] = (u64)((x / q_from) % q_to);
+    }
+}
+
+// Tables of the two-round method over Z_{2t} (see bm_bootstrap_arbitrary):
+// mp (shared by all jobs) and, per job, the negacyclic extension F of f.
+__global__ void k_two_round_tables(const u32 *__restrict__ f, u32 t, u32 count, u32 *__restrict__ mp,
+                                   u32 *__restrict__ F) {
+    const u32 T = 2 * t;
+    const size_t total = (size_t)count * T;
+    for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < total + T;
+         w += (size_t)gridDim.x * blockDim.x) {
+        if (w < T) {
+            const u32 x = (u32)w;
+            mp[x] = (x < t / 2 || x >= 3 * t / 2) ? T - t / 2 : t / 2;
+            continue;
+        }
+        const size_t j = (w - T) / T;
+        const u32 y = (u32)((w - T) % T);
+        const u32 *fj = f + j * t;
+        u32 v;
+        if (y < t / 2) v = fj[y] % T;
+        else if (y >= 3 * t / 2) v = fj[y - t] % T;
+        else {
+            const u32 z = (y + t) % T;    // (y - t) mod 2t, in [0, t/2) or [3t/2, 2t)
+            const u32 fz = z < t / 2 ? fj[z] : fj[z - t];
+            v = (T - fz % T) % T;
+        }
+        F[j * T + y] = v;
+    }
+}
+
+// out = x - y mod q word by word, and add_b added to the last word (b) of
+// every ciphertext of n + 1 words.
+__global__ void k_lwe_sub(const u64 *__restrict__ x, const u64 *__restrict__ y, u64 *__restrict__ out,
+                          size_t count, u32 n, u64 q, u64 add_b) {
+    const size_t words = count * (n + 1);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+         i += (size_t)gridDim.x * blockDim.x) {
+        u64 v = sub_mod(x[i] % q, y[i] % q, q);
+        if (i % (n + 1) == n) v = add_mod(v, add_b, q);
+        out[i] = v;
+    }
+}
+
 // Throughput probe: independent Shoup multiplication chains per thread.
 __global__ void k_modmul_probe(u64 *out, u32 iters, u64 Q, u64 w, u64 wsh) {
     u64 x0 = threadIdx.x + 1, x1 = x0 + 7, x2 = x0 + 13, x3 = x0 + 29;
@@ -555,6 +606,90 @@ extern "C" bm_status bm_poly_mul(const bm_eval_key *key, const uint64_t *d_a, co
     k_poly_mul<<<count, N / 2 < 512 ? N / 2 : 512, smem, (cudaStream_t)stream>>>(key->d_view, d_a, d_b, d_out);
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
+}
+
+extern "C" bm_status bm_mod_switch(const uint64_t *d_in, uint64_t *d_out, size_t words, uint64_t q_from,
+                                   uint64_t q_to, void *stream) {
+    if (q_from < 2 || q_to < 2 || (words && (!d_in || !d_out))) return BM_EINVAL;
+    if (!words) return BM_OK;
+    const size_t blocks = (words + 255) / 256 < 65535 ? (words + 255) / 256 : 65535;
+    k_mod_switch<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d_in, d_out, words, q_from, q_to);
+    BM_CUDA_TRY(cudaGetLastError());
+    return BM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Arbitrary functions by two rounds (Section 4, last part)
+// ---------------------------------------------------------------------------
+
+namespace {
+struct ArbLayout {
+    size_t ws_bs, a, b, c, mp, F, total;
+};
+
+ArbLayout arb_layout(const bm_eval_key *key, uint32_t m, uint32_t t, uint32_t count) {
+    ArbLayout L{};
+    std::vector<bm_job> jobs(count);
+    for (uint32_t i = 0; i < count; i++)
+        jobs[i] = bm_job{0, m, 2 * t, 0, (uint64_t)i * (key->p.n + 1), 0, (uint64_t)i * (key->p.n + 1)};
+    const bm_eval_key *keys[1] = {key};
+    Plan pl;
+    make_plan(keys, jobs.data(), count, pl);
+    const size_t W = (size_t)count * (key->p.n + 1) * 8;
+    L.ws_bs = align_up(pl.total, 256);
+    L.a = L.ws_bs;
+    L.b = L.a + align_up(W, 256);
+    L.c = L.b + align_up(W, 256);
+    L.mp = L.c + align_up(W, 256);
+    L.F = L.mp + align_up((size_t)2 * t * 4, 256);
+    L.total = L.F + align_up((size_t)count * 2 * t * 4, 256);
+    return L;
+}
+}  // namespace
+
+extern "C" size_t bm_arbitrary_workspace_bytes(const bm_eval_key *key, uint32_t m, uint32_t t, uint32_t count) {
+    if (!key || !count || m < 1 || m > BM_MAX_M || t < 2 || (t & 1)) return 0;
+    return arb_layout(key, m, t, count).total;
+}
+
+extern "C" bm_status bm_bootstrap_arbitrary(const bm_eval_key *key, uint32_t m, uint32_t t, uint64_t q,
+                                            const uint32_t *d_f, uint32_t count, const uint64_t *d_ct_in,
+                                            uint64_t *d_ct_out, void *d_ws, size_t ws_bytes, void *stream) {
+    if (!key || !d_f || !d_ct_in || !d_ct_out || !d_ws || ((uintptr_t)d_ws & 255)) return BM_EINVAL;
+    if (!count) return BM_OK;
+    const uint64_t qp = 2ull * key->p.N * m;
+    if (m < 1 || m > BM_MAX_M || t < 2 || (t & 1) || 2ull * t > qp || q < 2ull * t || q >= key->p.Q)
+        return BM_EINVAL;
+    const ArbLayout L = arb_layout(key, m, t, count);
+    if (ws_bytes < L.total) return BM_EWORKSPACE;
+    DeviceGuard g(key->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)d_ws;
+    const u32 n = key->p.n, T = 2 * t;
+    const size_t words = (size_t)count * (n + 1);
+    u64 *A = (u64 *)(ws + L.a), *B = (u64 *)(ws + L.b), *Cb = (u64 *)(ws + L.c);
+    u32 *mp = (u32 *)(ws + L.mp), *F = (u32 *)(ws + L.F);
+    const unsigned blocks = (unsigned)((words + 255) / 256 < 4096 ? (words + 255) / 256 : 4096);
+    k_two_round_tables<<<blocks, 256, 0, st>>>(d_f, t, count, mp, F);
+    BM_CUDA_TRY(cudaGetLastError());
+    std::vector<bm_job> jobs(count);
+    for (uint32_t i = 0; i < count; i++)
+        jobs[i] = bm_job{0, m, T, 0, (uint64_t)i * (n + 1), 0, (uint64_t)i * (n + 1)};
+    const bm_eval_key *keys[1] = {key};
+    bm_status s;
+    // round 1: the top bit, mp over Z_{2t}
+    if ((s = bm_mod_switch(d_ct_in, A, words, q, qp, stream)) != BM_OK) return s;
+    if ((s = bm_bootstrap_batch(keys, 1, jobs.data(), count, A, mp, B, d_ws, L.ws_bs, stream)) != BM_OK) return s;
+    if ((s = bm_mod_switch(B, B, words, key->p.Q, q, stream)) != BM_OK) return s;
+    // y = x - (mp(x) + t/2): subtract the round-1 output and t/2 floor(q/2t)
+    const u64 half = (u64)((unsigned __int128)(t / 2) * (q / T) % q);
+    k_lwe_sub<<<blocks, 256, 0, st>>>(d_ct_in, B, Cb, count, n, q, half ? q - half : 0);
+    BM_CUDA_TRY(cudaGetLastError());
+    // round 2: f's negacyclic extension, one table per job
+    if ((s = bm_mod_switch(Cb, A, words, q, qp, stream)) != BM_OK) return s;
+    for (uint32_t i = 0; i < count; i++) jobs[i].lut_off = (uint64_t)i * T;
+    if ((s = bm_bootstrap_batch(keys, 1, jobs.data(), count, A, F, B, d_ws, L.ws_bs, stream)) != BM_OK) return s;
+    return bm_mod_switch(B, d_ct_out, words, key->p.Q, q, stream);
 }
 
 extern "C" bm_status bm_workspace_status(void *d_ws, void *stream) {

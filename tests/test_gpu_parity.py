@@ -382,3 +382,67 @@ def test_batch_graph_replay_matches_direct_path(api, orc, n1024, flags):
         assert np.array_equal(api.from_device_u64(d_out), ref)
     assert api.bm_workspace_status(ws) == 0
     b.free()
+
+
+# --- modulus switches and the full Algorithm 1 ----------------------------------------
+
+def test_mod_switch_matches_oracle(api, orc, toy):
+    rng = np.random.default_rng(31)
+    for q_from, q_to in [(1 << 14, 1024), (toy.kp.Q, 1 << 14), (18014359854776321, 8192), (1000003, 999983)]:
+        x = rng.integers(0, q_from, 4099, dtype=np.uint64)
+        x[:4] = [0, q_from - 1, q_from // 2, (q_from + 1) // 2]
+        d_in = api.to_device_u64(x)
+        d_out = torch.zeros_like(d_in)
+        api.bm_mod_switch(d_in, d_out, q_from, q_to)
+        torch.cuda.synchronize()
+        assert np.array_equal(api.from_device_u64(d_out), orc.mod_switch(x, q_from, q_to))
+
+
+def test_full_algorithm1_with_both_modulus_switches(api, orc, toy):
+    """Algorithm 1 end to end on the toy keys with q = 2^14, t = 8: switch
+    q -> 2Nm = 1024, bootstrap, switch Q -> q; every message decrypts to f(msg)
+    at the input modulus, and the device output equals the oracle's bits."""
+    kp, m, t, q = toy.kp, 2, 8, 1 << 14
+    qp = 2 * kp.N * m
+    msg = np.arange(t, dtype=np.uint32)
+    enc = synth.encryption_randomness(kp.n, q, kp.sigma, t, 4040)
+    ct = orc.encrypt(kp.n, q, t, toy.rnd["s"], msg, enc["mask"], enc["err"])
+    luts, _ = synth.luts(t, t, 2040)
+    jobs = _uniform_jobs(api, t, kp.n, t, m)
+    d_ct = api.to_device_u64(ct.ravel())
+    d_sw = torch.zeros_like(d_ct)
+    api.bm_mod_switch(d_ct, d_sw, q, qp)
+    d_out = torch.zeros(t * (kp.n + 1), dtype=torch.int64, device="cuda")
+    ws = api.workspace(api.bm_workspace_bytes([toy.ek], jobs))
+    api.bm_bootstrap_batch([toy.ek], jobs, d_sw, api.to_device_u32(luts.ravel()), d_out, ws)
+    d_fin = torch.zeros_like(d_out)
+    api.bm_mod_switch(d_out, d_fin, kp.Q, q)
+    torch.cuda.synchronize()
+    got = api.from_device_u64(d_fin).reshape(t, kp.n + 1)
+    sw = orc.mod_switch(ct, q, qp)
+    want = orc.mod_switch(orc.bootstrap(kp, m, t, toy.bsk, toy.ksk, sw, luts), kp.Q, q)
+    assert np.array_equal(got, want)
+    assert np.array_equal(api.bm_decrypt(toy.sk, q, t, got), luts[np.arange(t), msg])
+
+
+def test_two_round_arbitrary_function_matches_oracle(api, orc, toy):
+    """Non-negacyclic f by two rounds (one table per ciphertext), inputs with
+    either top bit: bit-exact with the oracle, decrypting to f(x mod t)."""
+    kp, m, t, q = toy.kp, 2, 4, 1 << 14
+    T = 2 * t
+    cnt = 2 * T
+    x = np.tile(np.arange(T, dtype=np.uint32), 2)
+    rng = np.random.default_rng(91)
+    f = rng.integers(0, t, (cnt, t)).astype(np.uint32)
+    f[0] = np.arange(t)                                 # identity
+    enc = synth.encryption_randomness(kp.n, q, kp.sigma, cnt, 4091)
+    ct = orc.encrypt(kp.n, q, T, toy.rnd["s"], x, enc["mask"], enc["err"])
+    d_in = api.to_device_u64(ct.ravel())
+    d_out = torch.zeros_like(d_in)
+    ws = api.workspace(api.bm_arbitrary_workspace_bytes(toy.ek, m, t, cnt))
+    api.bm_bootstrap_arbitrary(toy.ek, m, t, q, api.to_device_u32(f.ravel()), cnt, d_in, d_out, ws)
+    torch.cuda.synchronize()
+    assert api.bm_workspace_status(ws) == 0
+    got = api.from_device_u64(d_out).reshape(cnt, kp.n + 1)
+    assert np.array_equal(got, orc.bootstrap_arbitrary(kp, m, t, q, toy.bsk, toy.ksk, ct, f))
+    assert np.array_equal(api.bm_decrypt(toy.sk, q, T, got), f[np.arange(cnt), x % t])

@@ -239,3 +239,71 @@ def test_prefix_blind_rotation_skips_zero_steps(orc):
     assert np.array_equal(full, part)
     with pytest.raises(ValueError):
         orc.blind_rotate(kp, m, t, bsk[:4], ct[0], lut)
+
+
+def test_mod_switch_identity_and_phase_bound(orc):
+    """Section 2 (9): switching q -> q' rounds each word, so the phase moves
+    to phase q'/q up to (|s|_1 + 1)/2 (one rounding of at most 1/2 per term)."""
+    rng = np.random.default_rng(21)
+    n, q = 64, 1 << 14
+    s = rng.integers(-1, 2, n, dtype=np.int8)
+    ct = rng.integers(0, q, (50, n + 1), dtype=np.uint64)
+    assert np.array_equal(orc.mod_switch(ct, q, q), ct)
+    bound = (np.abs(s.astype(int)).sum() + 1) / 2
+    for qp in (1024, 4096, 1 << 13):
+        sw = orc.mod_switch(ct, q, qp)
+        assert int(sw.max()) < qp
+        for i in range(len(ct)):
+            ph = orc.lwe_phase(n, q, s, ct[i])
+            ph2 = orc.lwe_phase(n, qp, s, sw[i])
+            d = (ph2 - ph * qp / q) % qp
+            d = d - qp if d > qp / 2 else d
+            assert abs(d) <= bound + 1e-9
+
+
+def test_mod_switch_keeps_messages(orc):
+    kp = P.KEYS_TOY
+    s = synth.lwe_secret(kp, 7)
+    q, t, qp = 1 << 14, 8, 1024
+    msg = synth.messages(t, 200, 9)
+    enc = synth.encryption_randomness(kp.n, q, kp.sigma, 200, 10)
+    ct = orc.encrypt(kp.n, q, t, s, msg, enc["mask"], enc["err"])
+    assert np.array_equal(orc.decrypt(kp.n, qp, t, s, orc.mod_switch(ct, q, qp)), msg)
+
+
+def test_two_round_tables(orc):
+    """mp is negacyclic with sign(x) t = mp(x) + t/2 (Eqs. (rel:mp), (rel:sign));
+    F is negacyclic over Z_{2t} and equals f(y mod t) on y in [-t/2, t/2)."""
+    rng = np.random.default_rng(8)
+    for t in (4, 8, 16, 32):
+        T = 2 * t
+        f = rng.integers(0, t, t).astype(np.uint32)
+        mp, F = orc.two_round_tables(t, f)
+        for x in range(T):
+            xs = x if x < t else x - T                      # representative in [-t, t)
+            sign = 0 if -t // 2 <= xs < t // 2 else 1
+            assert (int(mp[x]) + t // 2) % T == sign * t
+            assert int(mp[(x + t) % T]) == (T - int(mp[x])) % T
+            assert int(F[(x + t) % T]) == (T - int(F[x])) % T
+        for y in range(-t // 2, t // 2):
+            assert int(F[y % T]) == int(f[y % t])
+
+
+@pytest.mark.parametrize("fname", ["identity", "random", "constant"])
+def test_two_round_bootstrap_any_function(orc, fname):
+    """Section 4 (last part): with the two rounds every x in Z_{2t} (m = x mod t,
+    any top bit) bootstraps to f(m) for f that need not be negacyclic."""
+    kp = P.KEYS_TOY
+    rnd = synth.key_randomness(kp, 1001)
+    bsk = orc.keygen_bsk(kp, rnd)
+    ksk = orc.keygen_ksk(kp, rnd)
+    q, t, m = 1 << 14, 4, 2
+    T = 2 * t
+    f = {"identity": np.arange(t), "random": np.array([2, 3, 0, 3]),
+         "constant": np.full(t, 1)}[fname].astype(np.uint32)
+    x = np.arange(T, dtype=np.uint32)
+    enc = synth.encryption_randomness(kp.n, q, kp.sigma, T, 78)
+    ct = orc.encrypt(kp.n, q, T, rnd["s"], x, enc["mask"], enc["err"])
+    tables = np.stack([f] * T) + np.arange(T)[:, None].astype(np.uint32) * 0
+    out = orc.bootstrap_arbitrary(kp, m, t, q, bsk, ksk, ct, tables)
+    assert np.array_equal(orc.decrypt(kp.n, q, T, rnd["s"], out), f[x % t])
