@@ -310,8 +310,24 @@ def run_gpu(args, w):
             b.record(stream)
             torch.cuda.synchronize(dev)
             pv = P_ / (a.elapsed_time(b) * 1e-3)
+            # the same with one block per job (no thread-block cluster over the rows)
+            P1 = min(8, P_)
+            d_out1 = torch.zeros_like(d_out)
+            one = [api.Batch([ek], j1[i], d_in, d_lut, d_out1, ws, api.BATCH_ONE_BLOCK) for i in range(P1)]
+            one[0].run(stream)
+            torch.cuda.synchronize(dev)
+            a.record(stream)
+            for bt in one:
+                bt.run(stream)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            pv1 = P1 / (a.elapsed_time(b) * 1e-3)
+            for bt in one:
+                bt.free()
             result["plain"] = {"value": pv, "unit": "bootstraps/s", "ciphertexts": P_,
-                               "batched_over_plain": value / pv}
+                               "batched_over_plain": value / pv,
+                               "launch": "one job per launch, rows split over a thread-block cluster",
+                               "one_block_per_job": {"value": pv1, "ciphertexts": P1}}
         # end to end through the host-buffer C-ABI call (pinned host memory)
         h_in = torch.from_numpy(ct.ravel().view(np.int64)).pin_memory()
         h_lut = torch.from_numpy(luts.ravel().view(np.int32)).pin_memory()

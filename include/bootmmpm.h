@@ -199,12 +199,19 @@ bm_status bm_poly_mul(const bm_eval_key *key, const uint64_t *d_a,
  *                        mixes of key sets and shapes run as one launch;
  *   BM_BATCH_GRAPH       the first run records the launches in a CUDA graph
  *                        on `stream` (which must not be the legacy default
- *                        stream) and later runs replay it.
+ *                        stream) and later runs replay it;
+ *   BM_BATCH_ONE_BLOCK   every job runs on one block.  Without it (and in
+ *                        bm_bootstrap_batch), a launch of fewer jobs than the
+ *                        GPU holds gives each job a thread-block cluster of
+ *                        up to 8 blocks that split its m rows (the rows of one
+ *                        CMux step are independent, Eq. (ex1:BPc)), which cuts
+ *                        the latency of small batches; results are identical.
  * The buffers and the workspace stay bound to the batch until bm_batch_free;
  * runs of one batch must not overlap on the GPU (they share the workspace). */
 typedef struct bm_batch bm_batch;
 #define BM_BATCH_PERSISTENT 1u
 #define BM_BATCH_GRAPH 2u
+#define BM_BATCH_ONE_BLOCK 4u
 bm_status bm_batch_create(const bm_eval_key *const *keys, uint32_t n_keys,
                           const bm_job *jobs, uint32_t count,
                           const uint64_t *d_ct_in, const uint32_t *d_lut,

@@ -32,6 +32,7 @@ SYMBOLS = ["bm_keygen", "bm_free_secret_key", "bm_free_eval_key", "bm_eval_key_b
 
 BATCH_PERSISTENT = 1
 BATCH_GRAPH = 2
+BATCH_ONE_BLOCK = 4
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
 

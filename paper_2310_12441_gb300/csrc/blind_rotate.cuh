@@ -10,13 +10,38 @@
 // Device helpers
 // ---------------------------------------------------------------------------
 
+// Load of an accumulator word.  Rows written by other blocks of a cluster are
+// read at L2 (ld.global.cg), never from this SM's L1.
+__device__ __forceinline__ u64 acc_load(const u64 *p, bool l2) { return l2 ? __ldcg(p) : *p; }
+
 // Coefficient `c` of x^e * p in R_{N,Q}, e in [0, 2N).
-__device__ __forceinline__ u64 rotated_coeff(const u64 *p, u32 c, u32 e, u32 N, u64 Q) {
+__device__ __forceinline__ u64 rotated_coeff(const u64 *p, u32 c, u32 e, u32 N, u64 Q, bool l2 = false) {
     u32 j = c + 2 * N - e;
     if (j >= 2 * N) j -= 2 * N;
-    if (j < N) return p[j];
-    const u64 v = p[j - N];
+    if (j < N) return acc_load(p + j, l2);
+    const u64 v = acc_load(p + j - N, l2);
     return v ? Q - v : 0;
+}
+
+// Rank of this block in its thread-block cluster and the cluster's size (0
+// and 1 for a launch without clusters).
+__device__ __forceinline__ u32 cluster_rank() {
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ u32 cluster_size() {
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// Barrier over every thread of every block of the cluster; writes before it
+// (global memory included) are visible to all of them after it.  Every
+// block arrives once per CMux step, so no block can wait for one that has
+// left: the blocks of a cluster run the same job and the same step count.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void set_status(u32 *status, bm_status code) {
@@ -41,8 +66,9 @@ static __device__ bool lut_is_negacyclic(const u32 *__restrict__ lut, u32 t) {
 // ACC <- P(b) (0, v_test floor(Q/t)), v_test of Eq. (equ:test-use):
 // row i, coefficient a of v_test is f'(-(a m + i) mod 2Nm), with the
 // negacyclic extension f'(u) = f(floor((u t + Nm) / 2Nm) mod t).
+// Rows i with i mod rows_step == row0 only (the rows of one block of a cluster).
 static __device__ void acc_init(u64 *__restrict__ acc, const u32 *__restrict__ lut, u64 b, u32 m, u32 t,
-                         u32 N, u64 Q) {
+                         u32 N, u64 Q, u32 row0 = 0, u32 rows_step = 1) {
     const u64 qp = 2ull * N * m;
     const u64 dq = Q / t;
     const u32 ea = (u32)(b / m), bb = (u32)(b % m);
@@ -50,6 +76,7 @@ static __device__ void acc_init(u64 *__restrict__ acc, const u32 *__restrict__ l
         const u32 c = idx % N;
         const u32 comp = (idx / N) & 1;
         const u32 i = idx / (2 * N);
+        if (i % rows_step != row0) continue;
         u64 val = 0;
         if (comp == 1) {
             const u32 src = i >= bb ? i - bb : i + m - bb;
@@ -104,6 +131,11 @@ struct Cfg {
 
 // Blind rotation of one job by the whole block (all threads must call it).
 // sm: C::SMEM bytes of shared memory.  Variant flags: see choose_variant().
+// Launched in thread-block clusters of S blocks per job, block s of the
+// cluster takes the rows r = s mod S: the rows of a step only read the
+// previous accumulator, so they are independent, and one cluster barrier per
+// step orders the accumulator updates (rows S times fewer per block, so the
+// job's latency drops by up to S; the work is the same).
 //
 // A CMux step handles the m rows G at a time.  For a group of rows, the
 // 4 l_B digit polynomials per row ("combos": sign x component x digit) are
@@ -140,13 +172,18 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     const u64 *ct = ct_in + J.in_off;
     const u32 *lut = luts + J.lut_off;
 
+    // row split over the blocks of a cluster (1 block: all rows)
+    const u32 crank = cluster_rank(), csize = cluster_size();
+    const bool split = csize > 1;
     if (!lut_is_negacyclic(lut, t)) {
-        if (tid == 0) set_status(status, BM_ENONNEGACYCLIC);
-        for (u32 idx = tid; idx < 2 * vec; idx += blockDim.x) acc0[idx] = 0;
+        // every block of the cluster sees the same table and leaves here
+        if (tid == 0 && crank == 0) set_status(status, BM_ENONNEGACYCLIC);
+        for (u32 idx = tid; idx < 2 * vec; idx += blockDim.x)
+            if ((idx / (2 * N)) % m % csize == crank) acc0[idx] = 0;
         return;
     }
-    acc_init(acc0, lut, ct[n] % qp, m, t, N, Q);
-    __syncthreads();
+    acc_init(acc0, lut, ct[n] % qp, m, t, N, Q, crank, csize);
+    if (split) cluster_sync(); else __syncthreads();
 
     const u32 p = tid / C::T;          // polynomial slot within a batch
     const u32 l = tid % C::T;          // thread within the polynomial
@@ -171,7 +208,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     for (u32 k = 0; k < steps; k++) {
         const u32 ak = (u32)(ct[k] % qp);
         const u64 *bsk_k = K->bsk + (size_t)k * 2 * rgsw;
-        for (u32 r0 = 0; r0 < m; r0 += G) {
+        for (u32 r0 = crank * G; r0 < m; r0 += G * csize) {
             u64 lo[G][2][C::PPT], hi[G][2][C::PPT];
 #pragma unroll
             for (int g = 0; g < G; g++)
@@ -200,7 +237,8 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                         const u32 sgn = pair >> 1, comp = pair & 1;
                         const u64 *srow = cur + ((size_t)rsrc[g][sgn] * 2 + comp) * N;
                         const u64 *orow = cur + ((size_t)r * 2 + comp) * N;
-                        dbuf[w] = sub_mod(rotated_coeff(srow, idx, rexp[g][sgn], N, Q), orow[idx], Q);
+                        dbuf[w] = sub_mod(rotated_coeff(srow, idx, rexp[g][sgn], N, Q, split),
+                                          acc_load(orow + idx, split), Q);
                     }
                 }
                 __syncthreads();
@@ -223,7 +261,8 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
 #pragma unroll
                         for (int i = 0; i < 16; i++) {
                             const u32 idx = l + C::T * i;
-                            const u64 D = sub_mod(rotated_coeff(srow, idx, rexp[pg][sgn], N, Q), orow[idx], Q);
+                            const u64 D = sub_mod(rotated_coeff(srow, idx, rexp[pg][sgn], N, Q, split),
+                                                  acc_load(orow + idx, split), Q);
                             x[i] = (D >> sh) & Bmask;
                         }
                     }
@@ -313,10 +352,13 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
             }
         }
         __syncthreads();
-        // --- inverse transforms of the 2m row sums, ACC update
-        for (u32 u0 = 0; u0 < 2 * m; u0 += C::P) {
-            const u32 u = u0 + p;
-            const bool active = u < 2 * m;
+        // --- inverse transforms of this block's 2 mr row sums (rows crank +
+        // csize i), ACC update
+        const u32 mr = crank < m ? (m - 1 - crank) / csize + 1 : 0;
+        for (u32 u0 = 0; u0 < 2 * mr; u0 += C::P) {
+            const u32 ui = u0 + p;
+            const bool active = ui < 2 * mr;
+            const u32 u = 2 * (crank + csize * (ui >> 1)) + (ui & 1);
             u64 x[16];
             u64 *in = sw.take();
             if (active) {
@@ -338,7 +380,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 }
             }
         }
-        __syncthreads();
+        if (split) cluster_sync(); else __syncthreads();
         u64 *tmp = cur;
         cur = nxt;
         nxt = tmp;

@@ -336,8 +336,9 @@ __global__ void __launch_bounds__(group_threads<LOGN>(), 512 / group_threads<LOG
     k_blind_rotate(const DevJob *__restrict__ jobs, u32 steps_limit, const u64 *__restrict__ ct_in,
                    const u32 *__restrict__ luts, u64 *ws, u32 *status) {
     extern __shared__ u64 sm[];
-    brk::br_job<LOGN, group_threads<LOGN>(), LAZY, SMALL0, QLOW1>(jobs[blockIdx.x], steps_limit, ct_in, luts,
-                                                                   ws, status, sm);
+    // a cluster of blocks shares one job (rows split); plain launches: 1 block
+    brk::br_job<LOGN, group_threads<LOGN>(), LAZY, SMALL0, QLOW1>(jobs[blockIdx.x / cluster_size()],
+                                                                   steps_limit, ct_in, luts, ws, status, sm);
 }
 
 // Sets the dynamic shared-memory limit of a kernel once per device.
@@ -353,25 +354,100 @@ bm_status ensure_smem(K kern, size_t smem, std::atomic<uint64_t> &done) {
     return BM_OK;
 }
 
-// dry: only set the kernel's attributes (done before a CUDA-graph capture).
+// Blocks per job (thread-block cluster size, rows split) for a launch of
+// `cnt` jobs of at most `mmax` rows: the smallest S in {1, 2, 4, 8}, S <=
+// min(mmax, max_cluster), that minimises waves(S) x ceil(mmax / S), where
+// waves(S) = ceil(cnt / clusters resident at once).  A full batch keeps one
+// block per job; a batch of fewer jobs than SMs spreads each job's rows over
+// a cluster, cutting its latency by up to S.
+template <typename K>
+u32 pick_cluster(K kern, u32 threads, size_t smem, u32 cnt, u32 mmax, u32 max_cluster) {
+    struct Occ { const void *k; u32 s; int dev; int slots; };
+    static std::mutex mu;
+    static std::vector<Occ> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    auto slots = [&](u32 S) -> int {
+        std::lock_guard<std::mutex> lk(mu);
+        for (const Occ &o : cache)
+            if (o.k == (const void *)kern && o.s == S && o.dev == dev) return o.slots;
+        int n = 0;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(S);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = S;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        cache.push_back({(const void *)kern, S, dev, n});
+        return n;
+    };
+    u32 best = 1;
+    const int s1 = slots(1);
+    if (s1 <= 0) return 1;
+    u64 best_cost = (u64)((cnt + s1 - 1) / s1) * mmax;
+    for (u32 S = 2; S <= 8 && S <= max_cluster && S <= mmax; S *= 2) {
+        const int sl = slots(S);
+        if (sl <= 0) break;
+        const u64 cost = (u64)((cnt + sl - 1) / sl) * ((mmax + S - 1) / S);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = S;
+        }
+    }
+    return best;
+}
+
+// dry: only set the kernel's attributes and occupancy (done before a
+// CUDA-graph capture).
 template <int LOGN, bool LAZY, bool SMALL0, bool QLOW1>
-bm_status launch_br_v(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 steps, const uint64_t *ct_in,
-                      const uint32_t *lut, u64 *ws_acc, u32 *status, cudaStream_t st, bool dry) {
+bm_status launch_br_v(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 mmax, u32 max_cluster, u32 steps,
+                      const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status, cudaStream_t st,
+                      bool dry) {
     using C = brk::Cfg<LOGN, group_threads<LOGN>()>;
     static std::atomic<uint64_t> attr_done{0};
     auto kern = k_blind_rotate<LOGN, LAZY, SMALL0, QLOW1>;
     bm_status s = ensure_smem(kern, C::SMEM, attr_done);
-    if (s != BM_OK || dry) return s;
-    kern<<<cnt, C::kThreads, C::SMEM, st>>>(d_jobs + first, steps, ct_in, lut, ws_acc, status);
+    if (s != BM_OK) return s;
+    const u32 S = max_cluster > 1 ? pick_cluster(kern, C::kThreads, C::SMEM, cnt, mmax, max_cluster) : 1;
+    if (dry) return BM_OK;
+    const DevJob *jobs = d_jobs + first;
+    if (S == 1) {
+        kern<<<cnt, C::kThreads, C::SMEM, st>>>(jobs, steps, ct_in, lut, ws_acc, status);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cnt * S);
+        cfg.blockDim = dim3(C::kThreads);
+        cfg.dynamicSmemBytes = C::SMEM;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = S;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        BM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, jobs, steps, ct_in, lut, ws_acc, status));
+    }
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
 }
 
 template <int LOGN>
-bm_status launch_br(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 steps, const uint64_t *ct_in,
-                    const uint32_t *lut, u64 *ws_acc, u32 *status, u32 variant, cudaStream_t st, bool dry) {
-#define BM_LAUNCH(LZ, S0, QL) \
-    return launch_br_v<LOGN, LZ, S0, QL>(d_jobs, first, cnt, steps, ct_in, lut, ws_acc, status, st, dry)
+bm_status launch_br(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 mmax, u32 max_cluster, u32 steps,
+                    const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status, u32 variant,
+                    cudaStream_t st, bool dry) {
+#define BM_LAUNCH(LZ, S0, QL)                                                                          \
+    return launch_br_v<LOGN, LZ, S0, QL>(d_jobs, first, cnt, mmax, max_cluster, steps, ct_in, lut, ws_acc, \
+                                         status, st, dry)
     switch (variant) {
         case BR_V_LAZY | BR_V_QLOW1: BM_LAUNCH(true, true, true);
         case BR_V_LAZY: BM_LAUNCH(true, true, false);
@@ -381,10 +457,11 @@ bm_status launch_br(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 step
 #undef BM_LAUNCH
 }
 
-// Blind rotation of jobs [first, last) of the plan, one block per job, one
-// launch per run of equal ring degree and variant.
+// Blind rotation of jobs [first, last) of the plan, one launch per run of
+// equal ring degree and variant; each job takes one block, or a cluster of up
+// to max_cluster blocks when the run has fewer jobs than the GPU has room for.
 bm_status run_groups(const Plan &pl, uint32_t first, uint32_t last, u32 steps, const uint64_t *d_ct_in,
-                     const uint32_t *d_lut, char *ws, cudaStream_t st, bool dry) {
+                     const uint32_t *d_lut, char *ws, cudaStream_t st, bool dry, u32 max_cluster) {
     const DevJob *d_jobs = (const DevJob *)(ws + pl.jobs_off);
     u64 *ws_acc = (u64 *)(ws + pl.acc_off_bytes);
     u32 *status = (u32 *)ws;
@@ -392,10 +469,16 @@ bm_status run_groups(const Plan &pl, uint32_t first, uint32_t last, u32 steps, c
     while (i < last) {
         const u32 N = pl.dj[i].N;
         const u32 variant = pl.dj[i].variant;
+        u32 mmax = pl.dj[i].m;
         uint32_t j = i + 1;
-        while (j < last && pl.dj[j].N == N && pl.dj[j].variant == variant) j++;
+        while (j < last && pl.dj[j].N == N && pl.dj[j].variant == variant) {
+            mmax = pl.dj[j].m > mmax ? pl.dj[j].m : mmax;
+            j++;
+        }
         bm_status s = BM_OK;
-#define BM_GRP(L) s = launch_br<L>(d_jobs, i, j - i, steps, d_ct_in, d_lut, ws_acc, status, variant, st, dry)
+#define BM_GRP(L)                                                                                       \
+    s = launch_br<L>(d_jobs, i, j - i, mmax, max_cluster, steps, d_ct_in, d_lut, ws_acc, status, variant, st, \
+                     dry)
         switch (N) {
             case 256: BM_GRP(8); break;
             case 512: BM_GRP(9); break;
@@ -436,9 +519,12 @@ KsShape ks_shape(const bm_eval_key *const *keys, uint32_t n_keys) {
 }
 
 // Every launch of one batch (the plan is already in the workspace).
+// Largest thread-block cluster (blocks per job) a grouped launch may use.
+constexpr u32 kMaxCluster = 8;
+
 bm_status launch_all(const Plan &pl, uint32_t n_persistent, const KsShape &ks, int device, u32 steps, bool do_ks,
                      const uint64_t *d_ct_in, const uint32_t *d_lut, uint64_t *d_out, char *ws,
-                     cudaStream_t st) {
+                     cudaStream_t st, u32 max_cluster = kMaxCluster) {
     const uint32_t count = (uint32_t)pl.dj.size();
     const DevJob *d_jobs = (const DevJob *)(ws + pl.jobs_off);
     u64 *ws_acc = (u64 *)(ws + pl.acc_off_bytes);
@@ -448,7 +534,8 @@ bm_status launch_all(const Plan &pl, uint32_t n_persistent, const KsShape &ks, i
                                     (u32 *)ws + BM_WS_COUNTER_WORD, device, st);
         if (s != BM_OK) return s;
     }
-    if ((s = run_groups(pl, n_persistent, count, steps, d_ct_in, d_lut, ws, st, false)) != BM_OK) return s;
+    if ((s = run_groups(pl, n_persistent, count, steps, d_ct_in, d_lut, ws, st, false, max_cluster)) != BM_OK)
+        return s;
     if (do_ks) {
         k_extract_keyswitch<<<count, ks.threads, ks.smem, st>>>(d_jobs, steps, ws_acc, d_out);
     } else {
@@ -744,13 +831,14 @@ struct bm_batch {
     uint64_t *d_out;
     char *ws;
     cudaGraphExec_t exec;
+    u32 max_cluster() const { return (flags & BM_BATCH_ONE_BLOCK) ? 1u : kMaxCluster; }
 };
 
 extern "C" bm_status bm_batch_create(const bm_eval_key *const *keys, uint32_t n_keys, const bm_job *jobs,
                                      uint32_t count, const uint64_t *d_ct_in, const uint32_t *d_lut,
                                      uint64_t *d_ct_out, void *d_ws, size_t ws_bytes, uint32_t flags,
                                      bm_batch **out) {
-    if (!out || (flags & ~(BM_BATCH_PERSISTENT | BM_BATCH_GRAPH))) return BM_EINVAL;
+    if (!out || (flags & ~(BM_BATCH_PERSISTENT | BM_BATCH_GRAPH | BM_BATCH_ONE_BLOCK))) return BM_EINVAL;
     int dev = 0;
     bm_status s = validate_jobs(keys, n_keys, jobs, count, &dev);
     if (s != BM_OK) return s;
@@ -777,7 +865,7 @@ extern "C" bm_status bm_batch_create(const bm_eval_key *const *keys, uint32_t n_
     if (e == cudaSuccess) e = cudaMemset(b->ws, 0, BM_WS_HEADER);
     // kernel attributes are set now, outside any later stream capture
     if (e == cudaSuccess && run_groups(b->pl, b->n_persistent, count, 0, nullptr, nullptr, b->ws, nullptr,
-                                       true) != BM_OK)
+                                       true, b->max_cluster()) != BM_OK)
         e = cudaErrorUnknown;
     if (e == cudaSuccess && b->n_persistent && bm_prepare_persistent_br(dev) != BM_OK) e = cudaErrorUnknown;
     if (e != cudaSuccess) {
@@ -794,13 +882,13 @@ extern "C" bm_status bm_batch_run(bm_batch *b, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (!(b->flags & BM_BATCH_GRAPH))
         return launch_all(b->pl, b->n_persistent, b->ks, b->device, 0xffffffffu, true, b->d_ct_in, b->d_lut,
-                          b->d_out, b->ws, st);
+                          b->d_out, b->ws, st, b->max_cluster());
     if (!st) return BM_EINVAL;   // the legacy default stream cannot be captured
     if (!b->exec) {
         cudaGraph_t graph = nullptr;
         BM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         bm_status s = launch_all(b->pl, b->n_persistent, b->ks, b->device, 0xffffffffu, true, b->d_ct_in,
-                                 b->d_lut, b->d_out, b->ws, st);
+                                 b->d_lut, b->d_out, b->ws, st, b->max_cluster());
         cudaError_t e = cudaStreamEndCapture(st, &graph);
         if (s != BM_OK) {
             if (graph) cudaGraphDestroy(graph);

@@ -384,6 +384,38 @@ def test_batch_graph_replay_matches_direct_path(api, orc, n1024, flags):
     b.free()
 
 
+def test_cluster_row_split_equals_one_block(api, orc, n1024, n2048):
+    """A small batch spreads each job's rows over a thread-block cluster (up to
+    8 blocks, ragged row counts, blocks with no row); one block per job
+    (BATCH_ONE_BLOCK) and the oracle give the same bits."""
+    shapes = [(1, 8, 8192), (0, 3, 768), (1, 2, 2048), (0, 5, 1280), (0, 1, 256), (1, 6, 6144),
+              (0, 4, 1024)]
+    jobs, ct, luts, want, out_words = _mixed_batch(api, orc, [n1024, n2048], shapes, 80, prefix=3)
+    keys = [n1024.ek, n2048.ek]
+    d_in, d_lut = api.to_device_u64(ct), api.to_device_u32(luts)
+    split = api.from_device_u64(_device_run(api, keys, jobs, d_in, d_lut, out_words, None))
+    one = api.from_device_u64(_device_run(api, keys, jobs, d_in, d_lut, out_words, api.BATCH_ONE_BLOCK))
+    assert np.array_equal(split, one)
+    for j, w in zip(jobs, want):
+        o = int(j["out_off"])
+        assert np.array_equal(split[o:o + len(w)], w), j
+
+
+def _device_run(api, keys, jobs, d_in, d_lut, out_words, flags):
+    d_out = torch.zeros(out_words, dtype=torch.int64, device="cuda")
+    ws = api.workspace(api.bm_workspace_bytes(keys, jobs))
+    if flags is None:
+        api.bm_bootstrap_batch(keys, jobs, d_in, d_lut, d_out, ws)
+    else:
+        b = api.Batch(keys, jobs, d_in, d_lut, d_out, ws, flags)
+        b.run()
+        torch.cuda.synchronize()
+        b.free()
+    torch.cuda.synchronize()
+    assert api.bm_workspace_status(ws) == 0
+    return d_out
+
+
 # --- modulus switches and the full Algorithm 1 ----------------------------------------
 
 def test_mod_switch_matches_oracle(api, orc, toy):
