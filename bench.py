@@ -475,6 +475,76 @@ def run_suite(args):
             r["workload"] = "served t=2^13 m=8 N=2048"
             r["capacity_estimate"] = cap
             emit(r)
+    # (6) plaintext-size sweep of the Sec. 5 experiments: the identity function
+    # (not negacyclic, so two rounds) on log t = 5.., BootMMPM at N = 2^11 with
+    # m = 2^(log t - 5), q = 2Nm; the single-polynomial (TFHE) layout where its
+    # ring degree N = 2^(log t + 6) is one the kernels run (<= 4096)
+    if "sweep" in args.suite:
+        lo, hi = (int(v) for v in args.sweep_logt.split("-"))
+        paper_t1 = {5: 0.7375, 6: 1.3625, 7: 2.6376, 8: 5.2578, 9: 10.203, 10: 20.261, 11: 41.795}
+        paper_t1_tfhe = {5: 0.6969, 6: 3.6953, 7: 10.092}
+
+        def key_bytes_formula(kp):
+            bsk = 2 * kp.n * 2 * kp.l_B * 2 * kp.N * 8
+            ksk = kp.N * kp.l_ks * ((1 << kp.log2_Bks) - 1) * (kp.n + 1) * 8
+            return bsk, ksk
+
+        def identity_run(ks, m, logt, count, seed):
+            kp = ks.kp
+            t = 1 << logt
+            T, q = 2 * t, 2 * kp.N * m
+            rng = np.random.default_rng(seed)
+            x = rng.integers(0, T, count).astype(np.uint32)
+            enc = synth.encryption_randomness(kp.n, q, kp.sigma, count, 4000 + seed)
+            ct = api.bm_encrypt(ks.sk, q, T, x, enc["mask"], enc["err"])
+            f = np.tile(np.arange(t, dtype=np.uint32), count)
+            d_in, d_f = api.to_device_u64(ct.ravel(), dev), api.to_device_u32(f, dev)
+            d_out = torch.zeros(count * (kp.n + 1), dtype=torch.int64, device=dev)
+            ws = api.workspace(api.bm_arbitrary_workspace_bytes(ks.ek, m, t, count), dev)
+            run = lambda c: api.bm_bootstrap_arbitrary(ks.ek, m, t, q, d_f, c, d_in, d_out, ws, stream)
+            run(1)                                       # warm: one ciphertext
+            stream.synchronize()
+            plain_ms = _timed(lambda: run(1), stream, 1, flush)
+            ms = _timed(lambda: run(count), stream, 1, flush)
+            assert api.bm_workspace_status(ws, stream) == 0
+            out = api.from_device_u64(d_out).reshape(count, kp.n + 1)
+            bad = int(np.sum(api.bm_decrypt(ks.sk, q, T, out) != x % t))
+            del ws, d_in, d_f, d_out
+            torch.cuda.empty_cache()
+            return {"identity_per_s": count / ms * 1e3, "bootstraps_per_s": 2 * count / ms * 1e3,
+                    "batch_ms": ms, "count": count, "plain_identity_ms": plain_ms, "decrypt_failures": bad}
+
+        kp_s = P.KEYS_SWEEP_N2048 if args.sweep_n == 512 else \
+            P.KeyParams(**{**P.KEYS_SWEEP_N2048.__dict__, "n": args.sweep_n})
+        kss = wl.make_keyset(kp_s, 1006)
+        for logt in range(lo, hi + 1):
+            r = logt - 5
+            m = 1 << r
+            count = 152 * max(1, 8 >> r)
+            res = identity_run(kss, m, logt, count, 600 + logt)
+            bsk, ksk = key_bytes_formula(kp_s)
+            emit({"workload": f"sweep BootMMPM identity n={kp_s.n} N=2048 log t={logt}",
+                  "log_t": logt, "log_q": logt + 7, "log_N": 11, "log_r": r, "m": m, **res,
+                  "key_bytes": {"bsk": bsk, "ksk": ksk, "resident": kss.ek.nbytes},
+                  "paper_table1_s_per_identity_i7": paper_t1.get(logt) if kp_s.n == 512 else None})
+        del kss
+        for logt in range(lo, hi + 1):
+            logN = logt + 6
+            kp_t = P.KeyParams(**{**kp_s.__dict__, "N": 1 << logN})
+            bsk, ksk = key_bytes_formula(kp_t)
+            d = {"workload": f"sweep TFHE layout identity n={kp_s.n} N=2^{logN} log t={logt}",
+                 "log_t": logt, "log_q": logt + 7, "log_N": logN, "m": 1,
+                 "key_bytes": {"bsk": bsk, "ksk": ksk},
+                 "paper_table1_s_per_identity_i7": paper_t1_tfhe.get(logt) if kp_s.n == 512 else None}
+            if logN <= 12:
+                kst = wl.make_keyset(kp_t, 1006)
+                d.update(identity_run(kst, 1, logt, 152 * max(1, 8 >> (logN - 11)), 700 + logt))
+                d["key_bytes"]["resident"] = kst.ek.nbytes
+                del kst
+                torch.cuda.empty_cache()
+            else:
+                d["not_run"] = "ring degree above 4096"
+            emit(d)
     # (5) decryption failures over >= 1e5 bootstraps of the headline workload
     if "failures" in args.suite:
         total, bad_total = 0, 0
@@ -502,7 +572,9 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=16,
                     help="CMux steps per ciphertext in the bounded oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--suite", default="", help="comma list: layouts,large,uneven,served,failures")
+    ap.add_argument("--suite", default="", help="comma list: layouts,large,uneven,served,failures,sweep")
+    ap.add_argument("--sweep-logt", default="5-15", help="sweep: range of log2 t")
+    ap.add_argument("--sweep-n", type=int, default=512, help="sweep: LWE dimension (512 or 1024)")
     ap.add_argument("--rates", default="2000,0.25,0.5,0.9", help="served: req/s, or fractions of capacity")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--max-batch", type=int, default=512)

@@ -88,7 +88,7 @@ typedef struct bm_eval_key bm_eval_key;
 /* One bootstrapping job (Definition 1): ciphertext, table, shape, key set. */
 typedef struct bm_job {
     uint32_t key;       /* index into the key array of the call */
-    uint32_t m;         /* polynomials in the test vector, 1..64 */
+    uint32_t m;         /* polynomials in the test vector, 1..1024 */
     uint32_t t;         /* plaintext modulus, even, 2 <= t <= 2Nm */
     uint32_t reserved;  /* must be 0 */
     uint64_t in_off;    /* element offset of the input LWE_{n,2Nm} (n+1 words) */

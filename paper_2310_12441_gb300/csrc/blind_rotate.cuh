@@ -126,7 +126,10 @@ struct Cfg {
     static constexpr int CPB = P / G;                              // combos per batch
     static constexpr size_t REGIONS = 2ull * P * N * 8;            // two regions per polynomial
     static constexpr bool DSM = REGIONS + 4ull * G * N * 8 <= 200 * 1024;   // row differences in smem
-    static constexpr size_t SMEM = REGIONS + (DSM ? 4ull * G * N * 8 : 0);
+    static constexpr size_t DBYTES = DSM ? 4ull * G * N * 8 : 0;
+    static constexpr size_t TWBYTES = 16ull * N;                    // forward twiddle pairs
+    static constexpr size_t SMEM = REGIONS + DBYTES + TWBYTES;
+    static_assert(SMEM <= 227 * 1024 - 1024, "shared memory per block");
 };
 
 // Blind rotation of one job by the whole block (all threads must call it).
@@ -183,6 +186,14 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
         return;
     }
     acc_init(acc0, lut, ct[n] % qp, m, t, N, Q, crank, csize);
+    // forward twiddle pairs to shared memory (read by every transform), in
+    // the transposed order of ntr::twiddle_slot
+    u64 *tws = sm + (C::REGIONS + C::DBYTES) / 8;
+    for (u32 pos = tid; pos < (u32)N; pos += C::kThreads) {
+        const u32 src = ntr::twiddle_slot<LOGN>(pos);
+        tws[2 * pos] = __ldg(twp + 2 * src);
+        tws[2 * pos + 1] = __ldg(twp + 2 * src + 1);
+    }
     if (split) cluster_sync(); else __syncthreads();
 
     const u32 p = tid / C::T;          // polynomial slot within a batch
@@ -267,7 +278,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                         }
                     }
                 }
-                u64 *out = ntr::fwd_to_smem<LOGN, LAZY, SMALL0, QLOW1>(x, sw, l, active, twp, Q, mq.one_sh, qb);
+                u64 *out = ntr::fwd_to_smem<LOGN, LAZY, SMALL0, QLOW1, true>(x, sw, l, active, tws, Q, mq.one_sh, qb);
                 // regions of the other polynomials of the batch sit at stride N;
                 // polynomial cc G + g holds combo c0 + cc of row r0 + g
                 const u64 *slots = out - (size_t)p * N;
@@ -344,8 +355,8 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                     for (int j = 0; j < C::PPT; j++) {
                         const u32 q = tid + C::kThreads * j;
                         if (q < (u32)N) {
-                            sums[((size_t)r * 2) * N + q] = reduce128(lo[g][0][j], hi[g][0][j], mq);
-                            sums[((size_t)r * 2 + 1) * N + q] = reduce128(lo[g][1][j], hi[g][1][j], mq);
+                            sums[((size_t)r * 2) * N + q] = reduce128q<QLOW1>(lo[g][0][j], hi[g][0][j], mq);
+                            sums[((size_t)r * 2 + 1) * N + q] = reduce128q<QLOW1>(lo[g][1][j], hi[g][1][j], mq);
                         }
                     }
                 }

@@ -335,7 +335,7 @@ template <int LOGN, bool LAZY, bool SMALL0, bool QLOW1>
 __global__ void __launch_bounds__(group_threads<LOGN>(), 512 / group_threads<LOGN>())
     k_blind_rotate(const DevJob *__restrict__ jobs, u32 steps_limit, const u64 *__restrict__ ct_in,
                    const u32 *__restrict__ luts, u64 *ws, u32 *status) {
-    extern __shared__ u64 sm[];
+    extern __shared__ __align__(16) u64 sm[];
     // a cluster of blocks shares one job (rows split); plain launches: 1 block
     brk::br_job<LOGN, group_threads<LOGN>(), LAZY, SMALL0, QLOW1>(jobs[blockIdx.x / cluster_size()],
                                                                    steps_limit, ct_in, luts, ws, status, sm);

@@ -8,7 +8,7 @@
 #include "../../include/bootmmpm.h"
 
 #define BM_MAX_L_B 8
-#define BM_MAX_M 64
+#define BM_MAX_M 1024   // q' = 2Nm <= 2^23 (u32 arithmetic on exponents)
 
 // Device-resident description of one evaluation key set.  One copy lives in
 // device memory (owned by the bm_eval_key) so jobs can point at it.

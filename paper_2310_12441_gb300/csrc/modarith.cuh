@@ -123,3 +123,23 @@ __device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const ModQ &m) {
     if (s >= m.Q) s -= m.Q;
     return s;
 }
+
+// reduce128 with the cheaper quotients of Q = c 2^32 + 1 (QLOW1, so Q > 2^32
+// and floor(2^64 / Q) < 2^32): hi * (2^64 mod Q) by the three-product Shoup
+// ([0, 4Q)), lo by the quotient estimate floor((lo >> 32) floor(2^64/Q) / 2^32),
+// at most 2 below floor(lo / Q) ([0, 3Q)); the sum is below 7Q < 2^64.
+template <bool QLOW1>
+__device__ __forceinline__ u64 reduce128q(u64 lo, u64 hi, const ModQ &m) {
+    if constexpr (QLOW1) {
+        const u64 Q = m.Q;
+        const u64 x = shoup3_lazy<true>(hi, m.r64, m.r64_sh, Q);
+        const u32 qe = __umulhi((u32)(lo >> 32), (u32)m.one_sh);
+        u64 s = x + (lo - times_q<true>(qe, Q));
+        if (s >= 2 * m.two_Q) s -= 2 * m.two_Q;
+        if (s >= m.two_Q) s -= m.two_Q;
+        if (s >= Q) s -= Q;
+        return s;
+    } else {
+        return reduce128(lo, hi, m);
+    }
+}

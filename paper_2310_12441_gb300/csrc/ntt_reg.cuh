@@ -50,8 +50,15 @@ struct Swap {
     }
 };
 
+// Twiddle pair ti from a table in global memory, or in shared memory (SH).
+template <bool SH = false>
 __device__ __forceinline__ void twiddle(const u64 *__restrict__ tp, u32 ti, u64 &W, u64 &Wsh) {
-    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(tp) + ti);
+    ulonglong2 v;
+    if constexpr (SH) {
+        v = reinterpret_cast<const ulonglong2 *>(tp)[ti];
+    } else {
+        v = __ldg(reinterpret_cast<const ulonglong2 *>(tp) + ti);
+    }
     W = v.x;
     Wsh = v.y;
 }
@@ -65,7 +72,7 @@ __device__ __forceinline__ void twiddle(const u64 *__restrict__ tp, u32 ti, u64 
 // W * Y is formed exactly (a 64 x 32-bit product) and left unreduced:
 // X + W Y and X - W Y + Q B, both below B + Q B.  The caller guarantees
 // B + Q B + 4 Q (LOGN - 1) < 2^64.
-template <int LOGN, int F, int S0, int NST, bool LAZY, bool SMALL0 = false, bool QLOW1 = false>
+template <int LOGN, int F, int S0, int NST, bool LAZY, bool SMALL0 = false, bool QLOW1 = false, bool TWS = false>
 __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__restrict__ twp, u64 Q,
                                           u64 twoQ, u64 qb = 0) {
     const u32 high = l >> F;
@@ -79,7 +86,13 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__rest
             const int i2 = i | (1 << lb);
             const u32 g = (high << (3 - lb)) | (u32)(i >> (lb + 1));
             u64 W, Wsh;
-            twiddle(twp, (1u << s) + g, W, Wsh);
+            if constexpr (TWS) {
+                // shared table in the per-stage transposed order of
+                // twiddle_slot(): the thread part of g runs fastest
+                twiddle<true>(twp, (1u << s) + ((u32)(i >> (lb + 1)) << (LOGN - 4 - F)) + high, W, Wsh);
+            } else {
+                twiddle<false>(twp, (1u << s) + g, W, Wsh);
+            }
             if constexpr (LAZY && SMALL0 && S0 == 0) {
                 if (st == 0) {
                     const u32 y = (u32)x[i2];
@@ -131,6 +144,25 @@ __device__ __forceinline__ void inv_phase(u64 (&x)[16], u32 l, const u64 *__rest
     }
 }
 
+// Index into the plain forward table (psi^bitrev(k) at k = 2^s + g) of slot
+// `pos` of the transposed shared-memory copy read by fwd_phase<..., TWS>.
+// Stage s sits in the phase whose field starts at F; there g = (high << a) | j
+// with the thread part high = l >> F below 2^(LOGN-4-F) and the register part
+// j below 2^a, a = s - (LOGN-4-F); slot 2^s + j 2^(LOGN-4-F) + high holds it,
+// so the threads of a warp read consecutive slots (no bank conflicts).
+template <int LOGN>
+__device__ __forceinline__ u32 twiddle_slot(u32 pos) {
+    if (pos == 0) return 0;
+    constexpr u32 NPH = (LOGN + 3) / 4;
+    const u32 s = 31 - __clz(pos);
+    const u32 ph = s / 4;
+    const u32 F = ph < NPH - 1 ? LOGN - 4 - 4 * ph : 0;
+    const u32 sh = LOGN - 4 - F;
+    const u32 r = pos - (1u << s);
+    const u32 j = r >> sh, high = r & ((1u << sh) - 1);
+    return (1u << s) + ((high << (s - sh)) | j);
+}
+
 template <int F>
 __device__ __forceinline__ void store_field(const u64 (&x)[16], u64 *reg, u32 l) {
 #pragma unroll
@@ -144,25 +176,26 @@ __device__ __forceinline__ void load_field(u64 (&x)[16], const u64 *reg, u32 l) 
 }
 
 // Forward NTT.  On entry x holds indices l + T i (field [LOGN-4, LOGN)) of
-// this thread's polynomial, values below 4Q.  Returns the region that holds
+// this thread's polynomial, values below 4Q.  TWS: twp points to a copy of
+// the twiddle pairs in shared memory.  Returns the region that holds
 // the transform, fully reduced to [0, Q), in bit-reversed positions
 // (swizzled); the caller must __syncthreads() before reading it.  Every
 // thread of the block calls this (it contains barriers); threads with
 // active == false only take part in the barriers.
-template <int LOGN, bool LAZY, bool SMALL0 = false, bool QLOW1 = false>
+template <int LOGN, bool LAZY, bool SMALL0 = false, bool QLOW1 = false, bool TWS = false>
 __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool active,
                                             const u64 *__restrict__ twp, u64 Q, u64 one_sh, u64 qb = 0) {
     constexpr int NPH = (LOGN + 3) / 4;
     static_assert(LOGN >= 8 && LOGN <= 12, "ring degree 256..4096");
     const u64 twoQ = 2 * Q;
-    if (active) fwd_phase<LOGN, LOGN - 4, 0, 4, LAZY, SMALL0, QLOW1>(x, l, twp, Q, twoQ, qb);
+    if (active) fwd_phase<LOGN, LOGN - 4, 0, 4, LAZY, SMALL0, QLOW1, TWS>(x, l, twp, Q, twoQ, qb);
     u64 *r = sw.take();
     if (active) store_field<LOGN - 4>(x, r, l);
     __syncthreads();
     if constexpr (NPH == 3) {
         if (active) {
             load_field<LOGN - 8>(x, r, l);
-            fwd_phase<LOGN, LOGN - 8, 4, 4, LAZY, false, QLOW1>(x, l, twp, Q, twoQ);
+            fwd_phase<LOGN, LOGN - 8, 4, 4, LAZY, false, QLOW1, TWS>(x, l, twp, Q, twoQ);
         }
         r = sw.take();
         if (active) store_field<LOGN - 8>(x, r, l);
@@ -170,11 +203,18 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
     }
     if (active) {
         load_field<0>(x, r, l);
-        fwd_phase<LOGN, 0, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), LAZY, false, QLOW1>(x, l, twp, Q, twoQ);
+        fwd_phase<LOGN, 0, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), LAZY, false, QLOW1, TWS>(x, l, twp, Q, twoQ);
 #pragma unroll
         for (int i = 0; i < 16; i++) {
             u64 v = x[i];
-            if constexpr (LAZY) {
+            if constexpr (LAZY && QLOW1) {
+                // Q = c 2^32 + 1 > 2^32, so floor(2^64 / Q) < 2^32 and the
+                // estimate floor((v >> 32) floor(2^64/Q) / 2^32) lies at most
+                // 2 below floor(v / Q): one 32-bit high product, r in [0, 3Q)
+                const u32 qe = __umulhi((u32)(v >> 32), (u32)one_sh);
+                v -= times_q<true>(qe, Q);
+                v = v >= twoQ ? v - twoQ : v;
+            } else if constexpr (LAZY) {
                 v = v - __umul64hi(v, one_sh) * Q;     // Shoup with w = 1: [0, 2Q)
             } else {
                 v = v >= twoQ ? v - twoQ : v;

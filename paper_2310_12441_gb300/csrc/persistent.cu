@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     k_blind_rotate_persistent(const DevJob *__restrict__ jobs, u32 count, u32 steps,
                               const u64 *__restrict__ ct_in, const u32 *__restrict__ luts, u64 *ws,
                               u32 *status, u32 *counter) {
-    extern __shared__ u64 sm[];
+    extern __shared__ __align__(16) u64 sm[];
     __shared__ u32 s_next;
     for (;;) {
         if (threadIdx.x == 0) s_next = atomicAdd(counter, 1u);

@@ -88,6 +88,15 @@ KEYS_N4096 = KeyParams(n=630, N=4096, Q=18014359854776321, log2_B=9, l_B=6,
 KEYS_N2048 = KeyParams(n=750, N=2048, Q=1152921092289986561, log2_B=10, l_B=6,
                        log2_Bks=4, l_ks=7)
 
+# Plaintext-size sweep (Sec. 5 experiments): log n = 9, log Q = 54,
+# log B = 15 (l_B = 4), ring degree 2^11 for every plaintext size; the
+# single-polynomial (TFHE) layout needs N = 2^(log t + 6).  The paper's
+# key-switching base 25 is read as 2^5 with 8 digits of the approximate gadget.
+KEYS_SWEEP_N2048 = KeyParams(n=512, N=2048, Q=18014359854776321, log2_B=15, l_B=4,
+                             log2_Bks=5, l_ks=8)
+KEYS_SWEEP_N4096 = KeyParams(n=512, N=4096, Q=18014359854776321, log2_B=15, l_B=4,
+                             log2_Bks=5, l_ks=8)
+
 # Workloads ------------------------------------------------------------------
 TOY = Workload("toy_n64_N256_m2_t32", KEYS_TOY, JobShape(m=2, t=32), 1,
                "plain bootstrap of 1 ciphertext", seed_base=1)

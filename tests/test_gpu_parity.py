@@ -158,6 +158,19 @@ def test_blind_rotate_toy_full(api, orc, toy):
         assert np.array_equal(got[i], orc.blind_rotate(kp, m, t, toy.bsk, ct[i], luts[i]))
 
 
+@pytest.mark.parametrize("m,t", [(64, 1 << 12), (1024, 1 << 14)])
+def test_blind_rotate_toy_many_rows(api, orc, toy, m, t):
+    """Large m (the plaintext-size sweep goes to m = 1024): each of a
+    cluster's 8 blocks takes m/8 rows; prefix ciphertexts keep the oracle fast."""
+    kp = toy.kp
+    _, ct = _encrypt(orc, toy, m, t, 2, 5 + m, prefix=2)
+    luts, _ = synth.luts(t, 2, 2005 + m)
+    jobs = _uniform_jobs(api, 2, kp.n, t, m)
+    got = _blind_rotate_gpu(api, toy, jobs, ct, luts, 1 << 30)
+    for i in range(2):
+        assert np.array_equal(got[i], orc.blind_rotate(kp, m, t, toy.bsk, ct[i], luts[i])), i
+
+
 @pytest.mark.parametrize("steps", [0, 1, 5])
 def test_blind_rotate_steps_equal_truncated_ciphertext(api, orc, n1024, steps):
     """ACC after the first K CMux steps equals the oracle's full rotation of
@@ -478,3 +491,35 @@ def test_two_round_arbitrary_function_matches_oracle(api, orc, toy):
     got = api.from_device_u64(d_out).reshape(cnt, kp.n + 1)
     assert np.array_equal(got, orc.bootstrap_arbitrary(kp, m, t, q, toy.bsk, toy.ksk, ct, f))
     assert np.array_equal(api.bm_decrypt(toy.sk, q, T, got), f[np.arange(cnt), x % t])
+
+
+def test_sweep_key_shape_bit_exact(api, orc):
+    """The plaintext-size sweep's key shape (N = 2048, log Q = 54, B = 2^15 x 4
+    digits, key-switching base 2^5 x 8), with n = 16 so the oracle stays fast:
+    bootstraps and the two-round identity are bit-exact with the oracle."""
+    kq = P.KEYS_SWEEP_N2048
+    kp = P.KeyParams(n=16, N=kq.N, Q=kq.Q, log2_B=kq.log2_B, l_B=kq.l_B, log2_Bks=kq.log2_Bks,
+                     l_ks=kq.l_ks)
+    ks = KeySet(api, orc, kp, 1006, kp.n)
+    shapes = [(0, 2, 64), (0, 4, 256)]
+    jobs, ct, luts, want, out_words = _mixed_batch(api, orc, [ks], shapes, 90, prefix=None)
+    got = api.from_device_u64(_device_run(api, [ks.ek], jobs, api.to_device_u64(ct), api.to_device_u32(luts),
+                                          out_words, None))
+    for j, w in zip(jobs, want):
+        o = int(j["out_off"])
+        assert np.array_equal(got[o:o + len(w)], w), j
+    m, t = 2, 32
+    q = 2 * kp.N * m
+    x = np.array([3, 40], dtype=np.uint32)
+    f = np.tile(np.arange(t, dtype=np.uint32), (2, 1))
+    enc = synth.encryption_randomness(kp.n, q, kp.sigma, 2, 4092)
+    cti = orc.encrypt(kp.n, q, 2 * t, ks.rnd["s"], x, enc["mask"], enc["err"])
+    d_in = api.to_device_u64(cti.ravel())
+    d_out = torch.zeros_like(d_in)
+    ws = api.workspace(api.bm_arbitrary_workspace_bytes(ks.ek, m, t, 2))
+    api.bm_bootstrap_arbitrary(ks.ek, m, t, q, api.to_device_u32(f.ravel()), 2, d_in, d_out, ws)
+    torch.cuda.synchronize()
+    assert api.bm_workspace_status(ws) == 0
+    out = api.from_device_u64(d_out).reshape(2, kp.n + 1)
+    assert np.array_equal(out, orc.bootstrap_arbitrary(kp, m, t, q, ks.bsk, ks.ksk, cti, f))
+    assert np.array_equal(api.bm_decrypt(ks.sk, q, 2 * t, out), x % t)
