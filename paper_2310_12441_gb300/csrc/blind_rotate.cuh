@@ -158,9 +158,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     constexpr int N = C::N, G = C::G, CPB = C::CPB;
     const KeyDev *K = J.key;
     const u32 lbits = J.lbits;
-    // a batch's CPB limb products must fit 64 bits, else fold after each one
-    const bool fold_each = (unsigned __int128)CPB * ((2ull << lbits) - 1) * ((2ull << lbits) - 1) >=
-                           ((unsigned __int128)1 << 64);
+    const bool fold_each = J.fold_each != 0;
     const u32 m = J.m, t = J.t, lB = K->l_B, log2B = K->log2_B, n = K->n;
     const ModQ mq = K->mq;
     const u64 Q = mq.Q;
@@ -363,6 +361,17 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
             }
         }
         __syncthreads();
+        // inverse twiddle pairs into the row-difference buffer, free until the
+        // next step (transposed order of ntr::inv_twiddle_slot)
+        const u64 *itw_use = itwp;
+        if constexpr (C::DSM) {
+            for (u32 pos = tid; pos < (u32)N; pos += C::kThreads) {
+                const u32 src = ntr::inv_twiddle_slot<LOGN>(pos);
+                dbuf[2 * pos] = __ldg(itwp + 2 * src);
+                dbuf[2 * pos + 1] = __ldg(itwp + 2 * src + 1);
+            }
+            itw_use = dbuf;
+        }
         // --- inverse transforms of this block's 2 mr row sums (rows crank +
         // csize i), ACC update
         const u32 mr = crank < m ? (m - 1 - crank) / csize + 1 : 0;
@@ -381,7 +390,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 }
             }
             __syncthreads();
-            ntr::inv_from_smem<LOGN, QLOW1>(x, in, sw, l, active, itwp, Q);
+            ntr::inv_from_smem<LOGN, QLOW1, C::DSM>(x, in, sw, l, active, itw_use, Q);
             if (active) {
                 const size_t base = (size_t)u * N;
 #pragma unroll

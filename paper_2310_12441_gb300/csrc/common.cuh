@@ -35,7 +35,9 @@ struct DevJob {
     u64 acc_off;       // element offset of the job's three [m][2][N] buffers in the
                        // workspace: ACC ping-pong and the per-step row sums
     u32 variant;       // arithmetic variant of the key's modulus (BR_V_* flags)
-    u32 lbits;         // Karatsuba limb width, ceil(bits(Q - 1) / 2)
+    u32 lbits;         // Karatsuba limb width (see limb_plan on the host)
+    u32 fold_each;     // 1: a batch's limb products may exceed 64 bits, fold per combo
+    u32 pad;
 };
 
 // Arithmetic variants of the blind rotation, chosen per key set on the host.

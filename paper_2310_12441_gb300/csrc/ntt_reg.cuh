@@ -120,7 +120,7 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__rest
 }
 
 // Inverse phase: NST stages acting on bits SB, SB+1, ..., field [F, F+4).
-template <int LOGN, int F, int SB, int NST, bool QLOW1 = false>
+template <int LOGN, int F, int SB, int NST, bool QLOW1 = false, bool TWS = false>
 __device__ __forceinline__ void inv_phase(u64 (&x)[16], u32 l, const u64 *__restrict__ itwp, u64 Q,
                                           u64 twoQ) {
     const u32 high = l >> F;
@@ -134,7 +134,13 @@ __device__ __forceinline__ void inv_phase(u64 (&x)[16], u32 l, const u64 *__rest
             const int i2 = i | (1 << lb);
             const u32 g = (high << (3 - lb)) | (u32)(i >> (lb + 1));
             u64 W, Wsh;
-            twiddle(itwp, (1u << (LOGN - 1 - b)) + g, W, Wsh);
+            if constexpr (TWS) {
+                // shared table in the transposed order of inv_twiddle_slot()
+                twiddle<true>(itwp, (1u << (LOGN - 1 - b)) + ((u32)(i >> (lb + 1)) << (LOGN - 4 - F)) + high, W,
+                              Wsh);
+            } else {
+                twiddle<false>(itwp, (1u << (LOGN - 1 - b)) + g, W, Wsh);
+            }
             const u64 U = x[i], V = x[i2];
             u64 u = U + V;
             u = u >= twoQ ? u - twoQ : u;
@@ -163,6 +169,21 @@ __device__ __forceinline__ u32 twiddle_slot(u32 pos) {
     return (1u << s) + ((high << (s - sh)) | j);
 }
 
+// The same for the inverse table (psi^-bitrev(k) at k = 2^s + g, used by the
+// inverse stage on bit LOGN-1-s, which sits in the inverse phase with field F).
+template <int LOGN>
+__device__ __forceinline__ u32 inv_twiddle_slot(u32 pos) {
+    if (pos == 0) return 0;
+    constexpr u32 NPH = (LOGN + 3) / 4;
+    const u32 s = 31 - __clz(pos);
+    const u32 q = (LOGN - 1 - s) / 4;
+    const u32 F = q < NPH - 1 ? 4 * q : LOGN - 4;
+    const u32 sh = LOGN - 4 - F;
+    const u32 r = pos - (1u << s);
+    const u32 j = r >> sh, high = r & ((1u << sh) - 1);
+    return (1u << s) + ((high << (s - sh)) | j);
+}
+
 template <int F>
 __device__ __forceinline__ void store_field(const u64 (&x)[16], u64 *reg, u32 l) {
 #pragma unroll
@@ -178,7 +199,9 @@ __device__ __forceinline__ void load_field(u64 (&x)[16], const u64 *reg, u32 l) 
 // Forward NTT.  On entry x holds indices l + T i (field [LOGN-4, LOGN)) of
 // this thread's polynomial, values below 4Q.  TWS: twp points to a copy of
 // the twiddle pairs in shared memory.  Returns the region that holds
-// the transform, fully reduced to [0, Q), in bit-reversed positions
+// the transform in bit-reversed positions, values in [0, Q), or with LAZY
+// only partly reduced for the multiply-accumulate: [0, 3Q) when QLOW1, else
+// [0, 2Q)
 // (swizzled); the caller must __syncthreads() before reading it.  Every
 // thread of the block calls this (it contains barriers); threads with
 // active == false only take part in the barriers.
@@ -210,16 +233,16 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
             if constexpr (LAZY && QLOW1) {
                 // Q = c 2^32 + 1 > 2^32, so floor(2^64 / Q) < 2^32 and the
                 // estimate floor((v >> 32) floor(2^64/Q) / 2^32) lies at most
-                // 2 below floor(v / Q): one 32-bit high product, r in [0, 3Q)
+                // 2 below floor(v / Q): one 32-bit high product, [0, 3Q)
                 const u32 qe = __umulhi((u32)(v >> 32), (u32)one_sh);
                 v -= times_q<true>(qe, Q);
-                v = v >= twoQ ? v - twoQ : v;
             } else if constexpr (LAZY) {
                 v = v - __umul64hi(v, one_sh) * Q;     // Shoup with w = 1: [0, 2Q)
             } else {
                 v = v >= twoQ ? v - twoQ : v;
+                v = v >= Q ? v - Q : v;
             }
-            x[i] = v >= Q ? v - Q : v;
+            x[i] = v;
         }
     }
     r = sw.take();
@@ -231,14 +254,14 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
 // transform (swizzled, values below 2Q) and the block has passed a barrier
 // since it was written; `in` must be the region sw wrote last.  On exit x
 // holds natural-order coefficients l + T i, reduced to [0, Q).
-template <int LOGN, bool QLOW1 = false>
+template <int LOGN, bool QLOW1 = false, bool TWS = false>
 __device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap &sw, u32 l, bool active,
                                               const u64 *__restrict__ itwp, u64 Q) {
     constexpr int NPH = (LOGN + 3) / 4;
     const u64 twoQ = 2 * Q;
     if (active) {
         load_field<0>(x, in, l);
-        inv_phase<LOGN, 0, 0, 4, QLOW1>(x, l, itwp, Q, twoQ);
+        inv_phase<LOGN, 0, 0, 4, QLOW1, TWS>(x, l, itwp, Q, twoQ);
     }
     u64 *r = sw.take();
     if (active) store_field<0>(x, r, l);
@@ -246,7 +269,7 @@ __device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap 
     if constexpr (NPH == 3) {
         if (active) {
             load_field<4>(x, r, l);
-            inv_phase<LOGN, 4, 4, 4, QLOW1>(x, l, itwp, Q, twoQ);
+            inv_phase<LOGN, 4, 4, 4, QLOW1, TWS>(x, l, itwp, Q, twoQ);
         }
         r = sw.take();
         if (active) store_field<4>(x, r, l);
@@ -254,7 +277,7 @@ __device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap 
     }
     if (active) {
         load_field<LOGN - 4>(x, r, l);
-        inv_phase<LOGN, LOGN - 4, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), QLOW1>(x, l, itwp, Q, twoQ);
+        inv_phase<LOGN, LOGN - 4, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), QLOW1, TWS>(x, l, itwp, Q, twoQ);
 #pragma unroll
         for (int i = 0; i < 16; i++) x[i] = x[i] >= Q ? x[i] - Q : x[i];
     }
