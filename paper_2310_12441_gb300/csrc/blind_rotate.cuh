@@ -204,9 +204,10 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     const u32 ncomb = 4 * lB;
     const size_t rgsw = (size_t)2 * lB * 2 * N;
 
+    // bv: a key word stored pre-split, low limb | high limb << 32
     auto kara = [&](u64 xv, u64 bv, u64 &kh, u64 &kl, u64 &km) {
         const u32 x0 = (u32)(xv & lmask), x1 = (u32)(xv >> lbits);
-        const u32 b0 = (u32)(bv & lmask), b1 = (u32)(bv >> lbits);
+        const u32 b0 = (u32)bv, b1 = (u32)(bv >> 32);
         kh += (u64)x1 * b1;
         kl += (u64)x0 * b0;
         km += (u64)(x0 + x1) * (b0 + b1);

@@ -147,8 +147,11 @@ __global__ void k_bsk_rows(const u64 *__restrict__ mask, const int8_t *__restric
         add128(lo, hi, g1);
         const u64 c1 = reduce128(lo, hi, K.mq);
         const u64 c0 = add_mod(ah, g0, Q);
-        o[i] = mul_shoup(c0, K.ninv, K.ninv_sh, Q);
-        o[N + i] = mul_shoup(c1, K.ninv, K.ninv_sh, Q);
+        // stored split into the multiply-accumulate's limbs (KeyDev::lbits)
+        const u64 lmask = (1ull << K.lbits) - 1;
+        const u64 w0 = mul_shoup(c0, K.ninv, K.ninv_sh, Q), w1 = mul_shoup(c1, K.ninv, K.ninv_sh, Q);
+        o[i] = (w0 & lmask) | ((w0 >> K.lbits) << 32);
+        o[N + i] = (w1 & lmask) | ((w1 >> K.lbits) << 32);
     }
 }
 
@@ -214,7 +217,8 @@ static void fill_keydev_constants(KeyDev &K, const bm_key_params &p, u32 logN, u
     K.l_B = p.l_B;
     K.log2_Bks = p.log2_Bks;
     K.l_ks = p.l_ks;
-    K.pad = 0;
+    u32 fold_each = 0;
+    limb_plan(p, choose_variant(p), K.lbits, fold_each);
     (void)psi;
 }
 
