@@ -40,7 +40,7 @@ METRIC = "bootstraps/s on 1 GB300 (batched, bit-exact)"
 # of this workload (profiles/k_blind_rotate_n630_N1024_m4.md), valid while
 # the kernel sources hash to the captured version.
 KERNEL_SOURCES = ["blind_rotate.cuh", "ntt_reg.cuh", "modarith.cuh", "common.cuh", "bootstrap.cu"]
-CAPTURED_TRAFFIC = {"hash": "44e344ddbb778d79", "bytes_per_job": (262.189568e6 + 1.082509e9) / 152}
+CAPTURED_TRAFFIC = {"hash": "2cb1dba2557f158b", "bytes_per_job": (259.398144e6 + 266.243328e6) / 152}
 
 
 def kernel_hash():
