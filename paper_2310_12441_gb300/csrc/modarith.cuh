@@ -143,3 +143,46 @@ __device__ __forceinline__ u64 reduce128q(u64 lo, u64 hi, const ModQ &m) {
         return reduce128(lo, hi, m);
     }
 }
+
+// Lazy forward (Cooley-Tukey) butterfly for Q = c 2^32 + 1, written on 32-bit
+// halves so that the additions run as add-with-carry on the integer ALU and
+// only the seven products of the three-product Shoup quotient, the low word of
+// Y W and q Q use the multiplier:
+//   q = y1 s1 + hi(y1 s0) + hi(y0 s1)           (Wsh = s1:s0, Y = y1:y0)
+//   T = Y W - q Q  mod 2^64, in [0, 4Q)          (q Q = q + (q0 c) 2^32)
+//   X <- X + T,  Y <- X + 4Q - T.
+__device__ __forceinline__ void bfly_lazy_qlow1(u64 &X, u64 &Y, u64 W, u64 Wsh, u32 c, u64 fourQ) {
+    asm("{\n\t"
+        ".reg .u32 x0, x1, y0, y1, w0, w1, s0, s1, h1, h2, q0, q1, t0, t1, u0, u1, f0, f1, qc;\n\t"
+        ".reg .u64 q, t, hw;\n\t"
+        "mov.b64 {x0, x1}, %0;\n\t"
+        "mov.b64 {y0, y1}, %1;\n\t"
+        "mov.b64 {w0, w1}, %2;\n\t"
+        "mov.b64 {s0, s1}, %3;\n\t"
+        "mov.b64 {f0, f1}, %5;\n\t"
+        "mul.hi.u32 h1, y1, s0;\n\t"
+        "mul.hi.u32 h2, y0, s1;\n\t"
+        "mov.b64 hw, {h1, 0};\n\t"
+        "mad.wide.u32 q, y1, s1, hw;\n\t"
+        "mov.b64 {q0, q1}, q;\n\t"
+        "add.cc.u32 q0, q0, h2;\n\t"
+        "addc.u32 q1, q1, 0;\n\t"
+        "mul.wide.u32 t, y0, w0;\n\t"
+        "mov.b64 {t0, t1}, t;\n\t"
+        "mad.lo.u32 t1, y0, w1, t1;\n\t"
+        "mad.lo.u32 t1, y1, w0, t1;\n\t"
+        "mad.lo.u32 qc, q0, %4, q1;\n\t"
+        "sub.cc.u32 t0, t0, q0;\n\t"
+        "subc.u32 t1, t1, qc;\n\t"
+        "add.cc.u32 u0, x0, t0;\n\t"
+        "addc.u32 u1, x1, t1;\n\t"
+        "add.cc.u32 x0, x0, f0;\n\t"
+        "addc.u32 x1, x1, f1;\n\t"
+        "sub.cc.u32 x0, x0, t0;\n\t"
+        "subc.u32 x1, x1, t1;\n\t"
+        "mov.b64 %0, {u0, u1};\n\t"
+        "mov.b64 %1, {x0, x1};\n\t"
+        "}"
+        : "+l"(X), "+l"(Y)
+        : "l"(W), "l"(Wsh), "r"(c), "l"(fourQ));
+}

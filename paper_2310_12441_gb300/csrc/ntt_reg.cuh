@@ -103,7 +103,9 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__rest
                     continue;
                 }
             }
-            if constexpr (LAZY) {
+            if constexpr (LAZY && QLOW1) {
+                bfly_lazy_qlow1(x[i], x[i2], W, Wsh, (u32)(Q >> 32), 2 * twoQ);
+            } else if constexpr (LAZY) {
                 const u64 X = x[i];
                 const u64 T = shoup3_lazy<QLOW1>(x[i2], W, Wsh, Q);
                 x[i] = X + T;
