@@ -81,13 +81,56 @@ __device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 wsh, u64 Q) {
     return reduce_2q(mul_shoup_lazy(a, w, wsh, Q), Q);
 }
 
-__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 Q) {
-    u64 s = a + b;
-    return s >= Q ? s - Q : s;
+// 64-bit additions written on 32-bit halves with add-with-carry, so that
+// they run on the integer ALU (left to itself the compiler may form the high
+// word with a multiply-add, which takes the multiplier pipe the modular
+// products need).
+__device__ __forceinline__ u64 add64c(u64 a, u64 b) {
+    u64 r;
+    asm("{\n\t.reg .u32 a0, a1, b0, b1;\n\t"
+        "mov.b64 {a0, a1}, %1;\n\tmov.b64 {b0, b1}, %2;\n\t"
+        "add.cc.u32 a0, a0, b0;\n\taddc.u32 a1, a1, b1;\n\t"
+        "mov.b64 %0, {a0, a1};\n\t}"
+        : "=l"(r) : "l"(a), "l"(b));
+    return r;
 }
 
+__device__ __forceinline__ u64 sub64c(u64 a, u64 b) {
+    u64 r;
+    asm("{\n\t.reg .u32 a0, a1, b0, b1;\n\t"
+        "mov.b64 {a0, a1}, %1;\n\tmov.b64 {b0, b1}, %2;\n\t"
+        "sub.cc.u32 a0, a0, b0;\n\tsubc.u32 a1, a1, b1;\n\t"
+        "mov.b64 %0, {a0, a1};\n\t}"
+        : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+// x >= c ? x - c : x, from the borrow of x - c.
+__device__ __forceinline__ u64 csub64(u64 x, u64 c) {
+    u64 r;
+    asm("{\n\t.reg .u32 x0, x1, c0, c1, d0, d1, m;\n\t.reg .pred p;\n\t"
+        "mov.b64 {x0, x1}, %1;\n\tmov.b64 {c0, c1}, %2;\n\t"
+        "sub.cc.u32 d0, x0, c0;\n\tsubc.cc.u32 d1, x1, c1;\n\tsubc.u32 m, 0, 0;\n\t"
+        "setp.eq.u32 p, m, 0;\n\t"
+        "selp.b32 x0, d0, x0, p;\n\tselp.b32 x1, d1, x1, p;\n\t"
+        "mov.b64 %0, {x0, x1};\n\t}"
+        : "=l"(r) : "l"(x), "l"(c));
+    return r;
+}
+
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 Q) { return csub64(add64c(a, b), Q); }
+
+// a - b mod Q for a, b in [0, Q): a - b, plus Q when it borrowed.
 __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 Q) {
-    return a >= b ? a - b : a + Q - b;
+    u64 r;
+    asm("{\n\t.reg .u32 a0, a1, b0, b1, q0, q1, m;\n\t"
+        "mov.b64 {a0, a1}, %1;\n\tmov.b64 {b0, b1}, %2;\n\tmov.b64 {q0, q1}, %3;\n\t"
+        "sub.cc.u32 a0, a0, b0;\n\tsubc.cc.u32 a1, a1, b1;\n\tsubc.u32 m, 0, 0;\n\t"
+        "and.b32 q0, q0, m;\n\tand.b32 q1, q1, m;\n\t"
+        "add.cc.u32 a0, a0, q0;\n\taddc.u32 a1, a1, q1;\n\t"
+        "mov.b64 %0, {a0, a1};\n\t}"
+        : "=l"(r) : "l"(a), "l"(b), "l"(Q));
+    return r;
 }
 
 // (hi:lo) += a * b, exact 128-bit accumulation.
@@ -185,4 +228,53 @@ __device__ __forceinline__ void bfly_lazy_qlow1(u64 &X, u64 &Y, u64 W, u64 Wsh, 
         "}"
         : "+l"(X), "+l"(Y)
         : "l"(W), "l"(Wsh), "r"(c), "l"(fourQ));
+}
+
+// Three-product Shoup product for Q = c 2^32 + 1 on 32-bit halves (see
+// bfly_lazy_qlow1): Y W - q Q mod 2^64 in [0, 4Q).
+__device__ __forceinline__ u64 shoup3_qlow1_lazy(u64 Y, u64 W, u64 Wsh, u32 c) {
+    u64 T;
+    asm("{\n\t"
+        ".reg .u32 y0, y1, w0, w1, s0, s1, h1, h2, q0, q1, t0, t1, qc;\n\t"
+        ".reg .u64 q, t, hw;\n\t"
+        "mov.b64 {y0, y1}, %1;\n\t"
+        "mov.b64 {w0, w1}, %2;\n\t"
+        "mov.b64 {s0, s1}, %3;\n\t"
+        "mul.hi.u32 h1, y1, s0;\n\t"
+        "mul.hi.u32 h2, y0, s1;\n\t"
+        "mov.b64 hw, {h1, 0};\n\t"
+        "mad.wide.u32 q, y1, s1, hw;\n\t"
+        "mov.b64 {q0, q1}, q;\n\t"
+        "add.cc.u32 q0, q0, h2;\n\t"
+        "addc.u32 q1, q1, 0;\n\t"
+        "mul.wide.u32 t, y0, w0;\n\t"
+        "mov.b64 {t0, t1}, t;\n\t"
+        "mad.lo.u32 t1, y0, w1, t1;\n\t"
+        "mad.lo.u32 t1, y1, w0, t1;\n\t"
+        "mad.lo.u32 qc, q0, %4, q1;\n\t"
+        "sub.cc.u32 t0, t0, q0;\n\t"
+        "subc.u32 t1, t1, qc;\n\t"
+        "mov.b64 %0, {t0, t1};\n\t"
+        "}"
+        : "=l"(T)
+        : "l"(Y), "l"(W), "l"(Wsh), "r"(c));
+    return T;
+}
+
+// Harvey's forward butterfly with corrections (values in [0, 4Q), 4Q < 2^64),
+// Q = c 2^32 + 1: X <- X' + T, Y <- X' + 2Q - T with X' = X mod 2Q in [0, 2Q)
+// and T = Y W mod Q in [0, 2Q).
+__device__ __forceinline__ void bfly_ct_qlow1(u64 &X, u64 &Y, u64 W, u64 Wsh, u32 c, u64 twoQ) {
+    const u64 Xr = csub64(X, twoQ);
+    const u64 T = csub64(shoup3_qlow1_lazy(Y, W, Wsh, c), twoQ);
+    X = add64c(Xr, T);
+    Y = sub64c(add64c(Xr, twoQ), T);
+}
+
+// Gentleman-Sande inverse butterfly (values in [0, 2Q)), Q = c 2^32 + 1:
+// U <- (U + V) mod 2Q, V <- (U - V + 2Q) W mod Q in [0, 2Q).
+__device__ __forceinline__ void bfly_gs_qlow1(u64 &U, u64 &V, u64 W, u64 Wsh, u32 c, u64 twoQ) {
+    const u64 u = csub64(add64c(U, V), twoQ);
+    V = csub64(shoup3_qlow1_lazy(sub64c(add64c(U, twoQ), V), W, Wsh, c), twoQ);
+    U = u;
 }

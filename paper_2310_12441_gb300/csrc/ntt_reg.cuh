@@ -110,6 +110,8 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__rest
                 const u64 T = shoup3_lazy<QLOW1>(x[i2], W, Wsh, Q);
                 x[i] = X + T;
                 x[i2] = X - T + 2 * twoQ;
+            } else if constexpr (QLOW1) {
+                bfly_ct_qlow1(x[i], x[i2], W, Wsh, (u32)(Q >> 32), twoQ);
             } else {
                 u64 X = x[i];
                 X = X >= twoQ ? X - twoQ : X;
@@ -143,11 +145,15 @@ __device__ __forceinline__ void inv_phase(u64 (&x)[16], u32 l, const u64 *__rest
             } else {
                 twiddle<false>(itwp, (1u << (LOGN - 1 - b)) + g, W, Wsh);
             }
-            const u64 U = x[i], V = x[i2];
-            u64 u = U + V;
-            u = u >= twoQ ? u - twoQ : u;
-            x[i] = u;
-            x[i2] = shoup3<QLOW1>(U - V + twoQ, W, Wsh, Q, twoQ);
+            if constexpr (QLOW1) {
+                bfly_gs_qlow1(x[i], x[i2], W, Wsh, (u32)(Q >> 32), twoQ);
+            } else {
+                const u64 U = x[i], V = x[i2];
+                u64 u = U + V;
+                u = u >= twoQ ? u - twoQ : u;
+                x[i] = u;
+                x[i2] = shoup3<QLOW1>(U - V + twoQ, W, Wsh, Q, twoQ);
+            }
         }
     }
 }
@@ -241,8 +247,7 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
             } else if constexpr (LAZY) {
                 v = v - __umul64hi(v, one_sh) * Q;     // Shoup with w = 1: [0, 2Q)
             } else {
-                v = v >= twoQ ? v - twoQ : v;
-                v = v >= Q ? v - Q : v;
+                v = csub64(csub64(v, twoQ), Q);
             }
             x[i] = v;
         }
@@ -281,7 +286,7 @@ __device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap 
         load_field<LOGN - 4>(x, r, l);
         inv_phase<LOGN, LOGN - 4, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), QLOW1, TWS>(x, l, itwp, Q, twoQ);
 #pragma unroll
-        for (int i = 0; i < 16; i++) x[i] = x[i] >= Q ? x[i] - Q : x[i];
+        for (int i = 0; i < 16; i++) x[i] = csub64(x[i], Q);
     }
 }
 
