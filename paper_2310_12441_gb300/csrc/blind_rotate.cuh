@@ -204,13 +204,19 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     const u32 ncomb = 4 * lB;
     const size_t rgsw = (size_t)2 * lB * 2 * N;
 
-    // bv: a key word stored pre-split, low limb | high limb << 32
+    // bv: a key word stored pre-split, low limb | high limb << 32.  The three
+    // limb products accumulate with mad.wide.u32 (one multiplier instruction
+    // each, the addition included).
     auto kara = [&](u64 xv, u64 bv, u64 &kh, u64 &kl, u64 &km) {
         const u32 x0 = (u32)(xv & lmask), x1 = (u32)(xv >> lbits);
-        const u32 b0 = (u32)bv, b1 = (u32)(bv >> 32);
-        kh += (u64)x1 * b1;
-        kl += (u64)x0 * b0;
-        km += (u64)(x0 + x1) * (b0 + b1);
+        asm("{\n\t.reg .u32 b0, b1, xs, bs;\n\t"
+            "mov.b64 {b0, b1}, %5;\n\t"
+            "add.u32 xs, %3, %4;\n\tadd.u32 bs, b0, b1;\n\t"
+            "mad.wide.u32 %0, %4, b1, %0;\n\t"
+            "mad.wide.u32 %1, %3, b0, %1;\n\t"
+            "mad.wide.u32 %2, xs, bs, %2;\n\t}"
+            : "+l"(kh), "+l"(kl), "+l"(km)
+            : "r"(x0), "r"(x1), "l"(bv));
     };
 
     u64 *cur = acc0, *nxt = acc1;
@@ -239,16 +245,28 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                     rexp[g][sg] = e >= 2 * N ? e - 2 * N : e;
                 }
             if constexpr (C::DSM) {
-                // D_(row, sign, comp) = P(c) ACC - ACC
-                for (u32 w = tid; w < 4u * G * N; w += C::kThreads) {
-                    const u32 g = w / (4 * N), pair = (w / N) & 3, idx = w % N;
+                // D_(row, sign, comp) = P(c) ACC - ACC: coefficient idx of
+                // x^e src is src[idx - e] for idx >= e, else -src[idx - e + N]
+                // (e < N; for e >= N the two cases swap sign)
+#pragma unroll
+                for (int g = 0; g < G; g++) {
                     const u32 r = r0 + g;
-                    if (r < m) {
+                    if (G > 1 && r >= m) continue;
+#pragma unroll
+                    for (int pair = 0; pair < 4; pair++) {
                         const u32 sgn = pair >> 1, comp = pair & 1;
-                        const u64 *srow = cur + ((size_t)rsrc[g][sgn] * 2 + comp) * N;
-                        const u64 *orow = cur + ((size_t)r * 2 + comp) * N;
-                        dbuf[w] = sub_mod(rotated_coeff(srow, idx, rexp[g][sgn], N, Q, split),
-                                          acc_load(orow + idx, split), Q);
+                        const u64 *srow = cur + (rsrc[g][sgn] * 2 + comp) * (u32)N;
+                        const u64 *orow = cur + (r * 2 + comp) * (u32)N;
+                        u64 *drow = dbuf + (g * 4 + pair) * N;
+                        const u32 e = rexp[g][sgn];
+                        const bool flip = e >= (u32)N;
+                        const u32 es = flip ? e - N : e;
+                        for (u32 idx = tid; idx < (u32)N; idx += C::kThreads) {
+                            const bool wrap = idx < es;
+                            const u64 v = acc_load(srow + (wrap ? idx + N - es : idx - es), split);
+                            const u64 sv = (wrap != flip) ? sub_mod(0, v, Q) : v;
+                            drow[idx] = sub_mod(sv, acc_load(orow + idx, split), Q);
+                        }
                     }
                 }
                 __syncthreads();
