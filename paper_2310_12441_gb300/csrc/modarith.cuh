@@ -141,18 +141,29 @@ __device__ __forceinline__ void mac128(u64 &lo, u64 &hi, u64 a, u64 b) {
         : "l"(a), "l"(b));
 }
 
-// (hi:lo) += a, exact 128-bit accumulation of a 64-bit value.
+// (hi:lo) += a, exact 128-bit accumulation of a 64-bit value (a 32-bit
+// add-with-carry chain).
 __device__ __forceinline__ void add128(u64 &lo, u64 &hi, u64 a) {
-    asm("add.cc.u64 %0, %0, %2;\n\t"
-        "addc.u64 %1, %1, 0;"
+    asm("{\n\t.reg .u32 l0, l1, h0, h1, a0, a1;\n\t"
+        "mov.b64 {l0, l1}, %0;\n\tmov.b64 {h0, h1}, %1;\n\tmov.b64 {a0, a1}, %2;\n\t"
+        "add.cc.u32 l0, l0, a0;\n\taddc.cc.u32 l1, l1, a1;\n\t"
+        "addc.cc.u32 h0, h0, 0;\n\taddc.u32 h1, h1, 0;\n\t"
+        "mov.b64 %0, {l0, l1};\n\tmov.b64 %1, {h0, h1};\n\t}"
         : "+l"(lo), "+l"(hi)
         : "l"(a));
 }
 
 // (hi:lo) += v << sh for 0 < sh < 64.
 __device__ __forceinline__ void add128_shl(u64 &lo, u64 &hi, u64 v, u32 sh) {
-    add128(lo, hi, v << sh);
-    hi += v >> (64 - sh);
+    const u64 vl = v << sh, vh = v >> (64 - sh);
+    asm("{\n\t.reg .u32 l0, l1, h0, h1, a0, a1, b0, b1;\n\t"
+        "mov.b64 {l0, l1}, %0;\n\tmov.b64 {h0, h1}, %1;\n\t"
+        "mov.b64 {a0, a1}, %2;\n\tmov.b64 {b0, b1}, %3;\n\t"
+        "add.cc.u32 l0, l0, a0;\n\taddc.cc.u32 l1, l1, a1;\n\t"
+        "addc.cc.u32 h0, h0, b0;\n\taddc.u32 h1, h1, b1;\n\t"
+        "mov.b64 %0, {l0, l1};\n\tmov.b64 %1, {h0, h1};\n\t}"
+        : "+l"(lo), "+l"(hi)
+        : "l"(vl), "l"(vh));
 }
 
 // (hi 2^64 + lo) mod Q, any hi, lo < 2^64:  hi * (2^64 mod Q) + lo, each term
@@ -277,4 +288,35 @@ __device__ __forceinline__ void bfly_gs_qlow1(u64 &U, u64 &V, u64 W, u64 Wsh, u3
     const u64 u = csub64(add64c(U, V), twoQ);
     V = csub64(shoup3_qlow1_lazy(sub64c(add64c(U, twoQ), V), W, Wsh, c), twoQ);
     U = u;
+}
+
+// First forward stage on small digits (LAZY with SMALL0): y < 2^32, so W y is
+// formed exactly, W y = w0 y + (w1 y) 2^32, and left unreduced:
+// X <- X + W y, Y <- X - W y + qb (qb = Q B >= W y).
+__device__ __forceinline__ void small_bfly(u64 &X, u64 &Y, u64 W, u64 qb) {
+    asm("{\n\t.reg .u32 x0, x1, y0, y1, w0, w1, t0, t1, b0, b1, u0, u1;\n\t.reg .u64 t;\n\t"
+        "mov.b64 {x0, x1}, %0;\n\tmov.b64 {y0, y1}, %1;\n\t"
+        "mov.b64 {w0, w1}, %2;\n\tmov.b64 {b0, b1}, %3;\n\t"
+        "mul.wide.u32 t, w0, y0;\n\tmov.b64 {t0, t1}, t;\n\t"
+        "mad.lo.u32 t1, w1, y0, t1;\n\t"
+        "add.cc.u32 u0, x0, t0;\n\taddc.u32 u1, x1, t1;\n\t"
+        "add.cc.u32 x0, x0, b0;\n\taddc.u32 x1, x1, b1;\n\t"
+        "sub.cc.u32 x0, x0, t0;\n\tsubc.u32 x1, x1, t1;\n\t"
+        "mov.b64 %0, {u0, u1};\n\tmov.b64 %1, {x0, x1};\n\t}"
+        : "+l"(X), "+l"(Y)
+        : "l"(W), "l"(qb));
+}
+
+// v - qe Q with qe = floor((v >> 32) s / 2^32), s = floor(2^64 / Q) < 2^32,
+// Q = c 2^32 + 1: qe is at most 2 below floor(v / Q), result in [0, 3Q).
+__device__ __forceinline__ u64 reduce_est_qlow1(u64 v, u32 s, u32 c) {
+    u64 r;
+    asm("{\n\t.reg .u32 v0, v1, qe, qc;\n\t"
+        "mov.b64 {v0, v1}, %1;\n\t"
+        "mul.hi.u32 qe, v1, %2;\n\t"
+        "mul.lo.u32 qc, qe, %3;\n\t"
+        "sub.cc.u32 v0, v0, qe;\n\tsubc.u32 v1, v1, qc;\n\t"
+        "mov.b64 %0, {v0, v1};\n\t}"
+        : "=l"(r) : "l"(v), "r"(s), "r"(c));
+    return r;
 }

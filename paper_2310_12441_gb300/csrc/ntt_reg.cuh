@@ -95,11 +95,7 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__rest
             }
             if constexpr (LAZY && SMALL0 && S0 == 0) {
                 if (st == 0) {
-                    const u32 y = (u32)x[i2];
-                    const u64 T = (u64)(u32)W * y + ((u64)((u32)(W >> 32) * y) << 32);
-                    const u64 X = x[i];
-                    x[i] = X + T;
-                    x[i2] = X - T + qb;
+                    small_bfly(x[i], x[i2], W, qb);
                     continue;
                 }
             }
@@ -242,8 +238,7 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
                 // Q = c 2^32 + 1 > 2^32, so floor(2^64 / Q) < 2^32 and the
                 // estimate floor((v >> 32) floor(2^64/Q) / 2^32) lies at most
                 // 2 below floor(v / Q): one 32-bit high product, [0, 3Q)
-                const u32 qe = __umulhi((u32)(v >> 32), (u32)one_sh);
-                v -= times_q<true>(qe, Q);
+                v = reduce_est_qlow1(v, (u32)one_sh, (u32)(Q >> 32));
             } else if constexpr (LAZY) {
                 v = v - __umul64hi(v, one_sh) * Q;     // Shoup with w = 1: [0, 2Q)
             } else {
