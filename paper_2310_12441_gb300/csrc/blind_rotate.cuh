@@ -163,7 +163,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     const ModQ mq = K->mq;
     const u64 Q = mq.Q;
     const u32 qp = 2u * N * m;                 // 2Nm < 2^20
-    const u64 Bmask = (1ull << log2B) - 1;
+    const u32 Bmask = (u32)((1ull << log2B) - 1);   // digits fit 32 bits (log2 B <= 32)
     const u64 *twp = K->twp, *itwp = K->itwp;
     const u32 tid = threadIdx.x;
     const size_t vec = (size_t)m * 2 * N;
@@ -281,7 +281,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                     if constexpr (C::DSM) {
                         const u64 *dp = dbuf + ((size_t)pg * 4 + pair) * N;
 #pragma unroll
-                        for (int i = 0; i < 16; i++) x[i] = (dp[l + C::T * i] >> sh) & Bmask;
+                        for (int i = 0; i < 16; i++) x[i] = (u32)(dp[l + C::T * i] >> sh) & Bmask;
                     } else {
                         const u32 sgn = pair >> 1, comp = pair & 1;
                         const u64 *srow = cur + ((size_t)rsrc[pg][sgn] * 2 + comp) * N;
@@ -291,7 +291,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                             const u32 idx = l + C::T * i;
                             const u64 D = sub_mod(rotated_coeff(srow, idx, rexp[pg][sgn], N, Q, split),
                                                   acc_load(orow + idx, split), Q);
-                            x[i] = (D >> sh) & Bmask;
+                            x[i] = (u32)(D >> sh) & Bmask;
                         }
                     }
                 }
