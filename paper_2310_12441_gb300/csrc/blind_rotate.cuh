@@ -409,7 +409,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 }
             }
             __syncthreads();
-            ntr::inv_from_smem<LOGN, QLOW1, C::DSM>(x, in, sw, l, active, itw_use, Q);
+            ntr::inv_from_smem<LOGN, QLOW1, C::DSM, LAZY && QLOW1>(x, in, sw, l, active, itw_use, Q, mq.one_sh);
             if (active) {
                 const size_t base = (size_t)u * N;
 #pragma unroll

@@ -48,7 +48,8 @@ struct DevJob {
 // Arithmetic variant of a key set (BR_V_* flags):
 //  - BR_V_LAZY: the correction-free forward transform needs
 //    (1 + 4 log2 N) Q < 2^64 and its exact first stage
-//    B + Q B + 4 Q (log2 N - 1) < 2^64 with B < 2^32;
+//    B + Q B + 4 Q (log2 N - 1) < 2^64 with B < 2^32; the correction-free
+//    inverse (with Q = c 2^32 + 1) needs 128 Q < 2^64;
 //  - BR_V_QLOW1: Q = c 2^32 + 1.
 inline u32 choose_variant(const bm_key_params &p) {
     typedef unsigned __int128 u128;
@@ -56,7 +57,8 @@ inline u32 choose_variant(const bm_key_params &p) {
     while ((1u << logN) < p.N) logN++;
     const u128 lim = (u128)1 << 64, Q = p.Q, B = (u128)1 << p.log2_B;
     u32 v = 0;
-    if ((1 + 4 * (u128)logN) * Q < lim && p.log2_B <= 31 && B + Q * B + 4 * Q * (logN - 1) < lim)
+    if ((1 + 4 * (u128)logN) * Q < lim && p.log2_B <= 31 && B + Q * B + 4 * Q * (logN - 1) < lim &&
+        128 * Q < lim)
         v |= BR_V_LAZY;
     if ((p.Q & 0xffffffffull) == 1) v |= BR_V_QLOW1;
     return v;

@@ -320,3 +320,13 @@ __device__ __forceinline__ u64 reduce_est_qlow1(u64 v, u32 s, u32 c) {
         : "=l"(r) : "l"(v), "r"(s), "r"(c));
     return r;
 }
+
+// Gentleman-Sande inverse butterfly without corrections (Q = c 2^32 + 1):
+// U <- U + V, V <- (U - V + q64) W mod Q in [0, 4Q), where q64 is a multiple
+// of Q above every V.  Values below b grow to below max(2b, 4Q) per stage;
+// the caller reduces them between radix-16 phases (see ntr::inv_from_smem).
+__device__ __forceinline__ void bfly_gs_lazy_qlow1(u64 &U, u64 &V, u64 W, u64 Wsh, u32 c, u64 q64) {
+    const u64 u = add64c(U, V);
+    V = shoup3_qlow1_lazy(sub64c(add64c(U, q64), V), W, Wsh, c);
+    U = u;
+}

@@ -120,7 +120,7 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__rest
 }
 
 // Inverse phase: NST stages acting on bits SB, SB+1, ..., field [F, F+4).
-template <int LOGN, int F, int SB, int NST, bool QLOW1 = false, bool TWS = false>
+template <int LOGN, int F, int SB, int NST, bool QLOW1 = false, bool TWS = false, bool LZI = false>
 __device__ __forceinline__ void inv_phase(u64 (&x)[16], u32 l, const u64 *__restrict__ itwp, u64 Q,
                                           u64 twoQ) {
     const u32 high = l >> F;
@@ -141,7 +141,9 @@ __device__ __forceinline__ void inv_phase(u64 (&x)[16], u32 l, const u64 *__rest
             } else {
                 twiddle<false>(itwp, (1u << (LOGN - 1 - b)) + g, W, Wsh);
             }
-            if constexpr (QLOW1) {
+            if constexpr (LZI) {
+                bfly_gs_lazy_qlow1(x[i], x[i2], W, Wsh, (u32)(Q >> 32), Q << 6);
+            } else if constexpr (QLOW1) {
                 bfly_gs_qlow1(x[i], x[i2], W, Wsh, (u32)(Q >> 32), twoQ);
             } else {
                 const u64 U = x[i], V = x[i2];
@@ -256,14 +258,26 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
 // transform (swizzled, values below 2Q) and the block has passed a barrier
 // since it was written; `in` must be the region sw wrote last.  On exit x
 // holds natural-order coefficients l + T i, reduced to [0, Q).
-template <int LOGN, bool QLOW1 = false, bool TWS = false>
+// LZI (Q = c 2^32 + 1 and 128 Q < 2^64): butterflies without corrections
+// (bfly_gs_lazy_qlow1 with q64 = 64 Q).  A phase of four stages takes values
+// below 3Q to below 48Q (3Q, 6Q, 12Q, 24Q, 48Q; inputs below Q reach 32Q),
+// so U - V + 64Q < 112Q < 2^64; between phases the values are brought back
+// below 3Q by reduce_est_qlow1 (one_sh = floor(2^64 / Q)).
+template <int LOGN, bool QLOW1 = false, bool TWS = false, bool LZI = false>
 __device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap &sw, u32 l, bool active,
-                                              const u64 *__restrict__ itwp, u64 Q) {
+                                              const u64 *__restrict__ itwp, u64 Q, u64 one_sh = 0) {
     constexpr int NPH = (LOGN + 3) / 4;
     const u64 twoQ = 2 * Q;
+    auto between = [&]() {
+        if constexpr (LZI) {
+#pragma unroll
+            for (int i = 0; i < 16; i++) x[i] = reduce_est_qlow1(x[i], (u32)one_sh, (u32)(Q >> 32));
+        }
+    };
     if (active) {
         load_field<0>(x, in, l);
-        inv_phase<LOGN, 0, 0, 4, QLOW1, TWS>(x, l, itwp, Q, twoQ);
+        inv_phase<LOGN, 0, 0, 4, QLOW1, TWS, LZI>(x, l, itwp, Q, twoQ);
+        between();
     }
     u64 *r = sw.take();
     if (active) store_field<0>(x, r, l);
@@ -271,7 +285,8 @@ __device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap 
     if constexpr (NPH == 3) {
         if (active) {
             load_field<4>(x, r, l);
-            inv_phase<LOGN, 4, 4, 4, QLOW1, TWS>(x, l, itwp, Q, twoQ);
+            inv_phase<LOGN, 4, 4, 4, QLOW1, TWS, LZI>(x, l, itwp, Q, twoQ);
+            between();
         }
         r = sw.take();
         if (active) store_field<4>(x, r, l);
@@ -279,9 +294,10 @@ __device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap 
     }
     if (active) {
         load_field<LOGN - 4>(x, r, l);
-        inv_phase<LOGN, LOGN - 4, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), QLOW1, TWS>(x, l, itwp, Q, twoQ);
+        inv_phase<LOGN, LOGN - 4, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), QLOW1, TWS, LZI>(x, l, itwp, Q, twoQ);
+        between();
 #pragma unroll
-        for (int i = 0; i < 16; i++) x[i] = csub64(x[i], Q);
+        for (int i = 0; i < 16; i++) x[i] = LZI ? csub64(csub64(x[i], twoQ), Q) : csub64(x[i], Q);
     }
 }
 
