@@ -272,21 +272,23 @@ __device__ __forceinline__ u64 shoup3_qlow1_lazy(u64 Y, u64 W, u64 Wsh, u32 c) {
     return T;
 }
 
-// Harvey's forward butterfly with corrections (values in [0, 4Q), 4Q < 2^64),
-// Q = c 2^32 + 1: X <- X' + T, Y <- X' + 2Q - T with X' = X mod 2Q in [0, 2Q)
-// and T = Y W mod Q in [0, 2Q).
-__device__ __forceinline__ void bfly_ct_qlow1(u64 &X, u64 &Y, u64 W, u64 Wsh, u32 c, u64 twoQ) {
-    const u64 Xr = csub64(X, twoQ);
-    const u64 T = csub64(shoup3_qlow1_lazy(Y, W, Wsh, c), twoQ);
+// Forward butterfly with one correction for Q = c 2^32 + 1 (Harvey's method
+// with the invariant widened to [0, 8Q), which Q < 2^61 allows):
+// X' = X mod 4Q in [0, 4Q), T = Y W mod Q in [0, 4Q) uncorrected;
+// X <- X' + T, Y <- X' + 4Q - T, both in [0, 8Q).
+__device__ __forceinline__ void bfly_ct_qlow1(u64 &X, u64 &Y, u64 W, u64 Wsh, u32 c, u64 fourQ) {
+    const u64 Xr = csub64(X, fourQ);
+    const u64 T = shoup3_qlow1_lazy(Y, W, Wsh, c);
     X = add64c(Xr, T);
-    Y = sub64c(add64c(Xr, twoQ), T);
+    Y = sub64c(add64c(Xr, fourQ), T);
 }
 
-// Gentleman-Sande inverse butterfly (values in [0, 2Q)), Q = c 2^32 + 1:
-// U <- (U + V) mod 2Q, V <- (U - V + 2Q) W mod Q in [0, 2Q).
-__device__ __forceinline__ void bfly_gs_qlow1(u64 &U, u64 &V, u64 W, u64 Wsh, u32 c, u64 twoQ) {
-    const u64 u = csub64(add64c(U, V), twoQ);
-    V = csub64(shoup3_qlow1_lazy(sub64c(add64c(U, twoQ), V), W, Wsh, c), twoQ);
+// Gentleman-Sande inverse butterfly with one correction, Q = c 2^32 + 1,
+// values in [0, 4Q): U <- (U + V) mod 4Q, V <- (U - V + 4Q) W mod Q in
+// [0, 4Q) uncorrected (the Shoup input stays below 8Q < 2^64).
+__device__ __forceinline__ void bfly_gs_qlow1(u64 &U, u64 &V, u64 W, u64 Wsh, u32 c, u64 fourQ) {
+    const u64 u = csub64(add64c(U, V), fourQ);
+    V = shoup3_qlow1_lazy(sub64c(add64c(U, fourQ), V), W, Wsh, c);
     U = u;
 }
 

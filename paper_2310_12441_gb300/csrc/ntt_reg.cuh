@@ -67,7 +67,9 @@ __device__ __forceinline__ void twiddle(const u64 *__restrict__ tp, u32 ti, u64 
 // LAZY: no per-stage corrections.  Products lie in [0, 4Q) and the sum and
 // difference X + T, X - T + 4Q each grow the bound by 4Q, so inputs below Q
 // leave the last stage below (1 + 4 LOGN) Q, which the caller guarantees
-// fits in 64 bits.  Otherwise Harvey's [0, 4Q) invariant is kept.
+// fits in 64 bits.  Otherwise Harvey's [0, 4Q) invariant is kept, widened to
+// [0, 8Q) with a single correction per butterfly when Q = c 2^32 + 1
+// (bfly_ct_qlow1).
 // SMALL0 (with LAZY): the first stage's inputs are digits below B < 2^32, so
 // W * Y is formed exactly (a 64 x 32-bit product) and left unreduced:
 // X + W Y and X - W Y + Q B, both below B + Q B.  The caller guarantees
@@ -107,7 +109,7 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__rest
                 x[i] = X + T;
                 x[i2] = X - T + 2 * twoQ;
             } else if constexpr (QLOW1) {
-                bfly_ct_qlow1(x[i], x[i2], W, Wsh, (u32)(Q >> 32), twoQ);
+                bfly_ct_qlow1(x[i], x[i2], W, Wsh, (u32)(Q >> 32), 2 * twoQ);
             } else {
                 u64 X = x[i];
                 X = X >= twoQ ? X - twoQ : X;
@@ -144,7 +146,7 @@ __device__ __forceinline__ void inv_phase(u64 (&x)[16], u32 l, const u64 *__rest
             if constexpr (LZI) {
                 bfly_gs_lazy_qlow1(x[i], x[i2], W, Wsh, (u32)(Q >> 32), Q << 6);
             } else if constexpr (QLOW1) {
-                bfly_gs_qlow1(x[i], x[i2], W, Wsh, (u32)(Q >> 32), twoQ);
+                bfly_gs_qlow1(x[i], x[i2], W, Wsh, (u32)(Q >> 32), 2 * twoQ);
             } else {
                 const u64 U = x[i], V = x[i2];
                 u64 u = U + V;
@@ -243,6 +245,8 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
                 v = reduce_est_qlow1(v, (u32)one_sh, (u32)(Q >> 32));
             } else if constexpr (LAZY) {
                 v = v - __umul64hi(v, one_sh) * Q;     // Shoup with w = 1: [0, 2Q)
+            } else if constexpr (QLOW1) {
+                v = csub64(csub64(csub64(v, 2 * twoQ), twoQ), Q);     // [0, 8Q) -> [0, Q)
             } else {
                 v = csub64(csub64(v, twoQ), Q);
             }
@@ -257,8 +261,9 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
 // Inverse NTT (without N^-1).  On entry region `in` holds the bit-reversed
 // transform (swizzled, values below 2Q) and the block has passed a barrier
 // since it was written; `in` must be the region sw wrote last.  On exit x
-// holds natural-order coefficients l + T i, reduced to [0, Q).
-// LZI (Q = c 2^32 + 1 and 128 Q < 2^64): butterflies without corrections
+// holds natural-order coefficients l + T i, reduced to [0, Q).  With
+// Q = c 2^32 + 1 the butterflies keep [0, 4Q) with one correction each
+// (bfly_gs_qlow1), or with LZI (Q = c 2^32 + 1 and 128 Q < 2^64) none
 // (bfly_gs_lazy_qlow1 with q64 = 64 Q).  A phase of four stages takes values
 // below 3Q to below 48Q (3Q, 6Q, 12Q, 24Q, 48Q; inputs below Q reach 32Q),
 // so U - V + 64Q < 112Q < 2^64; between phases the values are brought back
@@ -297,7 +302,8 @@ __device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap 
         inv_phase<LOGN, LOGN - 4, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), QLOW1, TWS, LZI>(x, l, itwp, Q, twoQ);
         between();
 #pragma unroll
-        for (int i = 0; i < 16; i++) x[i] = LZI ? csub64(csub64(x[i], twoQ), Q) : csub64(x[i], Q);
+        for (int i = 0; i < 16; i++)
+            x[i] = (LZI || QLOW1) ? csub64(csub64(x[i], twoQ), Q) : csub64(x[i], Q);
     }
 }
 
