@@ -261,11 +261,26 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                         const u32 e = rexp[g][sgn];
                         const bool flip = e >= (u32)N;
                         const u32 es = flip ? e - N : e;
-                        for (u32 idx = tid; idx < (u32)N; idx += C::kThreads) {
-                            const bool wrap = idx < es;
-                            const u64 v = acc_load(srow + (wrap ? idx + N - es : idx - es), split);
-                            const u64 sv = (wrap != flip) ? sub_mod(0, v, Q) : v;
-                            drow[idx] = sub_mod(sv, acc_load(orow + idx, split), Q);
+                        // all of this thread's loads of the row issued together
+                        constexpr int ITER = (N + C::kThreads - 1) / C::kThreads;
+                        u64 v[ITER], o[ITER];
+#pragma unroll
+                        for (int it = 0; it < ITER; it++) {
+                            const u32 idx = tid + it * C::kThreads;
+                            if (idx < (u32)N) {
+                                const bool wrap = idx < es;
+                                v[it] = acc_load(srow + (wrap ? idx + N - es : idx - es), split);
+                                o[it] = acc_load(orow + idx, split);
+                            }
+                        }
+#pragma unroll
+                        for (int it = 0; it < ITER; it++) {
+                            const u32 idx = tid + it * C::kThreads;
+                            if (idx < (u32)N) {
+                                const bool wrap = idx < es;
+                                const u64 sv = (wrap != flip) ? sub_mod(0, v[it], Q) : v[it];
+                                drow[idx] = sub_mod(sv, o[it], Q);
+                            }
                         }
                     }
                 }

@@ -523,3 +523,33 @@ def test_sweep_key_shape_bit_exact(api, orc):
     out = api.from_device_u64(d_out).reshape(2, kp.n + 1)
     assert np.array_equal(out, orc.bootstrap_arbitrary(kp, m, t, q, ks.bsk, ks.ksk, cti, f))
     assert np.array_equal(api.bm_decrypt(ks.sk, q, 2 * t, out), x % t)
+
+
+def test_empty_batches_are_no_ops(api, toy):
+    """Zero jobs: the batch call and the two-round call return success and
+    write nothing; a reusable batch of zero jobs is refused."""
+    jobs = np.zeros(0, dtype=api.JOB_DTYPE)
+    d_in = api.to_device_u64(np.arange(65, dtype=np.uint64))
+    d_lut = api.to_device_u32(np.zeros(32, np.uint32))
+    d_out = torch.full((65,), 7, dtype=torch.int64, device="cuda")
+    ws = api.workspace(api.bm_workspace_bytes([toy.ek], jobs))
+    api.bm_bootstrap_batch([toy.ek], jobs, d_in, d_lut, d_out, ws)
+    api.bm_bootstrap_arbitrary(toy.ek, 2, 4, 1 << 14, d_lut, 0, d_in, d_out, ws)
+    torch.cuda.synchronize()
+    assert api.bm_workspace_status(ws) == 0
+    assert bool((d_out == 7).all())
+    with pytest.raises(api.BMError):
+        api.Batch([toy.ek], jobs, d_in, d_lut, d_out, ws)
+
+
+def test_blind_rotate_plaintext_space_fills_the_exponents(api, orc, toy):
+    """t = 2Nm, the largest plaintext the test vector holds (one table entry
+    per exponent of the orbit, Delta = 1): still bit-exact."""
+    kp, m = toy.kp, 2
+    t = 2 * kp.N * m
+    _, ct = _encrypt(orc, toy, m, t, 2, 77, prefix=3)
+    luts, _ = synth.luts(t, 2, 2077)
+    jobs = _uniform_jobs(api, 2, kp.n, t, m)
+    got = _blind_rotate_gpu(api, toy, jobs, ct, luts, 1 << 30)
+    for i in range(2):
+        assert np.array_equal(got[i], orc.blind_rotate(kp, m, t, toy.bsk, ct[i], luts[i])), i
