@@ -252,9 +252,10 @@ bm_status bm_bootstrap_arbitrary(const bm_eval_key *key, uint32_t m, uint32_t t,
  * workspace: BM_OK or the first device-side error recorded. */
 bm_status bm_workspace_status(void *d_ws, void *stream);
 
-/* Throughput probe of the library's Shoup modular multiplication (the
- * integer-ALU roofline denominator): runs `iters` dependent-chain steps on
- * every thread of a full-device grid and returns modmuls/s in *rate. */
+/* Throughput probe of the modular multiplication the blind rotation uses
+ * (three-product Shoup for Q = c 2^32 + 1, the integer-ALU roofline
+ * denominator): runs `iters` steps of eight independent chains on every
+ * thread of a full-device grid and returns modmuls/s in *rate. */
 bm_status bm_modmul_peak(int device, uint32_t iters, double *rate);
 
 /* Bootstrapping for callers that cannot allocate device memory (no

@@ -205,18 +205,22 @@ __global__ void k_lwe_sub(const u64 *__restrict__ x, const u64 *__restrict__ y, 
 }
 
 // Throughput probe: independent Shoup multiplication chains per thread.
-__global__ void k_modmul_probe(u64 *out, u32 iters, u64 Q, u64 w, u64 wsh) {
+// Throughput probe of the blind rotation's own modular product: the
+// three-product Shoup multiplication for Q = c 2^32 + 1 on 32-bit
+// add-with-carry chains (shoup3_qlow1_lazy), eight independent chains per
+// thread; every output in [0, 4Q) is a valid next input.
+__global__ void k_modmul_probe(u64 *out, u32 iters, u32 c, u64 w, u64 wsh) {
     u64 x0 = threadIdx.x + 1, x1 = x0 + 7, x2 = x0 + 13, x3 = x0 + 29;
     u64 x4 = x0 + 31, x5 = x0 + 37, x6 = x0 + 41, x7 = x0 + 43;
     for (u32 i = 0; i < iters; i++) {
-        x0 = mul_shoup_lazy(x0, w, wsh, Q);
-        x1 = mul_shoup_lazy(x1, w, wsh, Q);
-        x2 = mul_shoup_lazy(x2, w, wsh, Q);
-        x3 = mul_shoup_lazy(x3, w, wsh, Q);
-        x4 = mul_shoup_lazy(x4, w, wsh, Q);
-        x5 = mul_shoup_lazy(x5, w, wsh, Q);
-        x6 = mul_shoup_lazy(x6, w, wsh, Q);
-        x7 = mul_shoup_lazy(x7, w, wsh, Q);
+        x0 = shoup3_qlow1_lazy(x0, w, wsh, c);
+        x1 = shoup3_qlow1_lazy(x1, w, wsh, c);
+        x2 = shoup3_qlow1_lazy(x2, w, wsh, c);
+        x3 = shoup3_qlow1_lazy(x3, w, wsh, c);
+        x4 = shoup3_qlow1_lazy(x4, w, wsh, c);
+        x5 = shoup3_qlow1_lazy(x5, w, wsh, c);
+        x6 = shoup3_qlow1_lazy(x6, w, wsh, c);
+        x7 = shoup3_qlow1_lazy(x7, w, wsh, c);
     }
     out[blockIdx.x * blockDim.x + threadIdx.x] = x0 ^ x1 ^ x2 ^ x3 ^ x4 ^ x5 ^ x6 ^ x7;
 }
@@ -775,14 +779,16 @@ extern "C" bm_status bm_modmul_peak(int device, uint32_t iters, double *rate) {
     const u32 blocks = (u32)sms * 8, threads = 256;
     u64 *d_out = nullptr;
     BM_CUDA_TRY(cudaMalloc(&d_out, (size_t)blocks * threads * 8));
-    const u64 Q = 18014398509404161ull, w = 123456789012345ull;
+    // the n = 630, N = 1024 key's modulus, Q = c 2^32 + 1
+    const u64 Q = 18014359854776321ull, w = 123456789012345ull;
     const u64 wsh = (u64)(((unsigned __int128)w << 64) / Q);
+    const u32 c = (u32)(Q >> 32);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    k_modmul_probe<<<blocks, threads>>>(d_out, iters / 8 + 1, Q, w, wsh);   // warm-up
+    k_modmul_probe<<<blocks, threads>>>(d_out, iters / 8 + 1, c, w, wsh);   // warm-up
     cudaEventRecord(e0);
-    k_modmul_probe<<<blocks, threads>>>(d_out, iters, Q, w, wsh);
+    k_modmul_probe<<<blocks, threads>>>(d_out, iters, c, w, wsh);
     cudaEventRecord(e1);
     cudaError_t err = cudaEventSynchronize(e1);
     float ms = 0;
