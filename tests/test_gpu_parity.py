@@ -553,3 +553,26 @@ def test_blind_rotate_plaintext_space_fills_the_exponents(api, orc, toy):
     got = _blind_rotate_gpu(api, toy, jobs, ct, luts, 1 << 30)
     for i in range(2):
         assert np.array_equal(got[i], orc.blind_rotate(kp, m, t, toy.bsk, ct[i], luts[i])), i
+
+
+def test_prefix_parity_1024_ciphertexts(api, orc, n1024):
+    """1024 ciphertexts of the n = 630, N = 1024, m = 4 set whose masks vanish
+    after 8 entries: ACC after the 8 CMux steps equals the oracle's on sampled
+    jobs; the full bootstraps of all 1024 agree between the grouped and the
+    persistent launch and decrypt to f(Dec(input))."""
+    kp, m, t, cnt = n1024.kp, 4, 1024, 1024
+    _, ct = _encrypt(orc, n1024, m, t, cnt, 88, prefix=8)
+    luts, _ = synth.luts(t, cnt, 2088)
+    jobs = _uniform_jobs(api, cnt, kp.n, t, m)
+    acc = _blind_rotate_gpu(api, n1024, jobs, ct, luts, 8)
+    for i in (0, 511, 1023):
+        assert np.array_equal(acc[i], orc.blind_rotate(kp, m, t, n1024.bsk, ct[i], luts[i])), i
+    W = kp.n + 1
+    grouped = _run_batch(api, [n1024.ek], jobs, ct, luts, cnt * W)
+    d_in, d_lut = api.to_device_u64(ct.ravel()), api.to_device_u32(luts.ravel())
+    persistent = api.from_device_u64(_device_run(api, [n1024.ek], jobs, d_in, d_lut, cnt * W,
+                                                 api.BATCH_PERSISTENT))
+    assert np.array_equal(grouped, persistent)
+    dec_in = api.bm_decrypt(n1024.sk, 2 * kp.N * m, t, ct)
+    dec_out = api.bm_decrypt(n1024.sk, kp.Q, t, grouped.reshape(cnt, W))
+    assert np.array_equal(dec_out, luts[np.arange(cnt), dec_in])
