@@ -29,27 +29,6 @@ __device__ __forceinline__ u64 mul_shoup_lazy(u64 a, u64 w, u64 wsh, u64 Q) {
     return a * w - q * Q;
 }
 
-// a * w mod Q in [0, 2Q), Shoup with the quotient taken from three of the
-// four 32 x 32-bit partial products of a * w': dropping a_lo * w'_lo and the
-// carries of the middle terms leaves an estimate at most 2 below
-// floor(a w' / 2^64), so a w - q Q lies in [0, 4Q); one conditional
-// subtraction of 2Q restores [0, 2Q).  Needs 4Q < 2^64.
-__device__ __forceinline__ u64 mul_shoup_q3(u64 a, u64 w, u64 wsh, u64 Q, u64 twoQ) {
-    const u32 a0 = (u32)a, a1 = (u32)(a >> 32);
-    const u32 s0 = (u32)wsh, s1 = (u32)(wsh >> 32);
-    const u64 q = (u64)a1 * s1 + __umulhi(a1, s0) + __umulhi(a0, s1);
-    const u64 r = a * w - q * Q;
-    return r >= twoQ ? r - twoQ : r;
-}
-
-// Same estimate without the final correction: result in [0, 4Q).
-__device__ __forceinline__ u64 mul_shoup_q3_lazy(u64 a, u64 w, u64 wsh, u64 Q) {
-    const u32 a0 = (u32)a, a1 = (u32)(a >> 32);
-    const u32 s0 = (u32)wsh, s1 = (u32)(wsh >> 32);
-    const u64 q = (u64)a1 * s1 + __umulhi(a1, s0) + __umulhi(a0, s1);
-    return a * w - q * Q;
-}
-
 // q * Q mod 2^64; when Q = c 2^32 + 1 (QLOW1), q Q = q + (q mod 2^32) c 2^32
 // modulo 2^64, one 32-bit multiply.
 template <bool QLOW1>
@@ -61,8 +40,11 @@ __device__ __forceinline__ u64 times_q(u64 q, u64 Q) {
     }
 }
 
-// Three-product Shoup (see mul_shoup_q3) without the final correction, for
-// either kind of modulus: result in [0, 4Q).
+// a * w mod Q by Shoup's method with the quotient taken from three of the
+// four 32 x 32-bit partial products of a * w': dropping a_lo * w'_lo and the
+// carries of the middle terms leaves an estimate at most 2 below
+// floor(a w' / 2^64), so a w - q Q lies in [0, 4Q) (needs 4Q < 2^64).  No
+// final correction; shoup3 adds one (result in [0, 2Q)).
 template <bool QLOW1>
 __device__ __forceinline__ u64 shoup3_lazy(u64 a, u64 w, u64 wsh, u64 Q) {
     const u32 a0 = (u32)a, a1 = (u32)(a >> 32);
