@@ -322,6 +322,20 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 // sums as hi 2^(2 lbits) + (mid - hi - lo) 2^lbits + lo.
                 const u64 *bsk_c0 = bsk_k + (size_t)c0 * 2 * N;
                 const u32 nc = ncomb - c0 < (u32)CPB ? ncomb - c0 : (u32)CPB;
+                const bool full = nc == (u32)CPB && !fold_each;
+                // Small batches (CPB <= 4) load the next position's key words while
+                // the current one is multiplied (two buffers of CPB x 2 words).
+                constexpr bool PIPE = CPB <= 4 && C::PPT > 1 && (int)C::kThreads * C::PPT == N;
+                u64 bnext[PIPE ? CPB : 1][2];
+                if constexpr (PIPE) {
+                    if (full) {
+#pragma unroll
+                        for (int cc = 0; cc < CPB; cc++) {
+                            bnext[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + tid);
+                            bnext[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + tid);
+                        }
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < C::PPT; j++) {
                     const u32 q = tid + C::kThreads * j;
@@ -341,13 +355,28 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                                     kh[g][col] = kl[g][col] = km[g][col] = 0;
                                 }
                         };
-                        if (nc == (u32)CPB && !fold_each) {
+                        if (full) {
                             // full batch: the position's key words are requested first
                             u64 bv[CPB][2];
+                            if constexpr (PIPE) {
 #pragma unroll
-                            for (int cc = 0; cc < CPB; cc++) {
-                                bv[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q);
-                                bv[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q);
+                                for (int cc = 0; cc < CPB; cc++) {
+                                    bv[cc][0] = bnext[cc][0];
+                                    bv[cc][1] = bnext[cc][1];
+                                }
+                                if (j + 1 < C::PPT) {
+#pragma unroll
+                                    for (int cc = 0; cc < CPB; cc++) {
+                                        bnext[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q + C::kThreads);
+                                        bnext[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q + C::kThreads);
+                                    }
+                                }
+                            } else {
+#pragma unroll
+                                for (int cc = 0; cc < CPB; cc++) {
+                                    bv[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q);
+                                    bv[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q);
+                                }
                             }
 #pragma unroll
                             for (int cc = 0; cc < CPB; cc++)
