@@ -40,7 +40,7 @@ METRIC = "bootstraps/s on 1 GB300 (batched, bit-exact)"
 # of this workload (profiles/k_blind_rotate_n630_N1024_m4.md), valid while
 # the kernel sources hash to the captured version.
 KERNEL_SOURCES = ["blind_rotate.cuh", "ntt_reg.cuh", "modarith.cuh", "common.cuh", "bootstrap.cu"]
-CAPTURED_TRAFFIC = {"hash": "ed96d14802d0318f", "bytes_per_job": (258.108416e6 + 10.327296e6) / 152}
+CAPTURED_TRAFFIC = {"hash": "420eedf6f471f001", "bytes_per_job": (255.315456e6 + 5.345536e6) / 152}
 
 
 def kernel_hash():

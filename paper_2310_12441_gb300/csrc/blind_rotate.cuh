@@ -323,14 +323,16 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 const u64 *bsk_c0 = bsk_k + (size_t)c0 * 2 * N;
                 const u32 nc = ncomb - c0 < (u32)CPB ? ncomb - c0 : (u32)CPB;
                 const bool full = nc == (u32)CPB && !fold_each;
-                // Small batches (CPB <= 4) load the next position's key words while
-                // the current one is multiplied (two buffers of CPB x 2 words).
-                constexpr bool PIPE = CPB <= 4 && C::PPT > 1 && (int)C::kThreads * C::PPT == N;
-                u64 bnext[PIPE ? CPB : 1][2];
+                // The next position's key words for the first PRE combos (all of a
+                // batch of at most 4, half of a larger one) are loaded while the
+                // current position is multiplied.
+                constexpr bool PIPE = C::PPT > 1 && (int)C::kThreads * C::PPT == N;
+                constexpr int PRE = CPB <= 4 ? CPB : CPB / 2;
+                u64 bnext[PIPE ? PRE : 1][2];
                 if constexpr (PIPE) {
                     if (full) {
 #pragma unroll
-                        for (int cc = 0; cc < CPB; cc++) {
+                        for (int cc = 0; cc < PRE; cc++) {
                             bnext[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + tid);
                             bnext[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + tid);
                         }
@@ -360,13 +362,18 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                             u64 bv[CPB][2];
                             if constexpr (PIPE) {
 #pragma unroll
-                                for (int cc = 0; cc < CPB; cc++) {
+                                for (int cc = 0; cc < PRE; cc++) {
                                     bv[cc][0] = bnext[cc][0];
                                     bv[cc][1] = bnext[cc][1];
                                 }
+#pragma unroll
+                                for (int cc = PRE; cc < CPB; cc++) {
+                                    bv[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q);
+                                    bv[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q);
+                                }
                                 if (j + 1 < C::PPT) {
 #pragma unroll
-                                    for (int cc = 0; cc < CPB; cc++) {
+                                    for (int cc = 0; cc < PRE; cc++) {
                                         bnext[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q + C::kThreads);
                                         bnext[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q + C::kThreads);
                                     }
