@@ -70,6 +70,23 @@ def lib():
         L.orc_bootstrap.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_uint32, u64p, C.c_uint32,
                                     u64p, u64p, u32p, C.c_size_t, u64p]
         L.orc_bootstrap.restype = C.c_int
+        L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.orc_draw_uniform.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64]
+        L.orc_draw_uniform.restype = C.c_uint64
+        L.orc_draw_ternary.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64]
+        L.orc_draw_ternary.restype = C.c_int
+        L.orc_draw_binary.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64]
+        L.orc_draw_binary.restype = C.c_int
+        L.orc_cdt.argtypes = [C.c_double, u64p]
+        L.orc_draw_gaussian.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, u64p]
+        L.orc_draw_gaussian.restype = C.c_int
+        L.orc_seeded_lwe_secret.argtypes = [C.c_uint32, C.c_int, C.c_uint64, i8p]
+        L.orc_seeded_rlwe_secret.argtypes = [C.c_uint32, C.c_uint64, i8p]
+        L.orc_seeded_bsk_randomness.argtypes = [C.POINTER(_Params), C.c_double, C.c_uint64, C.c_uint32,
+                                                u64p, i8p]
+        L.orc_seeded_ksk_randomness.argtypes = [C.POINTER(_Params), C.c_double, C.c_uint64, u64p, i8p]
+        L.orc_seeded_enc_randomness.argtypes = [C.c_uint32, C.c_uint64, C.c_double, C.c_uint64,
+                                                C.c_size_t, u64p, i8p]
         _lib = L
     return _lib
 
@@ -287,3 +304,84 @@ def bootstrap_arbitrary(kp, m: int, t: int, q: int, bsk, ksk, ct_in, f) -> np.nd
     if rc != 0:
         raise ValueError("ciphertext uses a bootstrapping key that was not provided")
     return out
+
+
+# -- seeded randomness (Philox4x32-10 streams; see bootmmpm_oracle.c) ---------------
+
+ERR_CUT = 41
+KIND = {"lwe_secret": 1, "rlwe_secret": 2, "bsk_mask": 3, "bsk_err": 4, "ksk_mask": 5,
+        "ksk_err": 6, "enc_mask": 7, "enc_err": 8}
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c, pc = _p(ctr, np.uint32, u32p)
+    k, pk = _p(key, np.uint32, u32p)
+    out = np.empty(4, np.uint32)
+    lib().orc_philox4x32_10(pc, pk, out.ctypes.data_as(u32p))
+    return out
+
+
+def draw_uniform(seed: int, kind: int, domain: int, i: int, modulus: int) -> int:
+    return int(lib().orc_draw_uniform(seed, kind, domain, i, modulus))
+
+
+def draw_ternary(seed: int, kind: int, domain: int, i: int) -> int:
+    return int(lib().orc_draw_ternary(seed, kind, domain, i))
+
+
+def draw_binary(seed: int, kind: int, domain: int, i: int) -> int:
+    return int(lib().orc_draw_binary(seed, kind, domain, i))
+
+
+def cdt(sigma: float) -> np.ndarray:
+    T = np.empty(2 * ERR_CUT, np.uint64)
+    lib().orc_cdt(sigma, T.ctypes.data_as(u64p))
+    return T
+
+
+def draw_gaussian(seed: int, kind: int, domain: int, i: int, T) -> int:
+    T, pt = _p(T, np.uint64, u64p)
+    return int(lib().orc_draw_gaussian(seed, kind, domain, i, pt))
+
+
+def seeded_key_randomness(kp, seed: int, bsk_keys: int | None = None, with_ksk: bool = True) -> dict:
+    """The randomness of key generation drawn from `seed` by the Philox stream
+    layout (same shapes as the array-taking keygen functions read)."""
+    n, N, lB = kp.n, kp.N, kp.l_B
+    K = n if bsk_keys is None else int(bsk_keys)
+    L = lib()
+    s = np.empty(n, np.int8)
+    L.orc_seeded_lwe_secret(n, int(kp.secret == "ternary"), seed, s.ctypes.data_as(i8p))
+    z = np.empty(N, np.int8)
+    L.orc_seeded_rlwe_secret(N, seed, z.ctypes.data_as(i8p))
+    prm = _params(kp)
+    bm = np.empty((K, 2, 2 * lB, N), np.uint64)
+    be = np.empty((K, 2, 2 * lB, N), np.int8)
+    L.orc_seeded_bsk_randomness(C.byref(prm), kp.sigma, seed, K, bm.ctypes.data_as(u64p),
+                                be.ctypes.data_as(i8p))
+    out = {"s": s, "z": z, "bsk_mask": bm, "bsk_err": be}
+    if with_ksk:
+        rows = (N, kp.l_ks, kp.Bks - 1)
+        km = np.empty(rows + (n,), np.uint64)
+        ke = np.empty(rows, np.int8)
+        L.orc_seeded_ksk_randomness(C.byref(prm), kp.sigma, seed, km.ctypes.data_as(u64p),
+                                    ke.ctypes.data_as(i8p))
+        out["ksk_mask"], out["ksk_err"] = km, ke
+    return out
+
+
+def seeded_enc_randomness(n: int, q: int, sigma: float, count: int, seed: int) -> dict:
+    """Encryption masks [count][n] in [0, q) and errors [count] from `seed`."""
+    mask = np.empty((count, n), np.uint64)
+    err = np.empty(count, np.int8)
+    lib().orc_seeded_enc_randomness(n, q, sigma, seed, count, mask.ctypes.data_as(u64p),
+                                    err.ctypes.data_as(i8p))
+    return {"mask": mask, "err": err}
+
+
+def encrypt_seeded(n: int, q: int, t: int, s, msg, sigma: float, seed: int) -> np.ndarray:
+    """LWE_{n,q} encryption (Section 2, (8)) with masks and errors drawn from
+    `seed`."""
+    msg = np.ascontiguousarray(msg, np.uint32)
+    r = seeded_enc_randomness(n, q, sigma, msg.shape[0], seed)
+    return encrypt(n, q, t, s, msg, r["mask"], r["err"])

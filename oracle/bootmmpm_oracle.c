@@ -26,6 +26,7 @@
  *  - Key-switching key: [N][l_ks][B_ks - 1][n+1]; entry (i, j, v-1) is an
  *    LWE_{n,Q} encryption under s of v * z_i * g_j (Section 2, (11)).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -173,16 +174,16 @@ static void mac_small(uint32_t N, const u64 *d, const u64 *c, u128 *pos, u128 *n
     }
 }
 
-/* (out_a, out_b) = g^{-1}(a, b) * C, with g^{-1}(a, b) = [g^{-1}(a) | g^{-1}(b)]
- * the 2*l_B digit polynomials and C the [2*l_B][2][N] RGSW matrix.  Column
- * col of the result is sum_j digit_j(a) * C[j][col] + digit_j(b) * C[l_B+j][col]. */
-void orc_external_product(const orc_params *p, const u64 *a, const u64 *b,
-                          const u64 *C, u64 *out_a, u64 *out_b)
+/* Column col of g^{-1}(a, b) * C, with g^{-1}(a, b) = [g^{-1}(a) | g^{-1}(b)]
+ * the 2*l_B digit polynomials and C the [2*l_B][2][N] RGSW matrix:
+ * out = sum_j digit_j(a) * C[j][col] + digit_j(b) * C[l_B+j][col]. */
+static void external_product_col(const orc_params *p, const u64 *a, const u64 *b,
+                                 const u64 *C, int col, u64 *out)
 {
     uint32_t N = p->N, lB = p->l_B;
     u64 *dig = malloc(sizeof(u64) * N);
-    u128 *pos = calloc(2 * (size_t)N, sizeof(u128));
-    u128 *neg = calloc(2 * (size_t)N, sizeof(u128));
+    u128 *pos = calloc(N, sizeof(u128));
+    u128 *neg = calloc(N, sizeof(u128));
     u64 *tmp = malloc(sizeof(u64) * lB);
     for (int comp = 0; comp < 2; comp++) {
         const u64 *src = comp == 0 ? a : b;
@@ -192,16 +193,20 @@ void orc_external_product(const orc_params *p, const u64 *a, const u64 *b,
                 dig[i] = tmp[j];
             }
             const u64 *row = C + (size_t)(comp * lB + j) * 2 * N;
-            for (int col = 0; col < 2; col++)
-                mac_small(N, dig, row + (size_t)col * N, pos + (size_t)col * N,
-                          neg + (size_t)col * N);
+            mac_small(N, dig, row + (size_t)col * N, pos, neg);
         }
     }
-    for (uint32_t k = 0; k < N; k++) {
-        out_a[k] = sub_mod((u64)(pos[k] % p->Q), (u64)(neg[k] % p->Q), p->Q);
-        out_b[k] = sub_mod((u64)(pos[N + k] % p->Q), (u64)(neg[N + k] % p->Q), p->Q);
-    }
+    for (uint32_t k = 0; k < N; k++)
+        out[k] = sub_mod((u64)(pos[k] % p->Q), (u64)(neg[k] % p->Q), p->Q);
     free(dig); free(pos); free(neg); free(tmp);
+}
+
+/* (out_a, out_b) = g^{-1}(a, b) * C: both columns. */
+void orc_external_product(const orc_params *p, const u64 *a, const u64 *b,
+                          const u64 *C, u64 *out_a, u64 *out_b)
+{
+    external_product_col(p, a, b, C, 0, out_a);
+    external_product_col(p, a, b, C, 1, out_b);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -210,8 +215,8 @@ void orc_external_product(const orc_params *p, const u64 *a, const u64 *b,
 
 /* acc <- acc + g^{-1}(P(-a_k) acc - acc) C_k+ + g^{-1}(P(a_k) acc - acc) C_k-,
  * the RLWE-vector x RGSW products taken row by row.  ak in Z_{2Nm}.
- * Cp, Cm: [2*l_B][2][N].  'threads' > 1 runs the 2*m independent row
- * products in parallel. */
+ * Cp, Cm: [2*l_B][2][N].  'parallel' runs the 2*m independent row
+ * products (and their two columns) in parallel. */
 void orc_cmux(const orc_params *p, uint32_t m, uint64_t ak, const u64 *Cp,
               const u64 *Cm, u64 *acc, int parallel)
 {
@@ -228,12 +233,13 @@ void orc_cmux(const orc_params *p, uint32_t m, uint64_t ak, const u64 *Cp,
         diff[i] = sub_mod(rot[i], acc[i], Q);
         diff[vec + i] = sub_mod(rot[vec + i], acc[i], Q);
     }
+    /* the 2m row products and their two output columns are independent */
     #pragma omp parallel for schedule(dynamic) if (parallel)
-    for (int task = 0; task < (int)(2 * m); task++) {
-        int sgn = task / (int)m, r = task % (int)m;
+    for (int task = 0; task < (int)(4 * m); task++) {
+        int col = task & 1, sgn = (task >> 1) / (int)m, r = (task >> 1) % (int)m;
         const u64 *d = diff + (size_t)sgn * vec + (size_t)r * 2 * N;
         u64 *o = prod + (size_t)sgn * vec + (size_t)r * 2 * N;
-        orc_external_product(p, d, d + N, sgn == 0 ? Cp : Cm, o, o + N);
+        external_product_col(p, d, d + N, sgn == 0 ? Cp : Cm, col, o + (size_t)col * N);
     }
     for (size_t i = 0; i < vec; i++)
         acc[i] = add_mod(add_mod(acc[i], prod[i], Q), prod[vec + i], Q);
@@ -564,4 +570,174 @@ int orc_bootstrap_arbitrary(const orc_params *p, uint32_t m, uint32_t t, u64 q, 
     orc_mod_switch(b, W, p->Q, q, ct_out);
     free(a); free(b); free(mp); free(F);
     return rc ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Seeded randomness: keys and ciphertexts drawn from a seed                */
+/* (Algorithm 1 REQUIRE block: s, z, the keys' masks and errors; Section 2, */
+/* (8): encryption masks and errors).  The paper does not fix a generator;  */
+/* this is the counter-based Philox4x32-10 of Salmon, Moraes, Dror and      */
+/* Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11), written     */
+/* here from that definition.  The CUDA library implements the same         */
+/* published generator and stream layout independently.                    */
+/*                                                                          */
+/* Stream layout.  Every random quantity is one Philox block at             */
+/*   counter = (i mod 2^32, i >> 32, domain, kind),                         */
+/*   key     = (seed mod 2^32, seed >> 32),                                 */
+/* where i is the quantity's element index:                                 */
+/*   kind 1  LWE secret s_k,            i = k,                   domain 0   */
+/*   kind 2  RLWE secret z_i,           i = i,                   domain N   */
+/*   kind 3  bootstrapping-key mask,    i = ((k*2+sgn)*2l_B+row)*N + c, N   */
+/*   kind 4  bootstrapping-key error,   same i,                  domain N   */
+/*   kind 5  key-switching-key mask,    i = row*n + c,           domain N   */
+/*   kind 6  key-switching-key error,   i = row,                 domain N   */
+/*           (row = (i_N*l_ks + j)*(B_ks-1) + v-1)                          */
+/*   kind 7  encryption mask,           i = ct*n + c,            domain 0   */
+/*   kind 8  encryption error,          i = ct,                  domain 0   */
+/* From the block (w0, w1, w2, w3):                                         */
+/*   uniform mod M : (w0 + w1 2^32 + w2 2^64 + w3 2^96) mod M;              */
+/*   ternary       : floor(3 w0 / 2^32) - 1;   binary: floor(2 w0 / 2^32);  */
+/*   error         : the discrete Gaussian of parameter sigma (standard     */
+/*                   deviation, reading R11) on [-41, 41] by inversion of   */
+/*                   its cumulative table at r = w0 + w1 2^32 (orc_cdt).    */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_ERR_CUT 41
+
+/* Ten Philox rounds; the key is bumped by the Weyl constants before every
+ * round but the first. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void stream_block(uint64_t seed, uint32_t kind, uint32_t domain, uint64_t i, uint32_t w[4])
+{
+    uint32_t ctr[4] = {(uint32_t)i, (uint32_t)(i >> 32), domain, kind};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, w);
+}
+
+u64 orc_draw_uniform(uint64_t seed, uint32_t kind, uint32_t domain, uint64_t i, u64 modulus)
+{
+    uint32_t w[4];
+    stream_block(seed, kind, domain, i, w);
+    u128 U = (u128)w[0] | ((u128)w[1] << 32) | ((u128)w[2] << 64) | ((u128)w[3] << 96);
+    return (u64)(U % modulus);
+}
+
+int orc_draw_ternary(uint64_t seed, uint32_t kind, uint32_t domain, uint64_t i)
+{
+    uint32_t w[4];
+    stream_block(seed, kind, domain, i, w);
+    return (int)(((uint64_t)w[0] * 3u) >> 32) - 1;
+}
+
+int orc_draw_binary(uint64_t seed, uint32_t kind, uint32_t domain, uint64_t i)
+{
+    uint32_t w[4];
+    stream_block(seed, kind, domain, i, w);
+    return (int)(w[0] >> 31);
+}
+
+/* Cumulative table of the discrete Gaussian rho(k) = exp(-k^2 / (2 sigma^2))
+ * on k in [-41, 41]: F_j = (rho(-41) + ... + rho(-41 + j)) / S for j in
+ * [0, 82), S the sum over all 83 points, both summed in double from -41
+ * upward; T_j = floor(F_j 2^64), or 2^64 - 1 where F_j 2^64 >= 2^64 - 1. */
+void orc_cdt(double sigma, u64 *T)
+{
+    double rho[2 * ORC_ERR_CUT + 1];
+    double S = 0.0;
+    double den = 2.0 * sigma * sigma;
+    for (int k = -ORC_ERR_CUT; k <= ORC_ERR_CUT; k++) {
+        double x = (double)(k * k) / den;
+        rho[k + ORC_ERR_CUT] = exp(-x);
+        S += rho[k + ORC_ERR_CUT];
+    }
+    double F = 0.0;
+    for (int j = 0; j < 2 * ORC_ERR_CUT; j++) {
+        F += rho[j];
+        double v = ldexp(F / S, 64);
+        T[j] = v >= 18446744073709551615.0 ? UINT64_MAX : (u64)v;
+    }
+}
+
+/* Error sample: -41 plus the number of table entries at or below r. */
+int orc_draw_gaussian(uint64_t seed, uint32_t kind, uint32_t domain, uint64_t i, const u64 *T)
+{
+    uint32_t w[4];
+    stream_block(seed, kind, domain, i, w);
+    u64 r = (u64)w[0] | ((u64)w[1] << 32);
+    int e = -ORC_ERR_CUT;
+    for (int j = 0; j < 2 * ORC_ERR_CUT; j++)
+        if (r >= T[j]) e++;
+    return e;
+}
+
+/* LWE secret s (kind 1): ternary, or binary when ternary == 0. */
+void orc_seeded_lwe_secret(uint32_t n, int ternary, uint64_t seed, int8_t *s)
+{
+    for (uint32_t k = 0; k < n; k++)
+        s[k] = (int8_t)(ternary ? orc_draw_ternary(seed, 1, 0, k) : orc_draw_binary(seed, 1, 0, k));
+}
+
+/* RLWE secret z (kind 2, domain N): ternary. */
+void orc_seeded_rlwe_secret(uint32_t N, uint64_t seed, int8_t *z)
+{
+    for (uint32_t i = 0; i < N; i++) z[i] = (int8_t)orc_draw_ternary(seed, 2, N, i);
+}
+
+/* Masks and errors of the bootstrapping keys for k in [0, n_keys), laid out
+ * as [n_keys][2][2 l_B][N] (the arrays orc_keygen_bsk reads). */
+void orc_seeded_bsk_randomness(const orc_params *p, double sigma, uint64_t seed, uint32_t n_keys,
+                               u64 *mask, int8_t *err)
+{
+    u64 T[2 * ORC_ERR_CUT];
+    orc_cdt(sigma, T);
+    size_t total = (size_t)n_keys * 2 * 2 * p->l_B * p->N;
+    #pragma omp parallel for schedule(static)
+    for (long ii = 0; ii < (long)total; ii++) {
+        mask[ii] = orc_draw_uniform(seed, 3, p->N, (uint64_t)ii, p->Q);
+        err[ii] = (int8_t)orc_draw_gaussian(seed, 4, p->N, (uint64_t)ii, T);
+    }
+}
+
+/* Masks [rows][n] and errors [rows] of the key-switching keys, rows =
+ * N l_ks (B_ks - 1) (the arrays orc_keygen_ksk reads). */
+void orc_seeded_ksk_randomness(const orc_params *p, double sigma, uint64_t seed, u64 *mask, int8_t *err)
+{
+    u64 T[2 * ORC_ERR_CUT];
+    orc_cdt(sigma, T);
+    size_t rows = (size_t)p->N * p->l_ks * ((1u << p->log2_Bks) - 1);
+    #pragma omp parallel for schedule(static)
+    for (long rr = 0; rr < (long)rows; rr++) {
+        for (uint32_t c = 0; c < p->n; c++)
+            mask[(size_t)rr * p->n + c] = orc_draw_uniform(seed, 5, p->N, (uint64_t)rr * p->n + c, p->Q);
+        err[rr] = (int8_t)orc_draw_gaussian(seed, 6, p->N, (uint64_t)rr, T);
+    }
+}
+
+/* Encryption masks [count][n] in [0, q) and errors [count] (kinds 7, 8). */
+void orc_seeded_enc_randomness(uint32_t n, u64 q, double sigma, uint64_t seed, size_t count,
+                               u64 *mask, int8_t *err)
+{
+    u64 T[2 * ORC_ERR_CUT];
+    orc_cdt(sigma, T);
+    for (size_t i = 0; i < count; i++) {
+        for (uint32_t c = 0; c < n; c++)
+            mask[i * n + c] = orc_draw_uniform(seed, 7, 0, (uint64_t)i * n + c, q);
+        err[i] = (int8_t)orc_draw_gaussian(seed, 8, 0, (uint64_t)i, T);
+    }
 }

@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 def build_oracle(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
-    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", LIB + ".tmp", SRC]
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-o", LIB + ".tmp", SRC, "-lm"]
     for extra in (["-fopenmp"], []):
         cmd = base[:2] + extra + base[2:]
         r = subprocess.run(cmd, capture_output=True, text=True)
