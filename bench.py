@@ -1,18 +1,26 @@
-"""Benchmark: BootMMPM bootstraps/s on one GB300 (batched, bit-exact).
+"""Benchmark: BootMMPM bootstraps/s on one GB300 (batched vs plain, bit-exact),
+with p50/p99 served latency.
 
 One step = one batch of the workload (default: 4096 ciphertexts, n = 630,
 N = 1024, m = 4, t = 2^10) through the whole hot path: test vector and ACC
-initialisation, n CMux steps, sample extraction, key switching.  Inputs sit
-in HBM before the timed region; L2 is flushed between timed steps (the keys,
-236 MiB BSK and 518 MiB KSK, exceed L2 anyway).
+initialisation, n CMux steps, sample extraction, key switching.  Keys are
+generated on the device from a seed.  Every warm-up and timed step bootstraps
+its own freshly encrypted batch (distinct ciphertexts and tables), all
+resident in HBM before the timed region; every output of every step is
+decrypted afterwards and counted in `decrypt_failures`.  L2 is flushed
+between timed steps (the keys, 236 MiB BSK and 518 MiB KSK, exceed L2 too).
 
-Also reported: the plain form (one ciphertext per launch), the end-to-end
-rate through the host-buffer C-ABI call, the blind-rotation kernel's integer
-roofline, SM clocks during the timed region, and the CPU oracle's rate on a
-bounded sample (`--impl reference` prints the oracle arm alone).
+Also reported in the same JSON line: the plain form (one ciphertext per
+launch), the end-to-end rate through the host-buffer C-ABI call, the
+blind-rotation kernel's integer roofline, SM clocks during the timed region,
+the key switch's gather bandwidth, the large-plaintext (n = 750, N = 2048,
+m = 8) and single-polynomial (m = 1, N = 4096) workloads with their roofline
+fractions, the uneven mix in grouped and persistent launches, served p50/p99
+latency at three loads, and the CPU oracle's rate on a bounded sample
+(`--impl reference` prints the oracle arm alone).
 
 Multi-GPU: independent replicas (weak scaling), one process per GPU under
-torchrun; each rank bootstraps its own batch; value = total / max time.
+torchrun; each rank bootstraps its own batches; value = total / max time.
 """
 from __future__ import annotations
 
@@ -32,15 +40,18 @@ sys.path.insert(0, ROOT)
 from paper_2310_12441_gb300 import params as P  # noqa: E402
 from paper_2310_12441_gb300 import synth  # noqa: E402
 
-METRIC = "bootstraps/s on 1 GB300 (batched, bit-exact)"
+METRIC = "bootstraps/s on 1 GB300 (batched vs plain, bit-exact); p50/p99 served latency"
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# blind-rotation kernel per job, from one ncu capture of a 152-job launch
-# of this workload (profiles/k_blind_rotate_n630_N1024_m4.md), valid while
-# the kernel sources hash to the captured version.
+# blind-rotation kernel per job, from one ncu capture of a 152-job launch of
+# the workload (command: bench.py --workload <name> --count 152 under
+# `ncu --set full -k regex:k_blind_rotate`), valid while the kernel sources
+# hash to the captured version.
 KERNEL_SOURCES = ["blind_rotate.cuh", "ntt_reg.cuh", "modarith.cuh", "common.cuh", "bootstrap.cu"]
-CAPTURED_TRAFFIC = {"hash": "420eedf6f471f001", "bytes_per_job": (255.315456e6 + 5.345536e6) / 152}
+CAPTURED_TRAFFIC = {
+    P.BATCH_N1024.name: {"hash": "420eedf6f471f001", "bytes_per_job": (255.315456e6 + 5.345536e6) / 152},
+}
 
 
 def kernel_hash():
@@ -128,26 +139,27 @@ def dist_info():
 # ---------------------------------------------------------------------------
 
 def oracle_rate(w, cores_hint=None, steps_sample=8, seed=0):
-    """Oracle bootstraps/s on a bounded sample: `cores` ciphertexts of the
-    workload with only the first `steps_sample` CMux steps (the others have
-    a_k = 0), then scaled to n steps; the key switch is timed in full."""
+    """The oracle on a bounded sample of the workload: `cores` ciphertexts,
+    one per core, whose masks vanish after the first `steps_sample` entries
+    (so the oracle runs only those CMux steps), each followed by its full key
+    switch.  Returns the measured wall time of the sample and the rate it
+    projects for full bootstraps (CMux steps all cost the same, so the
+    rotation time scales by n / steps_sample; the key switch is timed alone)."""
     import oracle
     kp, m, t = w.keys, w.shape.m, w.shape.t
     cores = cores_hint or os.cpu_count() or 1
     S = cores
-    rnd = synth.key_randomness(kp, 1000 + w.seed_base, bsk_keys=steps_sample)
+    rnd = oracle.seeded_key_randomness(kp, 1000 + w.seed_base, bsk_keys=steps_sample)
     bsk = oracle.keygen_bsk(kp, rnd)
     ksk = oracle.keygen_ksk(kp, rnd)
     qp = 2 * kp.N * m
     msg = synth.messages(t, S, 3000 + w.seed_base + seed)
-    enc = synth.encryption_randomness(kp.n, qp, kp.sigma, S, 4000 + w.seed_base + seed,
-                                      prefix=steps_sample)
-    ct = oracle.encrypt(kp.n, qp, t, rnd["s"], msg, enc["mask"], enc["err"])
+    ct = oracle.encrypt_seeded(kp.n, qp, t, rnd["s"], msg, kp.sigma, 4000 + w.seed_base + seed)
+    ct[:, steps_sample:kp.n] = 0
     luts, _ = synth.luts(t, S, 2000 + w.seed_base + seed)
     t0 = time.perf_counter()
     oracle.bootstrap(kp, m, t, bsk, ksk, ct, luts)
     dt = time.perf_counter() - t0
-    # split: time one key switch per ciphertext separately to scale the rest
     t1 = time.perf_counter()
     lwe = np.zeros((S, kp.N + 1), np.uint64)
     for i in range(S):
@@ -156,27 +168,33 @@ def oracle_rate(w, cores_hint=None, steps_sample=8, seed=0):
     per_ct_rot = max(dt - ks, 1e-9)              # wall, S in parallel
     per_boot_wall = per_ct_rot * kp.n / steps_sample + ks
     rate = S / per_boot_wall
-    sample = (f"{S} ciphertexts x first {steps_sample} of {kp.n} CMux steps "
-              f"(+ full key switch), scaled to n steps; {dt:.1f} s wall")
-    return rate, cores, sample
+    sample = (f"{S} ciphertexts (one per core) x first {steps_sample} of {kp.n} CMux steps "
+              f"+ full key switch: {dt:.2f} s wall measured; full bootstraps/s projected "
+              f"by scaling the rotation time to n steps")
+    return rate, cores, sample, dt
 
 
 def run_reference(args, w):
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    vals = []
     for s in range(args.warmup):                  # untimed: loads the library, warms caches
         oracle_rate(w, steps_sample=1, seed=100 + s)
+    vals, walls = [], []
     for s in range(args.steps):
-        r, cores, sample = oracle_rate(w, steps_sample=args.cpu_steps, seed=s)
+        r, cores, sample, dt = oracle_rate(w, steps_sample=args.cpu_steps, seed=s)
         vals.append(r)
+        walls.append(dt)
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "bootstraps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * w.count / v, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * float(np.mean(walls)), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": config_of(w, args),
+            "step": "one bounded sample of the workload (see cpu_baseline.sample); ms_per_step "
+                    "is its measured wall time",
+            "projected_bootstraps_per_s": v,
+            "projected_ms_per_batch": 1e3 * (args.count or w.count) / v,
             "cpu_baseline": {"value": v, "unit": "bootstraps/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "bootstraps/s", "h2d_bytes_per_step": 0,
@@ -184,17 +202,167 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
-def config_of(w, args):
+def config_of(w, args, count=None):
     kp = w.keys
-    return {"workload": w.name, "count": args.count or w.count, "n": kp.n, "N": kp.N,
+    return {"workload": w.name, "count": count or args.count or w.count, "n": kp.n, "N": kp.N,
             "m": w.shape.m, "t": w.shape.t, "Q": kp.Q, "B": kp.B, "l_B": kp.l_B,
-            "B_ks": kp.Bks, "l_ks": kp.l_ks, "l2": "flushed between timed steps",
-            "parallelism": "replicas"}
+            "B_ks": kp.Bks, "l_ks": kp.l_ks, "keys": "drawn and built on the device from a seed",
+            "inputs": "a distinct encrypted batch per step, resident before timing",
+            "l2": "flushed between timed steps", "parallelism": "replicas"}
 
 
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def make_inputs(api, sk, w, count, seed, dev):
+    """One batch: messages, tables and seeded encryptions, copied to `dev`."""
+    import torch
+    kp, m, t = w.keys, w.shape.m, w.shape.t
+    qp = 2 * kp.N * m
+    luts, ident = synth.luts(t, count, 2000 + seed, mix=w.lut_mix)
+    msg = synth.messages(t, count, 3000 + seed, half=ident)
+    ct = api.bm_encrypt_seeded(sk, qp, t, msg, 4000 + seed)
+    return {"ct": ct, "luts": luts, "d_in": api.to_device_u64(ct.ravel(), dev),
+            "d_lut": api.to_device_u32(luts.ravel(), dev),
+            "d_out": torch.zeros(count * (kp.n + 1), dtype=torch.int64, device=dev)}
+
+
+def count_failures(api, sk, w, batches):
+    """Outputs that do not decrypt (at Q) to f(Dec(input))."""
+    kp, m, t = w.keys, w.shape.m, w.shape.t
+    qp, W = 2 * kp.N * m, kp.n + 1
+    bad = total = 0
+    for b in batches:
+        cnt = b["ct"].shape[0]
+        out = api.from_device_u64(b["d_out"]).reshape(cnt, W)
+        dec_in = api.bm_decrypt(sk, qp, t, b["ct"])
+        dec_out = api.bm_decrypt(sk, kp.Q, t, out)
+        bad += int((dec_out != b["luts"][np.arange(cnt), dec_in]).sum())
+        total += cnt
+    return bad, total
+
+
+def kernel_roofline(api, ek, w, jobs, batch, ws, stream, flush, dev, peak, reps=3):
+    """Blind rotation alone (bm_blind_rotate, same jobs and launch shape)
+    timed with CUDA events on its stream: algorithmic modmuls / time against
+    the measured modmul peak."""
+    import torch
+    kp, m = w.keys, w.shape.m
+    count = len(jobs)
+    d_acc = torch.zeros(count * 2 * m * kp.N, dtype=torch.int64, device=dev)
+    jobs_acc = jobs.copy()
+    jobs_acc["out_off"] = np.arange(count) * 2 * m * kp.N
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1)
+        a, b = _events(torch)
+        a.record(stream)
+        api.bm_blind_rotate([ek], jobs_acc, 1 << 30, batch["d_in"], batch["d_lut"], d_acc, ws, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ts.append(a.elapsed_time(b))
+    del d_acc
+    mm = modmuls_per_bootstrap(kp, m) * count
+    rot_s = float(np.mean(ts)) * 1e-3
+    traffic = None
+    cap = CAPTURED_TRAFFIC.get(w.name)
+    if cap and kernel_hash() == cap["hash"]:
+        traffic = cap["bytes_per_job"] * count
+    return {"bound": "alu", "achieved": mm / rot_s / 1e9, "peak": peak / 1e9, "unit": "Gmodmul/s",
+            "frac": (mm / rot_s) / peak, "traffic": traffic, "kernel": "k_blind_rotate",
+            "kernel_ms": rot_s * 1e3, "modmuls_per_launch": mm,
+            "peak_kind": "measured: the blind rotation's own modular product in a throughput loop"}
+
+
+def run_workload(api, w, dev, stream, flush, peak, count=None, steps=2, warmup=1, seed_shift=0):
+    """Rate, roofline and failures of one more workload (its own keys)."""
+    import torch
+    kp, m, t = w.keys, w.shape.m, w.shape.t
+    count = count or w.count
+    t0 = time.perf_counter()
+    sk, ek = api.bm_keygen_seeded(kp, 1000 + w.seed_base, dev.index)
+    torch.cuda.synchronize(dev)
+    keygen_s = time.perf_counter() - t0
+    W = kp.n + 1
+    jobs = api.make_jobs(0, m, t, np.arange(count) * W, np.arange(count) * t, np.arange(count) * W)
+    ws = api.workspace(api.bm_workspace_bytes([ek], jobs), dev)
+    batches = [make_inputs(api, sk, w, count, w.seed_base + 700 + seed_shift + i, dev)
+               for i in range(warmup + steps)]
+    for b in batches[:warmup]:
+        api.bm_bootstrap_batch([ek], jobs, b["d_in"], b["d_lut"], b["d_out"], ws, stream)
+    torch.cuda.synchronize(dev)
+    ms = []
+    for b in batches[warmup:]:
+        flush.fill_(4)
+        e0, e1 = _events(torch)
+        e0.record(stream)
+        api.bm_bootstrap_batch([ek], jobs, b["d_in"], b["d_lut"], b["d_out"], ws, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    assert api.bm_workspace_status(ws, stream) == 0
+    bad, total = count_failures(api, sk, w, batches)
+    roof = kernel_roofline(api, ek, w, jobs, batches[0], ws, stream, flush, dev, peak, reps=1)
+    value = count / (float(np.mean(ms)) * 1e-3)
+    del batches, ws
+    ek.free()
+    torch.cuda.empty_cache()
+    return {"workload": w.name, "value": value, "unit": "bootstraps/s", "ms_per_step": float(np.mean(ms)),
+            "steps": steps, "count": count, "keygen_s": keygen_s, "key_bytes": None,
+            "decrypt_failures": bad, "bootstraps_checked": total, "roofline": roof}
+
+
+def key_switch_rate(api, ek, kp, count, dev, stream, flush, hbm_gbs):
+    """bm_key_switch on `count` random LWE_{N,Q} samples: the selected KSK rows
+    (digits nonzero: 15/16 of N l_ks per sample, n + 1 words each) per second,
+    against the measured HBM copy bandwidth."""
+    import torch
+    rng = np.random.default_rng(5)
+    lwe = rng.integers(0, kp.Q, (count, kp.N + 1), dtype=np.uint64)
+    d_in = api.to_device_u64(lwe, dev)
+    d_out = torch.zeros(count * (kp.n + 1), dtype=torch.int64, device=dev)
+    api.bm_key_switch(ek, d_in, count, d_out, stream)
+    torch.cuda.synchronize(dev)
+    ts = []
+    for _ in range(3):
+        flush.fill_(5)
+        a, b = _events(torch)
+        a.record(stream)
+        api.bm_key_switch(ek, d_in, count, d_out, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ts.append(a.elapsed_time(b))
+    ms = float(np.median(ts))
+    rows = kp.N * kp.l_ks * (kp.Bks - 1) / kp.Bks * count
+    gbytes = rows * (kp.n + 1) * 8 / 1e9
+    ksk_bytes = kp.N * kp.l_ks * (kp.Bks - 1) * (kp.n + 1) * 8
+    one = []
+    for _ in range(3):
+        a, b = _events(torch)
+        a.record(stream)
+        api.bm_key_switch(ek, d_in, 1, d_out, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        one.append(a.elapsed_time(b))
+    return {"kernel": "key switch (bm_key_switch)", "count": count, "ms": ms,
+            "gathered_gbytes": gbytes, "gathered_GBps": gbytes / (ms * 1e-3),
+            "ksk_bytes": ksk_bytes, "hbm_peak_GBps": hbm_gbs,
+            "frac_gathered_of_hbm": gbytes / (ms * 1e-3) / hbm_gbs if hbm_gbs else None,
+            "single_ms": float(np.median(one))}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
 
 def run_gpu(args, w):
     import torch
@@ -211,40 +379,27 @@ def run_gpu(args, w):
     count = args.count or w.count
     api.load(build_if_needed=(rank == 0))
 
-    rnd = synth.key_randomness(kp, 1000 + w.seed_base)
-    sk, ek = api.bm_keygen(kp, rnd, local)
-    del rnd
-    qp = 2 * kp.N * m
-    seed = w.seed_base + 100 * rank
-    msg = synth.messages(t, count, 3000 + seed)
-    enc = synth.encryption_randomness(kp.n, qp, kp.sigma, count, 4000 + seed)
-    ct = api.bm_encrypt(sk, qp, t, msg, enc["mask"], enc["err"])
-    luts, _ = synth.luts(t, count, 2000 + seed, mix=w.lut_mix)
+    t0 = time.perf_counter()
+    sk, ek = api.bm_keygen_seeded(kp, 1000 + w.seed_base, local)
+    torch.cuda.synchronize(dev)
+    keygen_s = time.perf_counter() - t0
     W = kp.n + 1
     jobs = api.make_jobs(0, m, t, np.arange(count) * W, np.arange(count) * t, np.arange(count) * W)
-    d_in = api.to_device_u64(ct.ravel(), dev)
-    d_lut = api.to_device_u32(luts.ravel(), dev)
-    d_out = torch.zeros(count * W, dtype=torch.int64, device=dev)
+    seed = w.seed_base + 100 * rank
+    batches = [make_inputs(api, sk, w, count, seed + 1000 * i, dev) for i in range(args.warmup + args.steps)]
     ws = api.workspace(api.bm_workspace_bytes([ek], jobs), dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        api.bm_bootstrap_batch([ek], jobs, d_in, d_lut, d_out, ws, stream)
+    def step(b):
+        api.bm_bootstrap_batch([ek], jobs, b["d_in"], b["d_lut"], b["d_out"], ws, stream)
 
-    for _ in range(args.warmup):
-        step()
+    for b in batches[:args.warmup]:
+        step(b)
     torch.cuda.synchronize(dev)
     assert api.bm_workspace_status(ws, stream) == 0
 
-    # correctness spot check of this run's outputs: decryption (whole batch)
-    out = api.from_device_u64(d_out).reshape(count, W)
-    dec_in = api.bm_decrypt(sk, qp, t, ct)
-    dec_out = api.bm_decrypt(sk, kp.Q, t, out)
-    failures = int((dec_out != luts[np.arange(count), dec_in]).sum())
-
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+    evs = [_events(torch) for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -252,68 +407,48 @@ def run_gpu(args, w):
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
             evs[i][0].record(stream)
-            step()
+            step(batches[args.warmup + i])
             evs[i][1].record(stream)
         torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in evs]
     total_ms, value = aggregate(float(sum(ms)), count, args.steps, world, dist if world > 1 else None, dev)
-
-    # kernel-level timing of the blind rotation alone (same jobs, same launch
-    # configuration; bm_blind_rotate adds one ACC copy of m*2*N words per job)
-    d_acc = torch.zeros(count * 2 * m * kp.N, dtype=torch.int64, device=dev)
-    jobs_acc = jobs.copy()
-    jobs_acc["out_off"] = np.arange(count) * 2 * m * kp.N
-    rot_ms = []
-    for i in range(max(1, min(args.steps, 3))):
-        flush.fill_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        api.bm_blind_rotate([ek], jobs_acc, 1 << 30, d_in, d_lut, d_acc, ws, stream)
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        rot_ms.append(a.elapsed_time(b))
-    del d_acc
+    assert api.bm_workspace_status(ws, stream) == 0
+    failures, checked = count_failures(api, sk, w, batches)
+    timed_failures, timed_checked = count_failures(api, sk, w, batches[args.warmup:])
 
     result = {"metric": METRIC, "value": value, "unit": "bootstraps/s", "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
               "data": "synthetic", "config": config_of(w, args),
-              "decrypt_failures": failures, "gpu_launches": 2 * args.steps}
+              "decrypt_failures": timed_failures, "bootstraps_checked": timed_checked,
+              "decrypt_failures_incl_warmup": failures, "bootstraps_checked_incl_warmup": checked,
+              "gpu_launches": 2 * args.steps, "keygen_s": keygen_s}
     if rank == 0:
-        clocks = clk.summary()
-        result["clocks"] = clocks
-        # roofline of the dominant kernel: blind rotation
+        result["clocks"] = clk.summary()
+        peaks = measured_peaks()
         peak = api.bm_modmul_peak(local, 1 << 14)
-        mm = modmuls_per_bootstrap(kp, m) * count
-        rot_s = float(np.mean(rot_ms)) * 1e-3
-        traffic = None
-        if w is P.BATCH_N1024 and kernel_hash() == CAPTURED_TRAFFIC["hash"]:
-            traffic = CAPTURED_TRAFFIC["bytes_per_job"] * count
-        result["roofline"] = {"bound": "alu", "achieved": mm / rot_s / 1e9,
-                              "peak": peak / 1e9, "unit": "Gmodmul/s",
-                              "frac": (mm / rot_s) / peak, "traffic": traffic,
-                              "kernel": "k_blind_rotate", "kernel_ms": rot_s * 1e3,
-                              "modmuls_per_launch": mm}
+        result["roofline"] = kernel_roofline(api, ek, w, jobs, batches[0], ws, stream, flush, dev, peak)
         # plain form: one ciphertext per launch
         if args.plain > 0:
+            b0 = batches[0]
             P_ = min(args.plain, count)
             j1 = [jobs[i:i + 1] for i in range(P_)]
             for i in range(2):
-                api.bm_bootstrap_batch([ek], j1[i], d_in, d_lut, d_out, ws, stream)
+                api.bm_bootstrap_batch([ek], j1[i], b0["d_in"], b0["d_lut"], b0["d_out"], ws, stream)
             torch.cuda.synchronize(dev)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a, b = _events(torch)
             a.record(stream)
             for i in range(P_):
-                api.bm_bootstrap_batch([ek], j1[i], d_in, d_lut, d_out, ws, stream)
+                api.bm_bootstrap_batch([ek], j1[i], b0["d_in"], b0["d_lut"], b0["d_out"], ws, stream)
             b.record(stream)
             torch.cuda.synchronize(dev)
             pv = P_ / (a.elapsed_time(b) * 1e-3)
-            # the same with one block per job (no thread-block cluster over the rows)
             P1 = min(8, P_)
-            d_out1 = torch.zeros_like(d_out)
-            one = [api.Batch([ek], j1[i], d_in, d_lut, d_out1, ws, api.BATCH_ONE_BLOCK) for i in range(P1)]
+            d_out1 = torch.zeros_like(b0["d_out"])
+            one = [api.Batch([ek], j1[i], b0["d_in"], b0["d_lut"], d_out1, ws, api.BATCH_ONE_BLOCK)
+                   for i in range(P1)]
             one[0].run(stream)
             torch.cuda.synchronize(dev)
             a.record(stream)
@@ -329,8 +464,9 @@ def run_gpu(args, w):
                                "launch": "one job per launch, rows split over a thread-block cluster",
                                "one_block_per_job": {"value": pv1, "ciphertexts": P1}}
         # end to end through the host-buffer C-ABI call (pinned host memory)
-        h_in = torch.from_numpy(ct.ravel().view(np.int64)).pin_memory()
-        h_lut = torch.from_numpy(luts.ravel().view(np.int32)).pin_memory()
+        b0 = batches[0]
+        h_in = torch.from_numpy(b0["ct"].ravel().view(np.int64)).pin_memory()
+        h_lut = torch.from_numpy(b0["luts"].ravel().view(np.int32)).pin_memory()
         h_out = torch.zeros(count * W, dtype=torch.int64).pin_memory()
         ws2 = api.workspace(api.bm_workspace_bytes([ek], jobs) + api.bm_host_staging_bytes([ek], jobs) + 4096, dev)
         api.bm_bootstrap_batch_host([ek], jobs, h_in, h_lut, h_out, ws2, stream)
@@ -341,17 +477,95 @@ def run_gpu(args, w):
             t0 = time.perf_counter()
             api.bm_bootstrap_batch_host([ek], jobs, h_in, h_lut, h_out, ws2, stream)
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        del ws2
         result["e2e"] = {"value": count / (np.mean(e2e_ms) * 1e-3), "unit": "bootstraps/s",
                          "h2d_bytes_per_step": int(h_in.numel() * 8 + h_lut.numel() * 4),
                          "d2h_bytes_per_step": int(h_out.numel() * 8)}
+        result["key_switch"] = key_switch_rate(api, ek, kp, count, dev, stream, flush, peaks.get("hbm_gbs"))
+        if not args.no_extras and w is P.BATCH_N1024:
+            del batches
+            torch.cuda.empty_cache()
+            result.update(run_extras(args, api, dev, stream, flush, peak))
         if not args.no_cpu:
-            r, cores, sample = oracle_rate(w, steps_sample=args.cpu_steps)
+            r, cores, sample, _ = oracle_rate(w, steps_sample=args.cpu_steps)
             result["cpu_baseline"] = {"value": r, "unit": "bootstraps/s", "cores": cores,
                                       "kind": "oracle", "sample": sample}
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_extras(args, api, dev, stream, flush, peak):
+    """The other workloads of the metric, inside the same JSON line: the
+    large-plaintext and single-polynomial batches (rate and roofline), the
+    uneven mix in grouped and persistent launches, and served latency."""
+    import torch
+    from paper_2310_12441_gb300 import autotune, serve
+    from paper_2310_12441_gb300 import workload as wl
+    from paper_2310_12441_gb300.params import JobShape
+    out = {"workloads": []}
+    for w2 in (P.LARGE_N2048, P.SINGLEPOLY_N4096):
+        out["workloads"].append(run_workload(api, w2, dev, stream, flush, peak))
+    # uneven mix: 8192 jobs over six parameter sets, Zipf(1.2) counts
+    ks1024 = wl.make_keyset(P.KEYS_N1024, 1002)
+    ks2048 = wl.make_keyset(P.KEYS_N2048, 1003)
+    ksets = [ks1024, ks2048]
+    counts = synth.zipf_counts(8192, len(P.UNEVEN_SETS), 1.2, 5)
+    groups = [(0 if kp is P.KEYS_N1024 else 1, shape, int(c))
+              for (name, kp, shape), c in zip(P.UNEVEN_SETS, counts)]
+    bu = wl.make_batch(ksets, groups, 4)
+    d_in = api.to_device_u64(bu.ct_in, dev)
+    d_lut = api.to_device_u32(bu.luts, dev)
+    d_out = torch.zeros(bu.out_words, dtype=torch.int64, device=dev)
+    keys = [k.ek for k in ksets]
+    ws = api.workspace(api.bm_workspace_bytes(keys, bu.jobs), dev)
+    choice, tune_ms = autotune.tune(ksets, bu.jobs, d_in, d_lut, d_out, ws, stream, use_cache=False)
+    modes = {}
+    mm = sum(modmuls_per_bootstrap(ksets[int(j["key"])].kp, int(j["m"])) for j in bu.jobs)
+    for name, fl in autotune.CANDIDATES.items():
+        b = api.Batch(keys, bu.jobs, d_in, d_lut, d_out, ws, fl)
+        b.run(stream)
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(2):
+            flush.fill_(6)
+            e0, e1 = _events(torch)
+            e0.record(stream)
+            b.run(stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        b.free()
+        ms = float(np.min(ts))
+        bad = wl.check_outputs(ksets, bu, api.from_device_u64(d_out))
+        modes[name] = {"bootstraps_per_s": len(bu.jobs) / ms * 1e3, "ms": ms, "decrypt_failures": bad,
+                       "frac_of_modmul_peak": mm / (ms * 1e-3) / peak}
+    out["uneven"] = {"workload": "uneven 8192 jobs, sets S1..S6 (m 1..8, N 1024/2048), Zipf 1.2",
+                     "counts": {n: int(c) for (n, _, _), c in zip(P.UNEVEN_SETS, counts)},
+                     "autotune": {"choice": choice, "ms": tune_ms}, "modes": modes}
+    del d_in, d_lut, d_out, ws, bu
+    # served: single requests of the large-plaintext set at fractions of its batch capacity
+    cap = out["workloads"][0]["value"]
+    poolsz = 512
+    bp = wl.make_batch([ks2048], [(0, JobShape(8, 8192), poolsz)], 9, lut_mix="mixed", interleave=False)
+    Wn = P.KEYS_N2048.n + 1
+    pool = [(0, 8, 8192, bp.ct_in[i * Wn:(i + 1) * Wn], bp.luts[i * 8192:(i + 1) * 8192])
+            for i in range(poolsz)]
+    served = []
+    for frac in (0.25, 0.5, 0.9):
+        srv = serve.Server([ks2048], max_batch=args.max_batch, streams=3)
+        r = serve.run_open_loop(srv, pool, frac * cap, args.serve_seconds, 11)
+        r.pop("requests")
+        r["load"] = frac
+        served.append(r)
+    out["served"] = {"workload": "Poisson arrivals of single requests, n=750 N=2048 m=8 t=2^13, "
+                                 "random and identity tables", "capacity_bootstraps_per_s": cap,
+                     "memory_cap_bytes": 120 << 30,
+                     "loads": [{k: r[k] for k in ("load", "rate", "offered", "accepted", "rejected",
+                                                  "completed", "failed", "batches", "throughput",
+                                                  "p50_ms", "p99_ms")} for r in served]}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -572,11 +786,13 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=16,
                     help="CMux steps per ciphertext in the bounded oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline workload only (no other workloads, served latency)")
     ap.add_argument("--suite", default="", help="comma list: layouts,large,uneven,served,failures,sweep")
     ap.add_argument("--sweep-logt", default="5-15", help="sweep: range of log2 t")
     ap.add_argument("--sweep-n", type=int, default=512, help="sweep: LWE dimension (512 or 1024)")
     ap.add_argument("--rates", default="2000,0.25,0.5,0.9", help="served: req/s, or fractions of capacity")
-    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--max-batch", type=int, default=512)
     ap.add_argument("--fail-count", type=int, default=100000)
     args = ap.parse_args()

@@ -7,8 +7,8 @@
  * test-vector construction and ACC initialisation, n CMux steps over the
  * monic monomial permutation matrices P(c) (blind rotation), sample
  * extraction and LWE key switching.  Key generation builds the evaluation
- * keys on the GPU from caller-supplied randomness; encryption and decryption
- * are client-side host routines.
+ * keys on the GPU from a seed (or from caller-supplied randomness);
+ * encryption and decryption are client-side host routines.
  *
  * Conventions (Section 2 of the paper):
  *  - Z_Q values are uint64 in [0, Q); Q is prime, Q = 1 mod 2N, Q < 2^61.
@@ -111,6 +111,51 @@ bm_status bm_keygen(const bm_key_params *params, const bm_key_randomness *rnd,
 void bm_free_secret_key(bm_secret_key *sk);
 void bm_free_eval_key(bm_eval_key *ek);
 
+/* Keys drawn from a seed (Algorithm 1 REQUIRE block: s and z, and the masks
+ * and errors of the keys of Section 2 items (11) and (14)).  The paper fixes
+ * no generator; the library uses the counter-based Philox4x32-10 of Salmon,
+ * Moraes, Dror and Shaw ("Parallel random numbers: as easy as 1, 2, 3",
+ * SC'11), one 128-bit block per drawn value:
+ *   block(kind, domain, i) = Philox4x32-10(counter = (i mod 2^32, i >> 32,
+ *                            domain, kind), key = (seed mod 2^32, seed >> 32)).
+ *   kind 1  s_k                 i = k                                 domain 0
+ *   kind 2  z_i                 i = i                                 domain N
+ *   kind 3  BSK mask word       i = ((k 2 + sgn) 2 l_B + row) N + c   domain N
+ *   kind 4  BSK error           the same i                            domain N
+ *   kind 5  KSK mask word       i = r n + c, r = (i_N l_ks + j)(B_ks - 1) + v - 1,  domain N
+ *   kind 6  KSK error           i = r                                 domain N
+ *   kind 7  encryption mask     i = ct n + c                          domain 0
+ *   kind 8  encryption error    i = ct                                domain 0
+ * Values from a block (w0, w1, w2, w3): uniform mod M is (w0 + w1 2^32 +
+ * w2 2^64 + w3 2^96) mod M; ternary is floor(3 w0 / 2^32) - 1; binary is
+ * floor(2 w0 / 2^32); an error is the discrete Gaussian exp(-k^2/(2 sigma^2))
+ * on [-41, 41] by inversion, at r = w0 + w1 2^32, of the table
+ * T_j = floor(2^64 F_j) (saturated at 2^64 - 1), F_j the mass of
+ * [-41, -41 + j] summed in double from -41 upward.  sigma is the standard
+ * deviation parameter, 0 < sigma <= BM_SIGMA_MAX (so the cut at 41 lies
+ * beyond 10 sigma).  Two key sets with the same seed and n share s. */
+#define BM_SECRET_BINARY 0u
+#define BM_SECRET_TERNARY 1u
+#define BM_SIGMA_MAX 4.0
+
+/* Secret key only (host, no device): s (ternary, or binary with
+ * BM_SECRET_BINARY) and z from `seed`.  BM_EINVAL / BM_ENOTPRIME on bad
+ * parameters, BM_ENOMEM. */
+bm_status bm_secret_key_seeded(const bm_key_params *params, uint32_t lwe_secret, uint64_t seed,
+                               bm_secret_key **sk_out);
+
+/* Secret key and evaluation key from `seed`: the secret as in
+ * bm_secret_key_seeded, then the BSK and KSK built on `device` with every
+ * mask and error drawn by the GPU threads that use them (no randomness
+ * crosses the host-device link).  Same keys as bm_keygen given the arrays
+ * these streams define.  Errors as bm_keygen. */
+bm_status bm_keygen_seeded(const bm_key_params *params, uint32_t lwe_secret, double sigma, uint64_t seed,
+                           int device, bm_secret_key **sk_out, bm_eval_key **ek_out);
+
+/* Copies the secret key out: s (n int8, may be NULL) and z (N int8, may be
+ * NULL). */
+bm_status bm_secret_key_get(const bm_secret_key *sk, int8_t *s_out, int8_t *z_out);
+
 /* Device bytes held by an evaluation key (BSK + KSK + tables). */
 size_t bm_eval_key_bytes(const bm_eval_key *ek);
 
@@ -120,6 +165,11 @@ size_t bm_eval_key_bytes(const bm_eval_key *ek);
 bm_status bm_encrypt(const bm_secret_key *sk, uint64_t q, uint32_t t,
                      const uint32_t *msg, const uint64_t *mask, const int8_t *err,
                      size_t count, uint64_t *ct_out);
+
+/* bm_encrypt with the masks and errors drawn from `seed` (kinds 7 and 8 of
+ * the stream layout above; errors of parameter sigma). */
+bm_status bm_encrypt_seeded(const bm_secret_key *sk, uint64_t q, uint32_t t, const uint32_t *msg,
+                            size_t count, double sigma, uint64_t seed, uint64_t *ct_out);
 
 /* LWE decryption on the host: msg = floor((phase t + floor(q/2)) / q) mod t.
  * ct: [count][n+1] in [0, q). */
@@ -274,6 +324,8 @@ bm_status bm_modmul_peak(int device, uint32_t iters, double *rate);
  * BM_EWORKSPACE before anything is launched.
  *  - The first call on a device looks up the array's device address with
  *    that device current; make that first call before any stream capture.
+ *    The lookup is repeated when the device's context has changed since
+ *    (after a cudaDeviceReset), so that call too belongs outside a capture.
  *  - Every call shares the one array: calls whose work overlaps on the GPU
  *    (concurrent streams, or threads) race and corrupt each other.  Order
  *    them on one stream or synchronise between them.

@@ -28,7 +28,8 @@ SYMBOLS = ["bm_keygen", "bm_free_secret_key", "bm_free_eval_key", "bm_eval_key_b
            "bm_sample_extract", "bm_key_switch", "bm_poly_mul", "bm_workspace_status",
            "bm_modmul_peak", "bm_status_str", "bm_bootstrap_batch_noalloc",
            "bm_batch_create", "bm_batch_run", "bm_batch_free", "bm_mod_switch",
-           "bm_arbitrary_workspace_bytes", "bm_bootstrap_arbitrary"]
+           "bm_arbitrary_workspace_bytes", "bm_bootstrap_arbitrary", "bm_secret_key_seeded",
+           "bm_keygen_seeded", "bm_secret_key_get", "bm_encrypt_seeded"]
 
 BATCH_PERSISTENT = 1
 BATCH_GRAPH = 2
@@ -120,6 +121,15 @@ def load(build_if_needed: bool = True) -> C.CDLL:
     L.bm_arbitrary_workspace_bytes.restype = sz
     L.bm_bootstrap_arbitrary.argtypes = [vp, u32, u32, C.c_uint64, vp, u32, vp, vp, vp, sz, vp]
     L.bm_bootstrap_arbitrary.restype = i32
+    L.bm_secret_key_seeded.argtypes = [C.POINTER(_KeyParams), u32, C.c_uint64, C.POINTER(vp)]
+    L.bm_secret_key_seeded.restype = i32
+    L.bm_keygen_seeded.argtypes = [C.POINTER(_KeyParams), u32, C.c_double, C.c_uint64, C.c_int,
+                                   C.POINTER(vp), C.POINTER(vp)]
+    L.bm_keygen_seeded.restype = i32
+    L.bm_secret_key_get.argtypes = [vp, vp, vp]
+    L.bm_secret_key_get.restype = i32
+    L.bm_encrypt_seeded.argtypes = [vp, C.c_uint64, u32, vp, sz, C.c_double, C.c_uint64, vp]
+    L.bm_encrypt_seeded.restype = i32
     L.bm_status_str.argtypes = [i32]
     L.bm_status_str.restype = C.c_char_p
     _lib = L
@@ -177,7 +187,7 @@ class EvalKey:
 def bm_keygen(kp: KeyParams, rnd: dict, device: int = 0) -> tuple[SecretKey, EvalKey]:
     """Key generation from supplied randomness (see synth.key_randomness)."""
     L = load()
-    prm = _KeyParams(kp.n, kp.N, kp.log2_B, kp.l_B, kp.log2_Bks, kp.l_ks, kp.Q)
+    prm = _kparams(kp)
     arrs = {k: np.ascontiguousarray(rnd[k]) for k in
             ("s", "z", "bsk_mask", "bsk_err", "ksk_mask", "ksk_err")}
     if arrs["bsk_mask"].shape[0] != kp.n:
@@ -190,8 +200,54 @@ def bm_keygen(kp: KeyParams, rnd: dict, device: int = 0) -> tuple[SecretKey, Eva
 
 
 def keygen(kp: KeyParams, seed: int, device: int = 0) -> tuple[SecretKey, EvalKey]:
-    """Key generation from a seed: draws the randomness, then bm_keygen."""
+    """Key generation from caller-drawn randomness (synth's numpy streams)."""
     return bm_keygen(kp, synth.key_randomness(kp, seed), device)
+
+
+SECRET_BINARY, SECRET_TERNARY = 0, 1
+
+
+def _kparams(kp: KeyParams) -> _KeyParams:
+    return _KeyParams(kp.n, kp.N, kp.log2_B, kp.l_B, kp.log2_Bks, kp.l_ks, kp.Q)
+
+
+def _secret_kind(kp: KeyParams) -> int:
+    return SECRET_TERNARY if kp.secret == "ternary" else SECRET_BINARY
+
+
+def bm_secret_key_seeded(kp: KeyParams, seed: int) -> SecretKey:
+    """The secret key (s, z) drawn from `seed` on the host (no device)."""
+    prm = _kparams(kp)
+    sk = C.c_void_p()
+    _check(load().bm_secret_key_seeded(C.byref(prm), _secret_kind(kp), seed, C.byref(sk)),
+           "bm_secret_key_seeded")
+    return SecretKey(sk.value, kp)
+
+
+def bm_keygen_seeded(kp: KeyParams, seed: int, device: int = 0) -> tuple[SecretKey, EvalKey]:
+    """Secret and evaluation keys from `seed`, the evaluation key's masks and
+    errors drawn on the device (keygen-from-seed)."""
+    prm = _kparams(kp)
+    sk, ek = C.c_void_p(), C.c_void_p()
+    _check(load().bm_keygen_seeded(C.byref(prm), _secret_kind(kp), kp.sigma, seed, device, C.byref(sk),
+                                   C.byref(ek)), "bm_keygen_seeded")
+    return SecretKey(sk.value, kp), EvalKey(ek.value, kp, device)
+
+
+def bm_secret_key_get(sk: SecretKey) -> tuple[np.ndarray, np.ndarray]:
+    s = np.empty(sk.kp.n, np.int8)
+    z = np.empty(sk.kp.N, np.int8)
+    _check(load().bm_secret_key_get(sk.handle, _ptr(s), _ptr(z)), "bm_secret_key_get")
+    return s, z
+
+
+def bm_encrypt_seeded(sk: SecretKey, q: int, t: int, msg, seed: int, sigma: float | None = None) -> np.ndarray:
+    msg = np.ascontiguousarray(msg, np.uint32)
+    out = np.empty((msg.shape[0], sk.kp.n + 1), np.uint64)
+    sg = sk.kp.sigma if sigma is None else sigma
+    _check(load().bm_encrypt_seeded(sk.handle, q, t, _ptr(msg), msg.shape[0], sg, seed, _ptr(out)),
+           "bm_encrypt_seeded")
+    return out
 
 
 def bm_encrypt(sk: SecretKey, q: int, t: int, msg, mask, err) -> np.ndarray:

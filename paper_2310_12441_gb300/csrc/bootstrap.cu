@@ -914,6 +914,25 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[kMaxDevices];   // device address of the array, per device
+void *g_noalloc_ctx[kMaxDevices];   // the context that address belongs to
+
+// The current context, through the driver entry point of cuCtxGetCurrent
+// (the runtime does not expose it).  Null when it cannot be queried.
+void *current_context() {
+    typedef int (*CtxGet)(void **);
+    static CtxGet fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGet)f;
+    });
+    void *ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
 
 __global__ void k_noalloc_status(const u32 *word, int32_t *out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *out = -(int32_t)(*word);
@@ -939,9 +958,12 @@ extern "C" bm_status bm_bootstrap_batch_noalloc(const bm_eval_key *const *keys, 
     void *scratch = nullptr;
     {
         // Host code sees only a stand-in for the array; its device address is
-        // looked up once per device, with that device current.
+        // looked up once per device, with that device current, and again if
+        // the device's context has changed since (a cudaDeviceReset destroys
+        // the context the address belonged to).
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        void *ctx = current_context();
+        if (!g_noalloc_ptr[dev] || ctx != g_noalloc_ctx[dev]) {
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {
@@ -949,6 +971,7 @@ extern "C" bm_status bm_bootstrap_batch_noalloc(const bm_eval_key *const *keys, 
                 return BM_ECUDA;
             }
             g_noalloc_ptr[dev] = p;
+            g_noalloc_ctx[dev] = ctx;
         }
         scratch = g_noalloc_ptr[dev];
     }

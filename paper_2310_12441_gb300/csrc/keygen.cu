@@ -17,6 +17,7 @@
 
 #include "common.cuh"
 #include "ntt.cuh"
+#include "philox.cuh"
 
 typedef unsigned __int128 u128;
 
@@ -104,26 +105,18 @@ __global__ void k_ntt_z(const int8_t *__restrict__ z, u64 *__restrict__ zhat, Ke
     for (u32 i = threadIdx.x; i < K.N; i += blockDim.x) zhat[i] = sm[i];
 }
 
-// One RGSW row per block (see the file header for the formula).
-__global__ void k_bsk_rows(const u64 *__restrict__ mask, const int8_t *__restrict__ err,
-                           const int8_t *__restrict__ s, const u64 *__restrict__ zhat,
-                           u64 *__restrict__ bsk, KeyDev K) {
-    extern __shared__ u64 sm[];
+// RGSW row `row_id` (absolute index into [n][2][2 l_B]) from its mask
+// (sm[0, N)) and error (sm[N, 2N), in Z_Q), both in the coefficient domain;
+// the whole block calls it (see the file header for the formula).
+__device__ void bsk_row_finish(u64 *sm, size_t row_id, const int8_t *__restrict__ s,
+                               const u64 *__restrict__ zhat, u64 *__restrict__ bsk, const KeyDev &K) {
     const u32 N = K.N, lB = K.l_B;
     const u64 Q = K.mq.Q;
-    const size_t row_id = blockIdx.x;
-    const u64 *a = mask + row_id * N;
-    const int8_t *e = err + row_id * N;
-    for (u32 i = threadIdx.x; i < N; i += blockDim.x) {
-        sm[i] = a[i];
-        int v = e[i];
-        sm[N + i] = v >= 0 ? (u64)v : Q - (u64)(-v);
-    }
     __syncthreads();
     cta_ntt_fwd(sm, 2, K.logN, K.tw, K.twsh, Q);
     const u32 row = (u32)(row_id % (2 * lB));
     const u32 sgn = (u32)((row_id / (2 * lB)) % 2);
-    const u32 k = (u32)(row_id / (4 * lB));
+    const size_t k = row_id / (4 * lB);
     const int sk = s[k];
     const bool mu = sgn == 0 ? sk > 0 : sk < 0;
     u64 g = 0;
@@ -155,24 +148,55 @@ __global__ void k_bsk_rows(const u64 *__restrict__ mask, const int8_t *__restric
     }
 }
 
+__device__ __forceinline__ u64 signed_to_zq(int v, u64 Q) { return v >= 0 ? (u64)v : Q - (u64)(-v); }
+
+// One RGSW row per block from caller-supplied randomness: mask/err hold the
+// rows [row0, row0 + gridDim.x).
+__global__ void k_bsk_rows(const u64 *__restrict__ mask, const int8_t *__restrict__ err,
+                           const int8_t *__restrict__ s, const u64 *__restrict__ zhat,
+                           u64 *__restrict__ bsk, KeyDev K, size_t row0) {
+    extern __shared__ u64 sm[];
+    const u32 N = K.N;
+    const u64 *a = mask + (size_t)blockIdx.x * N;
+    const int8_t *e = err + (size_t)blockIdx.x * N;
+    for (u32 i = threadIdx.x; i < N; i += blockDim.x) {
+        sm[i] = a[i];
+        sm[N + i] = signed_to_zq(e[i], K.mq.Q);
+    }
+    bsk_row_finish(sm, row0 + blockIdx.x, s, zhat, bsk, K);
+}
+
+// One RGSW row per block, its mask and error drawn from the seed's streams
+// (kinds 3 and 4, element index row N + i, domain N).
+__global__ void k_bsk_rows_seeded(uint64_t seed, rng::Cdt cdt, const int8_t *__restrict__ s,
+                                  const u64 *__restrict__ zhat, u64 *__restrict__ bsk, KeyDev K,
+                                  size_t row0) {
+    extern __shared__ u64 sm[];
+    const u32 N = K.N;
+    const size_t row_id = row0 + blockIdx.x;
+    for (u32 i = threadIdx.x; i < N; i += blockDim.x) {
+        const uint64_t idx = (uint64_t)row_id * N + i;
+        sm[i] = rng::uniform_mod(rng::element(seed, rng::kBskMask, N, idx), K.mq.Q);
+        sm[N + i] = signed_to_zq(rng::gaussian(rng::element(seed, rng::kBskErr, N, idx), cdt), K.mq.Q);
+    }
+    bsk_row_finish(sm, row_id, s, zhat, bsk, K);
+}
+
 struct KsGadget { u64 g[16]; };
 
-// One key-switching row per warp: (a', <a', s> + e + v z_i g_j).
-// mask holds rows [row0, row_end) only; err and ksk are indexed absolutely.
-__global__ void k_ksk_rows(const u64 *__restrict__ mask, const int8_t *__restrict__ err,
-                           const int8_t *__restrict__ s, const int8_t *__restrict__ z,
-                           u64 *__restrict__ ksk, KeyDev K, KsGadget G, size_t row0,
-                           size_t row_end) {
-    const size_t warp = row0 + (size_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+// Key-switching row `row` = (i, j, v) by one warp: (a', <a', s> + e + v z_i g_j)
+// with mask word c given by get_a(c).
+template <typename GetA>
+__device__ __forceinline__ void ksk_row(size_t row, GetA get_a, int ev, const int8_t *__restrict__ s,
+                                        const int8_t *__restrict__ z, u64 *__restrict__ ksk, const KeyDev &K,
+                                        const KsGadget &G) {
     const u32 lane = threadIdx.x & 31;
-    if (warp >= row_end) return;
     const u32 n = K.n, B1 = (1u << K.log2_Bks) - 1;
     const u64 Q = K.mq.Q;
-    const u64 *a = mask + (warp - row0) * n;
-    u64 *o = ksk + warp * (n + 1);
+    u64 *o = ksk + row * (n + 1);
     u64 lo = 0, hi = 0;
     for (u32 c = lane; c < n; c += 32) {
-        const u64 x = a[c];
+        const u64 x = get_a(c);
         o[c] = x;
         const int sc = s[c];
         if (sc > 0) add128(lo, hi, x);
@@ -181,18 +205,42 @@ __global__ void k_ksk_rows(const u64 *__restrict__ mask, const int8_t *__restric
     u64 acc = reduce128(lo, hi, K.mq);
     for (int off = 16; off; off >>= 1) acc = add_mod(acc, __shfl_down_sync(0xffffffffu, acc, off), Q);
     if (lane == 0) {
-        const u32 v = (u32)(warp % B1) + 1;
-        const u32 j = (u32)((warp / B1) % K.l_ks);
-        const u32 i = (u32)(warp / ((size_t)B1 * K.l_ks));
+        const u32 v = (u32)(row % B1) + 1;
+        const u32 j = (u32)((row / B1) % K.l_ks);
+        const u32 i = (u32)(row / ((size_t)B1 * K.l_ks));
         u64 l2 = 0, h2 = 0;
         mac128(l2, h2, v, G.g[j]);
         u64 vg = reduce128(l2, h2, K.mq);
         const int zi = z[i];
         u64 msg = zi > 0 ? vg : (zi < 0 ? (vg ? Q - vg : 0) : 0);
-        const int ev = err[warp];
-        const u64 e = ev >= 0 ? (u64)ev : Q - (u64)(-ev);
-        o[n] = add_mod(add_mod(acc, e, Q), msg, Q);
+        o[n] = add_mod(add_mod(acc, signed_to_zq(ev, Q), Q), msg, Q);
     }
+}
+
+// One key-switching row per warp from caller-supplied randomness: mask holds
+// rows [row0, row_end) only; err is indexed absolutely.
+__global__ void k_ksk_rows(const u64 *__restrict__ mask, const int8_t *__restrict__ err,
+                           const int8_t *__restrict__ s, const int8_t *__restrict__ z,
+                           u64 *__restrict__ ksk, KeyDev K, KsGadget G, size_t row0,
+                           size_t row_end) {
+    const size_t row = row0 + (size_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (row >= row_end) return;
+    const u64 *a = mask + (row - row0) * K.n;
+    ksk_row(row, [&](u32 c) { return a[c]; }, err[row], s, z, ksk, K, G);
+}
+
+// One key-switching row per warp, mask and error drawn from the seed's
+// streams (kinds 5 and 6, domain N).
+__global__ void k_ksk_rows_seeded(uint64_t seed, rng::Cdt cdt, const int8_t *__restrict__ s,
+                                  const int8_t *__restrict__ z, u64 *__restrict__ ksk, KeyDev K, KsGadget G,
+                                  size_t rows) {
+    const size_t row = (size_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (row >= rows) return;
+    const u32 N = K.N, n = K.n;
+    const u64 Q = K.mq.Q;
+    const int ev = rng::gaussian(rng::element(seed, rng::kKskErr, N, row), cdt);
+    ksk_row(row, [&](u32 c) { return rng::uniform_mod(rng::element(seed, rng::kKskMask, N, (uint64_t)row * n + c), Q); },
+            ev, s, z, ksk, K, G);
 }
 
 // ---------------------------------------------------------------------------
@@ -259,8 +307,16 @@ struct DevBuf {
 };
 }  // namespace
 
-static bm_status keygen_impl(const bm_key_params *params, const bm_key_randomness *rnd,
-                             bm_eval_key *ek) {
+// Where the randomness of key generation comes from: caller arrays (rnd), or
+// the seed's Philox streams (rnd == nullptr).
+struct KeySource {
+    const bm_key_randomness *rnd;
+    uint64_t seed;
+    rng::Cdt cdt;
+};
+
+static bm_status keygen_impl(const bm_key_params *params, const int8_t *s, const int8_t *z,
+                             const KeySource &src, bm_eval_key *ek) {
     const bm_key_params &p = *params;
     const u32 N = p.N, n = p.n, lB = p.l_B;
     u32 logN = 0;
@@ -314,17 +370,18 @@ static bm_status keygen_impl(const bm_key_params *params, const bm_key_randomnes
     DevBuf d_s, d_z;
     BM_CUDA_TRY(cudaMalloc(&d_s.p, n));
     BM_CUDA_TRY(cudaMalloc(&d_z.p, N));
-    BM_CUDA_TRY(cudaMemcpy(d_s.p, rnd->s, n, cudaMemcpyHostToDevice));
-    BM_CUDA_TRY(cudaMemcpy(d_z.p, rnd->z, N, cudaMemcpyHostToDevice));
+    BM_CUDA_TRY(cudaMemcpy(d_s.p, s, n, cudaMemcpyHostToDevice));
+    BM_CUDA_TRY(cudaMemcpy(d_z.p, z, N, cudaMemcpyHostToDevice));
 
     const u32 threads = N / 2 < 512 ? N / 2 : 512;
     k_ntt_z<<<1, threads, N * 8>>>((const int8_t *)d_z.p, d_zhat, K);
     BM_CUDA_TRY(cudaGetLastError());
 
-    // Bootstrapping keys, in chunks of key indices to bound staging memory.
-    {
-        const size_t rows_per_k = 2 * 2 * (size_t)lB;
-        const u32 kchunk = 64;
+    // Bootstrapping keys: one RGSW row per block, in chunks of key indices
+    // (which bounds the staging memory of caller-supplied randomness).
+    const size_t rows_per_k = 2 * 2 * (size_t)lB;
+    const u32 kchunk = 64;
+    if (src.rnd) {
         DevBuf d_mask, d_err;
         BM_CUDA_TRY(cudaMalloc(&d_mask.p, kchunk * rows_per_k * N * 8));
         BM_CUDA_TRY(cudaMalloc(&d_err.p, kchunk * rows_per_k * N));
@@ -333,33 +390,44 @@ static bm_status keygen_impl(const bm_key_params *params, const bm_key_randomnes
         for (u32 k0 = 0; k0 < n; k0 += kchunk) {
             const u32 k1 = k0 + kchunk < n ? k0 + kchunk : n;
             const size_t rows = (size_t)(k1 - k0) * rows_per_k;
-            BM_CUDA_TRY(cudaMemcpy(d_mask.p, rnd->bsk_mask + (size_t)k0 * rows_per_k * N,
+            BM_CUDA_TRY(cudaMemcpy(d_mask.p, src.rnd->bsk_mask + (size_t)k0 * rows_per_k * N,
                                    rows * N * 8, cudaMemcpyHostToDevice));
-            BM_CUDA_TRY(cudaMemcpy(d_err.p, rnd->bsk_err + (size_t)k0 * rows_per_k * N, rows * N,
+            BM_CUDA_TRY(cudaMemcpy(d_err.p, src.rnd->bsk_err + (size_t)k0 * rows_per_k * N, rows * N,
                                    cudaMemcpyHostToDevice));
-            // the kernel derives k from the row id, so offset the secret
-            k_bsk_rows<<<(unsigned)rows, threads, 2 * N * 8>>>(
-                (const u64 *)d_mask.p, (const int8_t *)d_err.p, (const int8_t *)d_s.p + k0, d_zhat,
-                ek->d_bsk + (size_t)k0 * rows_per_k * 2 * N, K);
+            k_bsk_rows<<<(unsigned)rows, threads, 2 * N * 8>>>((const u64 *)d_mask.p, (const int8_t *)d_err.p,
+                                                                (const int8_t *)d_s.p, d_zhat, ek->d_bsk, K,
+                                                                (size_t)k0 * rows_per_k);
             BM_CUDA_TRY(cudaGetLastError());
             BM_CUDA_TRY(cudaDeviceSynchronize());
         }
+    } else {
+        BM_CUDA_TRY(cudaFuncSetAttribute(k_bsk_rows_seeded, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * N * 8));
+        for (u32 k0 = 0; k0 < n; k0 += kchunk) {
+            const u32 k1 = k0 + kchunk < n ? k0 + kchunk : n;
+            const size_t rows = (size_t)(k1 - k0) * rows_per_k;
+            k_bsk_rows_seeded<<<(unsigned)rows, threads, 2 * N * 8>>>(src.seed, src.cdt, (const int8_t *)d_s.p,
+                                                                       d_zhat, ek->d_bsk, K,
+                                                                       (size_t)k0 * rows_per_k);
+            BM_CUDA_TRY(cudaGetLastError());
+        }
+        BM_CUDA_TRY(cudaDeviceSynchronize());
     }
-    // Key-switching keys.
-    {
-        KsGadget G;
-        memset(&G, 0, sizeof(G));
-        const u128 P = (u128)1 << (p.log2_Bks * p.l_ks);
-        for (u32 j = 0; j < p.l_ks && j < 16; j++)
-            G.g[j] = (u64)((((u128)Q << (p.log2_Bks * j)) + P / 2) / P);
+    // Key-switching keys: one LWE row per warp.
+    KsGadget G;
+    memset(&G, 0, sizeof(G));
+    const u128 P = (u128)1 << (p.log2_Bks * p.l_ks);
+    for (u32 j = 0; j < p.l_ks && j < 16; j++)
+        G.g[j] = (u64)((((u128)Q << (p.log2_Bks * j)) + P / 2) / P);
+    if (src.rnd) {
         const size_t chunk_rows = 1u << 16;
         DevBuf d_mask, d_err;
         BM_CUDA_TRY(cudaMalloc(&d_mask.p, chunk_rows * n * 8));
         BM_CUDA_TRY(cudaMalloc(&d_err.p, ksk_rows));
-        BM_CUDA_TRY(cudaMemcpy(d_err.p, rnd->ksk_err, ksk_rows, cudaMemcpyHostToDevice));
+        BM_CUDA_TRY(cudaMemcpy(d_err.p, src.rnd->ksk_err, ksk_rows, cudaMemcpyHostToDevice));
         for (size_t r0 = 0; r0 < ksk_rows; r0 += chunk_rows) {
             const size_t r1 = r0 + chunk_rows < ksk_rows ? r0 + chunk_rows : ksk_rows;
-            BM_CUDA_TRY(cudaMemcpy(d_mask.p, rnd->ksk_mask + r0 * n, (r1 - r0) * n * 8,
+            BM_CUDA_TRY(cudaMemcpy(d_mask.p, src.rnd->ksk_mask + r0 * n, (r1 - r0) * n * 8,
                                    cudaMemcpyHostToDevice));
             const size_t rows = r1 - r0;
             const unsigned blocks = (unsigned)((rows + 7) / 8);
@@ -369,7 +437,49 @@ static bm_status keygen_impl(const bm_key_params *params, const bm_key_randomnes
             BM_CUDA_TRY(cudaGetLastError());
             BM_CUDA_TRY(cudaDeviceSynchronize());
         }
+    } else {
+        const unsigned blocks = (unsigned)((ksk_rows + 7) / 8);
+        k_ksk_rows_seeded<<<blocks, 256>>>(src.seed, src.cdt, (const int8_t *)d_s.p, (const int8_t *)d_z.p,
+                                           ek->d_ksk, K, G, ksk_rows);
+        BM_CUDA_TRY(cudaGetLastError());
+        BM_CUDA_TRY(cudaDeviceSynchronize());
     }
+    return BM_OK;
+}
+
+static bm_secret_key *new_secret_key(const bm_key_params &p) {
+    bm_secret_key *sk = new (std::nothrow) bm_secret_key();
+    if (!sk) return nullptr;
+    sk->p = p;
+    sk->s = (int8_t *)malloc(p.n);
+    sk->z = (int8_t *)malloc(p.N);
+    if (!sk->s || !sk->z) {
+        bm_free_secret_key(sk);
+        return nullptr;
+    }
+    return sk;
+}
+
+// Builds the evaluation key on `device` for secret key sk.
+static bm_status make_eval_key(const bm_key_params *params, const bm_secret_key *sk, const KeySource &src,
+                               int device, bm_eval_key **ek_out) {
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess) return BM_ECUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return BM_EINVAL;
+    bm_eval_key *ek = new (std::nothrow) bm_eval_key();
+    if (!ek) {
+        cudaSetDevice(prev);
+        return BM_ENOMEM;
+    }
+    ek->device = device;
+    ek->p = *params;
+    bm_status st = keygen_impl(params, sk->s, sk->z, src, ek);
+    cudaSetDevice(prev);
+    if (st != BM_OK) {
+        bm_free_eval_key(ek);
+        return st;
+    }
+    *ek_out = ek;
     return BM_OK;
 }
 
@@ -384,27 +494,59 @@ extern "C" bm_status bm_keygen(const bm_key_params *params, const bm_key_randomn
         if (rnd->s[i] < -1 || rnd->s[i] > 1) return BM_EINVAL;
     for (u32 i = 0; i < params->N; i++)
         if (rnd->z[i] < -1 || rnd->z[i] > 1) return BM_EINVAL;
-    int prev = 0;
-    if (cudaGetDevice(&prev) != cudaSuccess) return BM_ECUDA;
-    if (cudaSetDevice(device) != cudaSuccess) return BM_EINVAL;
-    bm_eval_key *ek = new (std::nothrow) bm_eval_key();
-    if (!ek) return BM_ENOMEM;
-    ek->device = device;
-    ek->p = *params;
-    st = keygen_impl(params, rnd, ek);
-    cudaSetDevice(prev);
-    if (st != BM_OK) {
-        bm_free_eval_key(ek);
-        return st;
-    }
-    bm_secret_key *sk = new (std::nothrow) bm_secret_key();
-    sk->p = *params;
-    sk->s = (int8_t *)malloc(params->n);
-    sk->z = (int8_t *)malloc(params->N);
+    bm_secret_key *sk = new_secret_key(*params);
+    if (!sk) return BM_ENOMEM;
     memcpy(sk->s, rnd->s, params->n);
     memcpy(sk->z, rnd->z, params->N);
+    KeySource src{rnd, 0, {}};
+    st = make_eval_key(params, sk, src, device, ek_out);
+    if (st != BM_OK) {
+        bm_free_secret_key(sk);
+        return st;
+    }
     *sk_out = sk;
-    *ek_out = ek;
+    return BM_OK;
+}
+
+extern "C" bm_status bm_secret_key_seeded(const bm_key_params *params, uint32_t lwe_secret, uint64_t seed,
+                                          bm_secret_key **sk_out) {
+    if (!params || !sk_out || lwe_secret > BM_SECRET_TERNARY) return BM_EINVAL;
+    bm_status st = bm_check_key_params(params);
+    if (st != BM_OK) return st;
+    bm_secret_key *sk = new_secret_key(*params);
+    if (!sk) return BM_ENOMEM;
+    for (u32 k = 0; k < params->n; k++) {
+        const rng::Block b = rng::element(seed, rng::kLweSecret, 0, k);
+        sk->s[k] = (int8_t)(lwe_secret == BM_SECRET_TERNARY ? rng::ternary(b) : rng::binary(b));
+    }
+    for (u32 i = 0; i < params->N; i++)
+        sk->z[i] = (int8_t)rng::ternary(rng::element(seed, rng::kRlweSecret, params->N, i));
+    *sk_out = sk;
+    return BM_OK;
+}
+
+extern "C" bm_status bm_keygen_seeded(const bm_key_params *params, uint32_t lwe_secret, double sigma,
+                                      uint64_t seed, int device, bm_secret_key **sk_out,
+                                      bm_eval_key **ek_out) {
+    if (!params || !sk_out || !ek_out || !(sigma > 0.0) || sigma > BM_SIGMA_MAX) return BM_EINVAL;
+    bm_secret_key *sk = nullptr;
+    bm_status st = bm_secret_key_seeded(params, lwe_secret, seed, &sk);
+    if (st != BM_OK) return st;
+    KeySource src{nullptr, seed, {}};
+    rng::make_cdt(sigma, src.cdt);
+    st = make_eval_key(params, sk, src, device, ek_out);
+    if (st != BM_OK) {
+        bm_free_secret_key(sk);
+        return st;
+    }
+    *sk_out = sk;
+    return BM_OK;
+}
+
+extern "C" bm_status bm_secret_key_get(const bm_secret_key *sk, int8_t *s_out, int8_t *z_out) {
+    if (!sk) return BM_EINVAL;
+    if (s_out) memcpy(s_out, sk->s, sk->p.n);
+    if (z_out) memcpy(z_out, sk->z, sk->p.N);
     return BM_OK;
 }
 
@@ -412,27 +554,48 @@ extern "C" bm_status bm_keygen(const bm_key_params *params, const bm_key_randomn
 // Client-side LWE encryption / decryption (Section 2 item (8))
 // ---------------------------------------------------------------------------
 
+// ct = (a, <a, s> + msg floor(q/t) + e) mod q, mask word c = mask(c) in [0, q).
+template <typename Mask>
+static void encrypt_one(const bm_secret_key *sk, u64 q, u32 t, u32 msg, Mask mask, int e, u64 *o) {
+    const u32 n = sk->p.n;
+    const u64 delta = q / t;
+    u128 pos = 0, neg = 0;
+    for (u32 c = 0; c < n; c++) {
+        const u64 a = mask(c);
+        o[c] = a;
+        if (sk->s[c] > 0) pos += a;
+        else if (sk->s[c] < 0) neg += a;
+    }
+    pos += (u128)(msg % t) * delta + (e >= 0 ? (u64)e : 0);
+    neg += e < 0 ? (u64)(-e) : 0;
+    const u64 pm = (u64)(pos % q), nm = (u64)(neg % q);
+    o[n] = pm >= nm ? pm - nm : pm + q - nm;
+}
+
 extern "C" bm_status bm_encrypt(const bm_secret_key *sk, uint64_t q, uint32_t t,
                                 const uint32_t *msg, const uint64_t *mask, const int8_t *err,
                                 size_t count, uint64_t *ct_out) {
     if (!sk || !msg || !mask || !err || !ct_out || q < 2 || t < 2 || t > q) return BM_EINVAL;
     const u32 n = sk->p.n;
-    const u64 delta = q / t;
+    for (size_t i = 0; i < count * n; i++)
+        if (mask[i] >= q) return BM_EINVAL;
+    for (size_t i = 0; i < count; i++)
+        encrypt_one(sk, q, t, msg[i], [&](u32 c) { return mask[i * n + c]; }, err[i], ct_out + i * (n + 1));
+    return BM_OK;
+}
+
+extern "C" bm_status bm_encrypt_seeded(const bm_secret_key *sk, uint64_t q, uint32_t t, const uint32_t *msg,
+                                       size_t count, double sigma, uint64_t seed, uint64_t *ct_out) {
+    if (!sk || !msg || !ct_out || q < 2 || t < 2 || t > q || !(sigma > 0.0) || sigma > BM_SIGMA_MAX)
+        return BM_EINVAL;
+    const u32 n = sk->p.n;
+    rng::Cdt cdt;
+    rng::make_cdt(sigma, cdt);
     for (size_t i = 0; i < count; i++) {
-        u64 *o = ct_out + i * (n + 1);
-        u128 pos = 0, neg = 0;
-        for (u32 c = 0; c < n; c++) {
-            const u64 a = mask[i * n + c];
-            if (a >= q) return BM_EINVAL;
-            o[c] = a;
-            if (sk->s[c] > 0) pos += a;
-            else if (sk->s[c] < 0) neg += a;
-        }
-        const int e = err[i];
-        pos += (u128)(msg[i] % t) * delta + (e >= 0 ? (u64)e : 0);
-        neg += e < 0 ? (u64)(-e) : 0;
-        const u64 pm = (u64)(pos % q), nm = (u64)(neg % q);
-        o[n] = pm >= nm ? pm - nm : pm + q - nm;
+        const int e = rng::gaussian(rng::element(seed, rng::kEncErr, 0, i), cdt);
+        encrypt_one(sk, q, t, msg[i],
+                    [&](u32 c) { return rng::uniform_mod(rng::element(seed, rng::kEncMask, 0, (uint64_t)i * n + c), q); },
+                    e, ct_out + i * (n + 1));
     }
     return BM_OK;
 }

@@ -13,6 +13,16 @@ admitted as soon as a stream frees up and their work overlaps on the device.
 
 Latency of a request = completion time - arrival time (the scheduled Poisson
 arrival, so a late producer does not hide queueing).
+
+Failures: tables are checked for negacyclicity at admission (refused with
+BM_ENONNEGACYCLIC).  After every batch the completion thread reads (and
+clears) the workspace status word; if the device reported an error, each
+request of that batch is run again alone on the same stream and only the
+ones that fail again are marked failed, with the device's code.
+
+Memory: the per-stream buffers are sized up front for `max_batch` requests
+of the largest shape admitted (rows up to `max_m`, tables up to 2 N max_m
+entries), and that reservation counts against the memory cap with the keys.
 """
 from __future__ import annotations
 
@@ -27,6 +37,7 @@ from . import api
 from .workload import KeySet
 
 BM_EBUSY = -7
+BM_ENONNEGACYCLIC = -4
 
 
 @dataclass
@@ -40,6 +51,7 @@ class Request:
     arrival: float
     done: float = 0.0
     out: np.ndarray | None = None
+    status: int = 0         # 0, or the device's error code for this request
 
 
 @dataclass
@@ -47,6 +59,7 @@ class Stats:
     accepted: int = 0
     rejected: int = 0
     completed: int = 0
+    failed: int = 0
     batches: int = 0
     latencies: list = field(default_factory=list)
 
@@ -54,7 +67,7 @@ class Stats:
 class Server:
     def __init__(self, keysets: list[KeySet], max_batch: int = 512, streams: int = 3,
                  queue_cap: int = 2048, mem_cap_bytes: int = 120 << 30, device: int = 0,
-                 keep_outputs: bool = False):
+                 keep_outputs: bool = False, max_m: int = 8, validate_tables: bool = True):
         import torch
         self.torch = torch
         self.keysets = keysets
@@ -63,8 +76,13 @@ class Server:
         self.queue_cap = queue_cap
         self.mem_cap = mem_cap_bytes
         self.keep_outputs = keep_outputs
+        self.max_m = max_m
+        self.validate_tables = validate_tables
         self.dev = torch.device("cuda", device)
         self.key_bytes = sum(k.nbytes for k in self.keys)
+        # per-stream buffers for max_batch requests of the largest shape
+        worst = max(self._bytes(ks.kp, max_m, 2 * ks.kp.N * max_m) for ks in keysets)
+        self.slab_bytes = int(1.25 * streams * max_batch * worst)   # buffers grow by 1.25x steps
         self.q: collections.deque[Request] = collections.deque()
         self.lock = threading.Condition()
         self.inflight_bytes = 0
@@ -80,16 +98,32 @@ class Server:
         self.threads = []
 
     # -- admission -------------------------------------------------------------------
+    @staticmethod
+    def _bytes(kp, m: int, t: int) -> int:
+        """Device bytes of one request: input and output ciphertext, table,
+        and the three [m][2][N] accumulator buffers of its workspace."""
+        return 2 * (kp.n + 1) * 8 + t * 4 + 3 * 2 * m * kp.N * 8 + 64
+
     def request_bytes(self, r: Request) -> int:
-        kp = self.keysets[r.key].kp
-        return (2 * (kp.n + 1) * 8 + r.t * 4 + 3 * 2 * r.m * kp.N * 8 + 64)
+        return self._bytes(self.keysets[r.key].kp, r.m, r.t)
 
     def submit(self, r: Request) -> int:
-        """Admits a request (0) or refuses it (BM_EBUSY)."""
+        """Admits a request (0) or refuses it (BM_EBUSY; BM_ENONNEGACYCLIC
+        for a table that is not negacyclic when tables are validated)."""
+        if r.m > self.max_m:
+            return BM_EBUSY
+        if self.validate_tables:
+            lut = np.asarray(r.lut, dtype=np.int64)
+            h = r.t // 2
+            if lut.size != r.t or (lut >= r.t).any() or \
+                    not np.array_equal(lut[h:], (r.t - lut[:h]) % r.t):
+                with self.lock:
+                    self.stats.rejected += 1
+                return BM_ENONNEGACYCLIC
         nb = self.request_bytes(r)
         with self.lock:
             if len(self.q) >= self.queue_cap or \
-                    self.key_bytes + self.inflight_bytes + nb > self.mem_cap:
+                    self.key_bytes + self.slab_bytes + self.inflight_bytes + nb > self.mem_cap:
                 self.stats.rejected += 1
                 return BM_EBUSY
             self.inflight_bytes += nb
@@ -107,6 +141,9 @@ class Server:
                 n2 = max(n, int(1.25 * (cur.numel() if cur is not None else 0)))
                 if pinned:
                     slab[name] = torch.empty(n2, dtype=dtype).pin_memory()
+                elif name == "ws":
+                    # the workspace's status word must start at zero
+                    slab[name] = torch.zeros(n2, dtype=dtype, device=self.dev)
                 else:
                     slab[name] = torch.empty(n2, dtype=dtype, device=self.dev)
         grow("in", words_in, torch.int64)
@@ -144,8 +181,20 @@ class Server:
             ev.record(st)
         return jobs, ev
 
+    def _isolate(self, slab, reqs: list[Request], code: int):
+        """The device reported `code` for a batch: run each request alone on
+        the slab's stream and mark those that fail again."""
+        for r in reqs:
+            _, ev = self._launch(slab, [r])
+            ev.synchronize()
+            c = api.bm_workspace_status(slab["ws"], slab["stream"])
+            r.status = c
+            if c == 0 and self.keep_outputs:
+                r.out = slab["h_out"].numpy().view(np.uint64)[:r.ct.size].copy()
+
     def _complete(self, slab, reqs, jobs, ev):
         ev.synchronize()
+        code = api.bm_workspace_status(slab["ws"], slab["stream"])   # reads and clears
         now = time.perf_counter()
         out = slab["h_out"].numpy().view(np.uint64)
         nb = 0
@@ -155,10 +204,14 @@ class Server:
                 o = int(jobs[j]["out_off"])
                 r.out = out[o:o + r.ct.size].copy()
             nb += self.request_bytes(r)
+        if code != 0:
+            self._isolate(slab, reqs, code)
+        failed = sum(1 for r in reqs if r.status != 0)
         with self.lock:
             self.inflight_bytes -= nb
-            self.stats.completed += len(reqs)
-            self.stats.latencies.extend(r.done - r.arrival for r in reqs)
+            self.stats.completed += len(reqs) - failed
+            self.stats.failed += failed
+            self.stats.latencies.extend(r.done - r.arrival for r in reqs if r.status == 0)
             slab["busy"] = False
             self.lock.notify_all()
 
@@ -226,7 +279,8 @@ def run_open_loop(server: Server, pool: list[tuple[int, int, int, np.ndarray, np
     lat = np.array(server.stats.latencies) if server.stats.latencies else np.array([np.nan])
     return {"rate": rate, "duration_s": duration, "offered": int(len(arr)),
             "accepted": server.stats.accepted, "rejected": server.stats.rejected,
-            "completed": server.stats.completed, "batches": server.stats.batches,
+            "completed": server.stats.completed, "failed": server.stats.failed,
+            "batches": server.stats.batches,
             "throughput": server.stats.completed / (end - t0),
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "drain_s": end - offered_end, "requests": reqs}

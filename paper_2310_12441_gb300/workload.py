@@ -1,8 +1,8 @@
 """Assembles bootstrapping batches from seeded synthetic inputs.
 
 A batch is a list of jobs (bm_job records) with their input ciphertexts,
-look-up tables and expected plaintexts.  Inputs are encrypted with the
-library's own client-side bm_encrypt; the randomness comes from synth.
+look-up tables and expected plaintexts.  Keys and encryptions come from the
+library's seeded entry points; messages and tables from synth.
 """
 from __future__ import annotations
 
@@ -23,8 +23,8 @@ class KeySet:
 
 
 def make_keyset(kp: KeyParams, seed: int, device: int = 0) -> KeySet:
-    rnd = synth.key_randomness(kp, seed)
-    sk, ek = api.bm_keygen(kp, rnd, device)
+    """Keys from a seed, the evaluation key drawn and built on the device."""
+    sk, ek = api.bm_keygen_seeded(kp, seed, device)
     return KeySet(kp, sk, ek, seed)
 
 
@@ -54,8 +54,7 @@ def make_batch(keysets: list[KeySet], groups: list[tuple[int, JobShape, int]], s
         qp = 2 * kp.N * m
         luts, ident = synth.luts(t, count, 2000 + seed + 17 * g, mix=lut_mix)
         msg = synth.messages(t, count, 3000 + seed + 17 * g, half=ident)
-        enc = synth.encryption_randomness(kp.n, qp, kp.sigma, count, 4000 + seed + 17 * g)
-        ct = api.bm_encrypt(ks.sk, qp, t, msg, enc["mask"], enc["err"])
+        ct = api.bm_encrypt_seeded(ks.sk, qp, t, msg, 4000 + seed + 17 * g)
         dec = api.bm_decrypt(ks.sk, qp, t, ct)
         for i in range(count):
             parts.append((ki, m, t, ct[i], luts[i], msg[i], dec[i], luts[i][dec[i]]))

@@ -63,3 +63,43 @@ def test_admission_refuses_beyond_limits(env):
     assert codes[:3] == [0, 0, 0] and all(c == serve.BM_EBUSY for c in codes[3:])
     small = serve.Server(ksets, mem_cap_bytes=sum(k.ek.nbytes for k in ksets) + 1)
     assert small.submit(serve.Request(0, *pool[0], arrival=0.0)) == serve.BM_EBUSY
+    # the stream buffers' reservation counts against the cap too
+    roomy = serve.Server(ksets, max_batch=4, streams=1)
+    tight = serve.Server(ksets, max_batch=4, streams=1,
+                         mem_cap_bytes=roomy.key_bytes + roomy.slab_bytes // 2)
+    assert roomy.submit(serve.Request(0, *pool[0], arrival=0.0)) == 0
+    assert tight.submit(serve.Request(0, *pool[0], arrival=0.0)) == serve.BM_EBUSY
+
+
+def test_device_error_is_reported_for_the_bad_request_only(env):
+    """A table that is not negacyclic, let through admission, makes the device
+    set the workspace status word; the server reads it, re-runs the batch's
+    requests alone, and fails only the bad one (BM_ENONNEGACYCLIC).  With table
+    validation on, admission refuses it."""
+    api, serve, wl, ksets = env
+    pool = _pool(wl, ksets)[:6]
+    key, m, t, ct, lut = pool[2]
+    bad_lut = lut.copy()
+    bad_lut[t // 2] = (bad_lut[t // 2] + 1) % t
+    pool[2] = (key, m, t, ct, bad_lut)
+    srv = serve.Server(ksets, max_batch=8, streams=1, keep_outputs=True, validate_tables=False)
+    reqs = [serve.Request(i, *pool[i], arrival=0.0) for i in range(len(pool))]
+    assert all(srv.submit(r) == 0 for r in reqs)       # queued before the scheduler starts
+    srv.start()
+    srv.drain_and_stop()
+    assert srv.stats.batches == 1
+    assert [r.status for r in reqs] == [0, 0, serve.BM_ENONNEGACYCLIC, 0, 0, 0]
+    assert srv.stats.failed == 1 and srv.stats.completed == 5
+    keys = [k.ek for k in ksets]
+    for r in reqs:
+        if r.status:
+            continue
+        n = ksets[r.key].kp.n
+        job = api.make_jobs(r.key, r.m, r.t, 0, 0, 0)
+        d_out = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+        ws = api.workspace(api.bm_workspace_bytes(keys, job))
+        api.bm_bootstrap_batch(keys, job, api.to_device_u64(r.ct), api.to_device_u32(r.lut), d_out, ws)
+        torch.cuda.synchronize()
+        assert np.array_equal(api.from_device_u64(d_out), r.out), r.rid
+    strict = serve.Server(ksets, max_batch=8, streams=1)
+    assert strict.submit(serve.Request(9, *pool[2], arrival=0.0)) == serve.BM_ENONNEGACYCLIC
