@@ -70,6 +70,15 @@ def lib():
         L.orc_bootstrap.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_uint32, u64p, C.c_uint32,
                                     u64p, u64p, u32p, C.c_size_t, u64p]
         L.orc_bootstrap.restype = C.c_int
+        L.orc_mmpm_apply_gen.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, u32p, C.c_uint64, u64p, u64p]
+        L.orc_mmpm_step_gen.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, u32p, u64p, u64p]
+        L.orc_test_vector_gen.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64, u32p, u32p, u64p]
+        L.orc_blind_rotate_gen.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_uint32, u32p, u64p,
+                                           C.c_uint32, u64p, u32p, u64p, C.c_int]
+        L.orc_blind_rotate_gen.restype = C.c_int
+        L.orc_bootstrap_gen.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_uint32, u32p, u64p,
+                                        C.c_uint32, u64p, u64p, u32p, C.c_size_t, u64p]
+        L.orc_bootstrap_gen.restype = C.c_int
         L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
         L.orc_draw_uniform.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64]
         L.orc_draw_uniform.restype = C.c_uint64
@@ -301,6 +310,67 @@ def bootstrap_arbitrary(kp, m: int, t: int, q: int, bsk, ksk, ct_in, f) -> np.nd
     prm = _params(kp)
     rc = lib().orc_bootstrap_arbitrary(C.byref(prm), m, t, q, pb, bsk.shape[0], pk, pc, pf,
                                        ct_in.shape[0], out.ctypes.data_as(u64p))
+    if rc != 0:
+        raise ValueError("ciphertext uses a bootstrapping key that was not provided")
+    return out
+
+
+# -- general transitive generators (Theorem 1) ------------------------------------------
+
+def mmpm_apply_gen(N: int, m: int, Q: int, u, c: int, vec) -> np.ndarray:
+    """P(c) = A^c times an RLWE vector [m][2][N], A the generator of exponents
+    u (Lemma 3's closed form)."""
+    u, pu = _p(u, np.uint32, u32p)
+    vec, pv = _p(vec, np.uint64, u64p)
+    out = np.empty((m, 2, N), np.uint64)
+    lib().orc_mmpm_apply_gen(N, m, Q, pu, int(c), pv, out.ctypes.data_as(u64p))
+    return out
+
+
+def mmpm_step_gen(N: int, m: int, Q: int, u, vec) -> np.ndarray:
+    """One application of the generator A (no closed form involved)."""
+    u, pu = _p(u, np.uint32, u32p)
+    vec, pv = _p(vec, np.uint64, u64p)
+    out = np.empty((m, 2, N), np.uint64)
+    lib().orc_mmpm_step_gen(N, m, Q, pu, pv, out.ctypes.data_as(u64p))
+    return out
+
+
+def test_vector_gen(N: int, m: int, t: int, Q: int, u, lut) -> np.ndarray:
+    u, pu = _p(u, np.uint32, u32p)
+    lut, pl = _p(lut, np.uint32, u32p)
+    v = np.empty((m, N), np.uint64)
+    lib().orc_test_vector_gen(N, m, t, Q, pu, pl, v.ctypes.data_as(u64p))
+    return v
+
+
+def blind_rotate_gen(kp, m: int, t: int, u, bsk, ct, lut, parallel: bool = True) -> np.ndarray:
+    u, pu = _p(u, np.uint32, u32p)
+    bsk, pb = _p(bsk, np.uint64, u64p)
+    ct, pc = _p(ct, np.uint64, u64p)
+    lut, pl = _p(lut, np.uint32, u32p)
+    acc = np.empty((m, 2, kp.N), np.uint64)
+    prm = _params(kp)
+    rc = lib().orc_blind_rotate_gen(C.byref(prm), m, t, pu, pb, bsk.shape[0], pc, pl,
+                                    acc.ctypes.data_as(u64p), int(parallel))
+    if rc != 0:
+        raise ValueError("ciphertext uses a bootstrapping key that was not provided")
+    return acc
+
+
+def bootstrap_gen(kp, m: int, t: int, u, bsk, ksk, ct_in, luts) -> np.ndarray:
+    """Algorithm 1 (modulus switches excluded) with generator exponents u
+    ([count][m]) per ciphertext."""
+    ct_in, pc = _p(np.atleast_2d(ct_in), np.uint64, u64p)
+    count = ct_in.shape[0]
+    u, pu = _p(np.broadcast_to(np.asarray(u, np.uint32).reshape(-1, m), (count, m)), np.uint32, u32p)
+    bsk, pb = _p(bsk, np.uint64, u64p)
+    ksk, pk = _p(ksk, np.uint64, u64p)
+    luts, pl = _p(np.atleast_2d(luts), np.uint32, u32p)
+    out = np.empty((count, kp.n + 1), np.uint64)
+    prm = _params(kp)
+    rc = lib().orc_bootstrap_gen(C.byref(prm), m, t, pu, pb, bsk.shape[0], pk, pc, pl, count,
+                                 out.ctypes.data_as(u64p))
     if rc != 0:
         raise ValueError("ciphertext uses a bootstrapping key that was not provided")
     return out

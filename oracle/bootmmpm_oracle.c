@@ -573,6 +573,161 @@ int orc_bootstrap_arbitrary(const orc_params *p, uint32_t m, uint32_t t, u64 q, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* General transitive generators (Section 3: Theorem 1, Lemma 3, Lemma 4,   */
+/* Example 2).                                                              */
+/*                                                                          */
+/* A generator is P(1) = A = (x^{u_i} delta_{tau(i), j}), tau(i) = i-1 mod m */
+/* (the form (BP1:form): row 0 holds x^{u_0} in column m-1, row i >= 1      */
+/* holds x^{u_i} in column i-1).  By Theorem 1 the group it generates acts  */
+/* transitively on the monic monomial indicator vectors iff                 */
+/* ord(x^{sum u}) = 2N, i.e. iff sum u is odd.  Example 1's P(1) is         */
+/* u = (1, 0, ..., 0).                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* E_c(i) = sum_{t in [c]} u_{(i - t) mod m}: the exponent of row i of A^c
+ * (Lemma 3, Eq. (Al:res)), whose nonzero entry sits in column (i - c) mod m. */
+static uint64_t gen_exponent(uint32_t m, const uint32_t *u, uint64_t c, uint32_t i)
+{
+    uint64_t S = 0;
+    for (uint32_t k = 0; k < m; k++) S += u[k];
+    uint64_t e = (c / m) * S;
+    for (uint64_t t = 0; t < c % m; t++) e += u[(i + m - (uint32_t)t) % m];
+    return e;
+}
+
+/* out = P(c) * in = A^c * in for an RLWE vector [m][2][N]: row i is
+ * x^{E_c(i)} in_{(i - c) mod m} (Lemma 3). */
+void orc_mmpm_apply_gen(uint32_t N, uint32_t m, u64 Q, const uint32_t *u, uint64_t c,
+                        const u64 *in, u64 *out)
+{
+    for (uint32_t i = 0; i < m; i++) {
+        uint32_t src = (uint32_t)((i + (uint64_t)m - c % m) % m);
+        int64_t e = (int64_t)(gen_exponent(m, u, c, i) % (2ull * N));
+        for (int comp = 0; comp < 2; comp++)
+            monomial_mul(N, Q, e, in + ((size_t)src * 2 + comp) * N, out + ((size_t)i * 2 + comp) * N);
+    }
+}
+
+/* One application of A: row i of the result is x^{u_i} in_{(i - 1) mod m}. */
+void orc_mmpm_step_gen(uint32_t N, uint32_t m, u64 Q, const uint32_t *u, const u64 *in, u64 *out)
+{
+    for (uint32_t i = 0; i < m; i++)
+        for (int comp = 0; comp < 2; comp++)
+            monomial_mul(N, Q, (int64_t)u[i], in + ((size_t)((i + m - 1) % m) * 2 + comp) * N,
+                         out + ((size_t)i * 2 + comp) * N);
+}
+
+/* Test vector of Eq. (equ:test-gene) scaled by floor(Q/t):
+ *   v_0 = sum_{a in [N], b in [m]} f'(-(a m + b)) x^{a S + E_b(b)} e_b,
+ * S = sum u, E_b(b) = u_b + ... + u_1 (the exponent of P(b) e_0, Eq.
+ * (equ:basis-test-gene)); x^N = -1 folds every exponent into [N]. */
+void orc_test_vector_gen(uint32_t N, uint32_t m, uint32_t t, u64 Q, const uint32_t *u,
+                         const uint32_t *lut, u64 *v)
+{
+    uint64_t qp = 2ull * N * m;
+    u64 dq = Q / t;
+    uint64_t S = 0;
+    for (uint32_t k = 0; k < m; k++) S += u[k];
+    memset(v, 0, sizeof(u64) * (size_t)m * N);
+    for (uint32_t b = 0; b < m; b++) {
+        uint64_t Eb = gen_exponent(m, u, b, b);
+        for (uint32_t a = 0; a < N; a++) {
+            uint64_t idx = (uint64_t)a * m + b;
+            uint64_t w = (qp - idx % qp) % qp;
+            u64 val = mul_mod(f_ext(lut, t, qp, w), dq, Q);
+            uint64_t e = ((uint64_t)a * S + Eb) % (2ull * N);
+            size_t pos = (size_t)b * N + (e % N);
+            v[pos] = e < N ? add_mod(v[pos], val, Q) : sub_mod(v[pos], val, Q);
+        }
+    }
+}
+
+/* acc <- acc + g^{-1}(P(-a_k) acc - acc) C_k+ + g^{-1}(P(a_k) acc - acc) C_k-
+ * for the generator u (Eq. (cmux:BP)). */
+static void cmux_gen(const orc_params *p, uint32_t m, const uint32_t *u, uint64_t ak, const u64 *Cp,
+                     const u64 *Cm, u64 *acc, int parallel)
+{
+    uint32_t N = p->N;
+    u64 Q = p->Q;
+    uint64_t qp = 2ull * N * m;
+    size_t vec = (size_t)m * 2 * N;
+    u64 *rot = malloc(sizeof(u64) * vec * 2);
+    u64 *diff = malloc(sizeof(u64) * vec * 2);
+    u64 *prod = malloc(sizeof(u64) * vec * 2);
+    orc_mmpm_apply_gen(N, m, Q, u, (qp - ak % qp) % qp, acc, rot);
+    orc_mmpm_apply_gen(N, m, Q, u, ak % qp, acc, rot + vec);
+    for (size_t i = 0; i < vec; i++) {
+        diff[i] = sub_mod(rot[i], acc[i], Q);
+        diff[vec + i] = sub_mod(rot[vec + i], acc[i], Q);
+    }
+    #pragma omp parallel for schedule(dynamic) if (parallel)
+    for (int task = 0; task < (int)(4 * m); task++) {
+        int col = task & 1, sgn = (task >> 1) / (int)m, r = (task >> 1) % (int)m;
+        const u64 *d = diff + (size_t)sgn * vec + (size_t)r * 2 * N;
+        u64 *o = prod + (size_t)sgn * vec + (size_t)r * 2 * N;
+        external_product_col(p, d, d + N, sgn == 0 ? Cp : Cm, col, o + (size_t)col * N);
+    }
+    for (size_t i = 0; i < vec; i++)
+        acc[i] = add_mod(add_mod(acc[i], prod[i], Q), prod[vec + i], Q);
+    free(rot); free(diff); free(prod);
+}
+
+/* Algorithm 1's phase accumulation with the generator u: ACC = P(b)(0, v_0),
+ * then the CMux of every step; same key and ciphertext conventions as
+ * orc_blind_rotate. */
+int orc_blind_rotate_gen(const orc_params *p, uint32_t m, uint32_t t, const uint32_t *u,
+                         const u64 *bsk, uint32_t n_keys, const uint64_t *ct,
+                         const uint32_t *lut, u64 *acc, int parallel)
+{
+    uint32_t N = p->N, n = p->n, lB = p->l_B;
+    u64 Q = p->Q;
+    uint64_t qp = 2ull * N * m;
+    size_t vec = (size_t)m * 2 * N;
+    size_t rgsw = (size_t)2 * lB * 2 * N;
+    u64 *v = malloc(sizeof(u64) * (size_t)m * N);
+    u64 *init = calloc(vec, sizeof(u64));
+    orc_test_vector_gen(N, m, t, Q, u, lut, v);
+    for (uint32_t r = 0; r < m; r++)
+        memcpy(init + ((size_t)r * 2 + 1) * N, v + (size_t)r * N, sizeof(u64) * N);
+    orc_mmpm_apply_gen(N, m, Q, u, ct[n] % qp, init, acc);
+    for (uint32_t k = 0; k < n; k++) {
+        uint64_t ak = ct[k] % qp;
+        if (k >= n_keys) {
+            if (ak != 0) { free(v); free(init); return -1; }
+            continue;
+        }
+        const u64 *Cp = bsk + (size_t)k * 2 * rgsw;
+        cmux_gen(p, m, u, ak, Cp, Cp + rgsw, acc, parallel);
+    }
+    free(v); free(init);
+    return 0;
+}
+
+/* Algorithm 1 (modulus switches excluded) with a generator per ciphertext:
+ * u holds count * m exponents, ciphertext i using u + i * m. */
+int orc_bootstrap_gen(const orc_params *p, uint32_t m, uint32_t t, const uint32_t *u,
+                      const u64 *bsk, uint32_t n_keys, const u64 *ksk, const uint64_t *ct_in,
+                      const uint32_t *luts, size_t count, u64 *ct_out)
+{
+    uint32_t N = p->N, n = p->n;
+    int bad = 0;
+    int inner = count == 1;
+    #pragma omp parallel for schedule(dynamic) if (!inner) reduction(|:bad)
+    for (long ii = 0; ii < (long)count; ii++) {
+        size_t i = (size_t)ii;
+        u64 *acc = malloc(sizeof(u64) * (size_t)m * 2 * N);
+        u64 *lwe = malloc(sizeof(u64) * (N + 1));
+        if (orc_blind_rotate_gen(p, m, t, u + i * m, bsk, n_keys, ct_in + i * (n + 1),
+                                 luts + i * t, acc, inner) != 0)
+            bad = 1;
+        orc_sample_extract(N, p->Q, acc, acc + N, lwe);
+        orc_key_switch(p, lwe, ksk, ct_out + i * (n + 1));
+        free(acc); free(lwe);
+    }
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Seeded randomness: keys and ciphertexts drawn from a seed                */
 /* (Algorithm 1 REQUIRE block: s, z, the keys' masks and errors; Section 2, */
 /* (8): encryption masks and errors).  The paper does not fix a generator;  */
