@@ -199,6 +199,28 @@ bm_status bm_bootstrap_batch(const bm_eval_key *const *keys, uint32_t n_keys,
                              uint64_t *d_ct_out, void *d_ws, size_t ws_bytes,
                              void *stream);
 
+/* Algorithm 1 with other transitive generators (Theorem 1; Lemma 3;
+ * Example 2, Eq. (equ:test-gene)).  A generator is given by m exponents
+ * u_0..u_{m-1} in [0, 2N): P(1) = (x^{u_i} delta_{i-1 mod m, j}), i.e. row 0
+ * holds x^{u_0} in column m-1 and row i >= 1 holds x^{u_i} in column i-1.
+ * By Theorem 1 it acts transitively on the monic monomial indicator vectors
+ * (so that the test vector has the look-up property) iff sum u is odd;
+ * other generators are refused (BM_EINVAL).  Then P(c) = P(1)^c has row i
+ * equal to x^{E_c(i)} e_{(i-c) mod m}, E_c(i) = sum_{t in [c]} u_{(i-t) mod m}
+ * (Lemma 3), and the test vector is v_0 = sum_{a in [N], b in [m]}
+ * f'(-(a m + b)) x^{a S + E_b(b)} e_b with S = sum u.
+ * gens: host array of exponents; job i uses gens[gen_off[i] .. + m_i), or
+ * Example 1's generator u = (1, 0, ..., 0) when gen_off[i] ==
+ * BM_GEN_EXAMPLE1 (bm_bootstrap_batch uses it for every job).  Otherwise as
+ * bm_bootstrap_batch, with a workspace of bm_workspace_bytes_gen(...) bytes. */
+#define BM_GEN_EXAMPLE1 (~(uint64_t)0)
+size_t bm_workspace_bytes_gen(const bm_eval_key *const *keys, uint32_t n_keys, const bm_job *jobs,
+                              uint32_t count, const uint32_t *gens, const uint64_t *gen_off);
+bm_status bm_bootstrap_batch_gen(const bm_eval_key *const *keys, uint32_t n_keys, const bm_job *jobs,
+                                 uint32_t count, const uint32_t *gens, const uint64_t *gen_off,
+                                 const uint64_t *d_ct_in, const uint32_t *d_lut, uint64_t *d_ct_out,
+                                 void *d_ws, size_t ws_bytes, void *stream);
+
 /* Same computation with host buffers: copies the inputs (h_ct_in, h_lut) to
  * the workspace, bootstraps, copies the outputs back to h_ct_out, and
  * synchronises the stream.  The workspace must hold

@@ -29,7 +29,8 @@ SYMBOLS = ["bm_keygen", "bm_free_secret_key", "bm_free_eval_key", "bm_eval_key_b
            "bm_modmul_peak", "bm_status_str", "bm_bootstrap_batch_noalloc",
            "bm_batch_create", "bm_batch_run", "bm_batch_free", "bm_mod_switch",
            "bm_arbitrary_workspace_bytes", "bm_bootstrap_arbitrary", "bm_secret_key_seeded",
-           "bm_keygen_seeded", "bm_secret_key_get", "bm_encrypt_seeded"]
+           "bm_keygen_seeded", "bm_secret_key_get", "bm_encrypt_seeded", "bm_workspace_bytes_gen",
+           "bm_bootstrap_batch_gen"]
 
 BATCH_PERSISTENT = 1
 BATCH_GRAPH = 2
@@ -130,6 +131,10 @@ def load(build_if_needed: bool = True) -> C.CDLL:
     L.bm_secret_key_get.restype = i32
     L.bm_encrypt_seeded.argtypes = [vp, C.c_uint64, u32, vp, sz, C.c_double, C.c_uint64, vp]
     L.bm_encrypt_seeded.restype = i32
+    L.bm_workspace_bytes_gen.argtypes = [vp, u32, vp, u32, vp, vp]
+    L.bm_workspace_bytes_gen.restype = sz
+    L.bm_bootstrap_batch_gen.argtypes = [vp, u32, vp, u32, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.bm_bootstrap_batch_gen.restype = i32
     L.bm_status_str.argtypes = [i32]
     L.bm_status_str.restype = C.c_char_p
     _lib = L
@@ -298,6 +303,35 @@ def bm_bootstrap_batch(keys, jobs: np.ndarray, d_ct_in, d_lut, d_ct_out, d_ws, s
     _check(load().bm_bootstrap_batch(karr, nk, _ptr(jobs), len(jobs), _ptr(d_ct_in), _ptr(d_lut),
                                      _ptr(d_ct_out), _ptr(d_ws), d_ws.numel() * d_ws.element_size(),
                                      _stream(stream)), "bm_bootstrap_batch")
+
+
+GEN_EXAMPLE1 = (1 << 64) - 1
+
+
+def _gens(gens, gen_off):
+    gens = np.ascontiguousarray(gens, np.uint32)
+    gen_off = np.ascontiguousarray(gen_off, np.uint64)
+    return gens, gen_off
+
+
+def bm_workspace_bytes_gen(keys, jobs: np.ndarray, gens, gen_off) -> int:
+    karr, nk = _keys(keys)
+    jobs = np.ascontiguousarray(jobs, JOB_DTYPE)
+    gens, gen_off = _gens(gens, gen_off)
+    return int(load().bm_workspace_bytes_gen(karr, nk, _ptr(jobs), len(jobs), _ptr(gens), _ptr(gen_off)))
+
+
+def bm_bootstrap_batch_gen(keys, jobs: np.ndarray, gens, gen_off, d_ct_in, d_lut, d_ct_out, d_ws, stream=None):
+    """bm_bootstrap_batch with a transitive generator per job (Theorem 1):
+    job i uses the exponents gens[gen_off[i]:gen_off[i] + m], or Example 1's
+    P(1) where gen_off[i] == GEN_EXAMPLE1."""
+    karr, nk = _keys(keys)
+    jobs = np.ascontiguousarray(jobs, JOB_DTYPE)
+    gens, gen_off = _gens(gens, gen_off)
+    _check(load().bm_bootstrap_batch_gen(karr, nk, _ptr(jobs), len(jobs), _ptr(gens), _ptr(gen_off),
+                                         _ptr(d_ct_in), _ptr(d_lut), _ptr(d_ct_out), _ptr(d_ws),
+                                         d_ws.numel() * d_ws.element_size(), _stream(stream)),
+           "bm_bootstrap_batch_gen")
 
 
 def bm_bootstrap_batch_noalloc(keys, jobs: np.ndarray, d_ct_in, d_lut, d_ct_out, d_status=None,

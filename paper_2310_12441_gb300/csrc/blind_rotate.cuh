@@ -63,15 +63,42 @@ static __device__ bool lut_is_negacyclic(const u32 *__restrict__ lut, u32 t) {
     return ok;
 }
 
-// ACC <- P(b) (0, v_test floor(Q/t)), v_test of Eq. (equ:test-use):
-// row i, coefficient a of v_test is f'(-(a m + i) mod 2Nm), with the
-// negacyclic extension f'(u) = f(floor((u t + Nm) / 2Nm) mod t).
+// Row i of P(c) = A^c (Lemma 3, Eq. (Al:res)): its source row (i - c) mod m
+// and monomial exponent E_c(i) mod 2N, c = a m + b.
+//  - gS == 0, the generator of Example 1: E_c(i) = a + [i < b] (Eq. (ex1:BPc));
+//  - otherwise a generator A = (x^{u_i} delta_{i-1 mod m, j}) of Theorem 1 with
+//    S = sum u = gS and pre[k] = u_0 + ... + u_{k-1} (all mod 2N):
+//    E_c(i) = a S + sum_{t in [b]} u_{(i - t) mod m}.
+__device__ __forceinline__ void mmpm_row(u32 c, u32 i, u32 m, u32 twoN, u32 gS, const u32 *pre, u32 &src,
+                                         u32 &e) {
+    const u32 a = c / m, b = c % m;
+    src = i >= b ? i - b : i + m - b;
+    if (!gS) {
+        e = i >= b ? a : a + 1;
+        if (e >= twoN) e -= twoN;
+        return;
+    }
+    u32 w = 0;
+    if (b != 0) w = b <= i + 1 ? pre[i + 1] + twoN - pre[i + 1 - b] : pre[i + 1] + pre[m] + twoN - pre[m + i + 1 - b];
+    e = (u32)(((u64)a * gS + w) % twoN);
+}
+
+// ACC <- P(b) (0, v_test floor(Q/t)) with the negacyclic extension
+// f'(u) = f(floor((u t + Nm) / 2Nm) mod t).
+//  - Generator of Example 1, v_test of Eq. (equ:test-use): coefficient j of
+//    row s is f'(-(j m + s) mod 2Nm).
+//  - General generator, v_test of Eq. (equ:test-gene): the term
+//    f'(-(a m + s)) x^{a S + E_s} of row s (a in [N], E_s = u_1 + ... + u_s)
+//    lands on coefficient j = (a S + E_s) mod N, negated when
+//    (a S + E_s) mod 2N >= N; so coefficient j holds the term
+//    a = (j - E_s) S^-1 mod N.
 // Rows i with i mod rows_step == row0 only (the rows of one block of a cluster).
 static __device__ void acc_init(u64 *__restrict__ acc, const u32 *__restrict__ lut, u64 b, u32 m, u32 t,
-                         u32 N, u64 Q, u32 row0 = 0, u32 rows_step = 1) {
+                                u32 N, u64 Q, u32 gS, u32 gSinv, const u32 *pre, u32 row0 = 0,
+                                u32 rows_step = 1) {
     const u64 qp = 2ull * N * m;
     const u64 dq = Q / t;
-    const u32 ea = (u32)(b / m), bb = (u32)(b % m);
+    const u32 twoN = 2 * N;
     for (u32 idx = threadIdx.x; idx < m * 2 * N; idx += blockDim.x) {
         const u32 c = idx % N;
         const u32 comp = (idx / N) & 1;
@@ -79,14 +106,19 @@ static __device__ void acc_init(u64 *__restrict__ acc, const u32 *__restrict__ l
         if (i % rows_step != row0) continue;
         u64 val = 0;
         if (comp == 1) {
-            const u32 src = i >= bb ? i - bb : i + m - bb;
-            u32 e = i >= bb ? ea : ea + 1;
-            if (e >= 2 * N) e -= 2 * N;
-            u32 j = c + 2 * N - e;
-            if (j >= 2 * N) j -= 2 * N;
-            const bool neg = j >= N;
+            u32 src, e;
+            mmpm_row((u32)(b % qp), i, m, twoN, gS, pre, src, e);
+            u32 j = c + twoN - e;
+            if (j >= twoN) j -= twoN;
+            bool neg = j >= N;
             if (neg) j -= N;
-            const u64 w = ((u64)j * m + src) % qp;
+            u32 a = j;
+            if (gS) {
+                const u32 Es = pre[src + 1] + twoN - pre[1];          // u_1 + ... + u_s (mod 2N)
+                a = (u32)(((u64)((j + twoN - Es % twoN) % N) * gSinv) % N);
+                if (((u64)a * gS + Es) % twoN >= N) neg = !neg;
+            }
+            const u64 w = ((u64)a * m + src) % qp;
             const u64 u = (qp - w) % qp;
             const u32 fi = (u32)(((u * t + qp / 2) / qp) % t);
             const u64 v = (u64)lut[fi] * dq;     // < t * floor(Q/t) <= Q
@@ -183,7 +215,8 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
             if ((idx / (2 * N)) % m % csize == crank) acc0[idx] = 0;
         return;
     }
-    acc_init(acc0, lut, ct[n] % qp, m, t, N, Q, crank, csize);
+    const u32 *gpre = J.gS ? status + J.gpre : nullptr;
+    acc_init(acc0, lut, ct[n] % qp, m, t, N, Q, J.gS, J.gSinv, gpre, crank, csize);
     // forward twiddle pairs to shared memory (read by every transform), in
     // the transposed order of ntr::twiddle_slot
     u64 *tws = sm + (C::REGIONS + C::DBYTES) / 8;
@@ -239,10 +272,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 for (int sg = 0; sg < 2; sg++) {
                     const u32 r = r0 + g;
                     const u32 cv = sg == 0 ? (ak ? qp - ak : 0u) : ak;
-                    const u32 ea = cv / m, bb = cv % m;
-                    rsrc[g][sg] = r >= bb ? r - bb : r + m - bb;
-                    const u32 e = r >= bb ? ea : ea + 1;
-                    rexp[g][sg] = e >= 2 * N ? e - 2 * N : e;
+                    mmpm_row(cv, r < m ? r : 0, m, 2 * N, J.gS, gpre, rsrc[g][sg], rexp[g][sg]);
                 }
             if constexpr (C::DSM) {
                 // D_(row, sign, comp) = P(c) ACC - ACC: coefficient idx of

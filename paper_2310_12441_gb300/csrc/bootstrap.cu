@@ -233,10 +233,45 @@ namespace {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// A run of plan jobs [first, last) with one ring degree and variant, run by
+// one persistent kernel.
+struct ClassRange {
+    uint32_t first, last;
+    u32 N, variant;
+};
+
 struct Plan {
     size_t jobs_off, acc_off_bytes, total;
     std::vector<DevJob> dj;
+    std::vector<ClassRange> classes;   // persistent classes (order_by_cost plans)
+    std::vector<u32> gen;     // prefix sums of the jobs' generators, uploaded after the job table
 };
+
+// The generator exponents of job i: gens + gen_off[i] (m words), or none
+// (gens == nullptr or gen_off[i] == BM_GEN_EXAMPLE1) for Example 1's P(1).
+const uint32_t *job_gen(const uint32_t *gens, const uint64_t *gen_off, uint32_t i) {
+    if (!gens || !gen_off || gen_off[i] == BM_GEN_EXAMPLE1) return nullptr;
+    return gens + gen_off[i];
+}
+
+// Theorem 1: the action is transitive iff ord(x^{sum u}) = 2N, i.e. sum u odd.
+bm_status validate_gens(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t count,
+                        const uint32_t *gens, const uint64_t *gen_off) {
+    if (!gens) return BM_OK;
+    if (!gen_off) return BM_EINVAL;
+    for (uint32_t i = 0; i < count; i++) {
+        const uint32_t *u = job_gen(gens, gen_off, i);
+        if (!u) continue;
+        const u32 twoN = 2 * keys[jobs[i].key]->p.N;
+        u64 S = 0;
+        for (u32 k = 0; k < jobs[i].m; k++) {
+            if (u[k] >= twoN) return BM_EINVAL;
+            S += u[k];
+        }
+        if (!(S & 1)) return BM_EINVAL;
+    }
+    return BM_OK;
+}
 
 bm_status validate_jobs(const bm_eval_key *const *keys, uint32_t n_keys, const bm_job *jobs,
                         uint32_t count, int *device) {
@@ -267,11 +302,20 @@ double job_cost(const DevJob &d) {
 // offsets): by ring degree and variant for one-block-per-job launches, or,
 // with order_by_cost, longest first for the persistent kernel.
 bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t count, Plan &pl,
-                    bool order_by_cost = false) {
+                    bool order_by_cost = false, const uint32_t *gens = nullptr,
+                    const uint64_t *gen_off = nullptr) {
     pl.jobs_off = BM_WS_HEADER;
-    size_t off = align_up(pl.jobs_off + sizeof(DevJob) * (size_t)count, 256);
+    // prefix sums of the generators right after the job table (one upload)
+    const size_t gen_base = pl.jobs_off + sizeof(DevJob) * (size_t)count;   // bytes, 8-aligned
+    pl.gen.clear();
+    for (uint32_t i = 0; i < count; i++) {
+        const uint32_t *u = job_gen(gens, gen_off, i);
+        if (u) pl.gen.resize(pl.gen.size() + jobs[i].m + 1);
+    }
+    size_t off = align_up(gen_base + 4 * pl.gen.size(), 256);
     pl.acc_off_bytes = off;
     pl.dj.resize(count);
+    size_t gpos = 0;
     size_t acc_words = 0;
     for (uint32_t i = 0; i < count; i++) {
         const bm_eval_key *k = keys[jobs[i].key];
@@ -288,17 +332,65 @@ bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t
         d.variant = choose_variant(k->p);
         limb_plan(k->p, d.variant, d.lbits, d.fold_each);   // lbits as in the key's BSK
         d.pad = 0;
+        d.gS = d.gSinv = 0;
+        d.gpre = 0;
+        if (const uint32_t *u = job_gen(gens, gen_off, i)) {
+            const u32 twoN = 2 * k->p.N, m = jobs[i].m;
+            u32 *pre = pl.gen.data() + gpos;
+            pre[0] = 0;
+            for (u32 q = 0; q < m; q++) pre[q + 1] = (pre[q] + u[q]) % twoN;
+            d.gS = pre[m];
+            u32 inv = 1;   // S^-1 mod 2N (S odd; 2N a power of two): Newton's iteration
+            for (int it = 0; it < 6; it++) inv = inv * (2u - d.gS * inv);
+            d.gSinv = inv % twoN;
+            d.gpre = (gen_base + 4 * gpos) / 4;
+            gpos += m + 1;
+        }
         acc_words += 3ull * 2 * jobs[i].m * k->p.N;
     }
+    pl.classes.clear();
     if (order_by_cost) {
-        // jobs of ring degree 1024..4096 first (the persistent kernel's share),
-        // longest first; the rest grouped by degree and variant
-        std::stable_sort(pl.dj.begin(), pl.dj.end(), [](const DevJob &a, const DevJob &b) {
-            const bool pa = a.N >= 1024 && a.N <= 4096, pb = b.N >= 1024 && b.N <= 4096;
+        // jobs of ring degree 1024..4096 first (the persistent kernels'
+        // share), grouped into classes of equal degree and variant, the class
+        // with the longest job first and every class longest job first; the
+        // rest grouped by degree and variant
+        auto eligible = [](const DevJob &d) { return d.N >= 1024 && d.N <= 4096; };
+        auto key = [](const DevJob &d) { return ((u64)d.N << 32) | d.variant; };
+        std::vector<std::pair<u64, double>> top;   // class key -> its longest job
+        for (const DevJob &d : pl.dj) {
+            if (!eligible(d)) continue;
+            bool found = false;
+            for (auto &kv : top)
+                if (kv.first == key(d)) {
+                    kv.second = std::max(kv.second, job_cost(d));
+                    found = true;
+                }
+            if (!found) top.push_back({key(d), job_cost(d)});
+        }
+        auto rank = [&](const DevJob &d) {
+            double c = 0;
+            for (auto &kv : top)
+                if (kv.first == key(d)) c = kv.second;
+            return c;
+        };
+        std::stable_sort(pl.dj.begin(), pl.dj.end(), [&](const DevJob &a, const DevJob &b) {
+            const bool pa = eligible(a), pb = eligible(b);
             if (pa != pb) return pa;
-            if (pa) return job_cost(a) > job_cost(b);
+            if (pa) {
+                if (key(a) != key(b)) {
+                    const double ra = rank(a), rb = rank(b);
+                    return ra != rb ? ra > rb : key(a) < key(b);
+                }
+                return job_cost(a) > job_cost(b);
+            }
             return a.N != b.N ? a.N < b.N : a.variant < b.variant;
         });
+        for (uint32_t i = 0; i < count && eligible(pl.dj[i]); i++) {
+            if (pl.classes.empty() || key(pl.dj[i]) != key(pl.dj[pl.classes.back().first]))
+                pl.classes.push_back({i, i + 1, pl.dj[i].N, pl.dj[i].variant});
+            else
+                pl.classes.back().last = i + 1;
+        }
     } else {
         // one launch per run of equal degree and variant: group them
         std::stable_sort(pl.dj.begin(), pl.dj.end(), [](const DevJob &a, const DevJob &b) {
@@ -476,13 +568,17 @@ bm_status run_groups(const Plan &pl, uint32_t first, uint32_t last, u32 steps, c
     return BM_OK;
 }
 
-// Number of leading plan jobs that the persistent kernel handles (ring
+// Number of leading plan jobs that the persistent kernels handle (ring
 // degree 1024..4096); make_plan(order_by_cost) puts them first.
 uint32_t persistent_prefix(const Plan &pl) {
-    uint32_t n = 0;
-    while (n < pl.dj.size() && pl.dj[n].N >= 1024 && pl.dj[n].N <= 4096) n++;
-    return n;
+    return pl.classes.empty() ? 0 : pl.classes.back().last;
 }
+
+// Side streams and events that run persistent classes concurrently.
+struct Fork {
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev;      // [0] fork, [1 + c] join of side stream c
+};
 
 struct KsShape {
     u32 threads;
@@ -506,15 +602,28 @@ constexpr u32 kMaxCluster = 8;
 
 bm_status launch_all(const Plan &pl, uint32_t n_persistent, const KsShape &ks, int device, u32 steps, bool do_ks,
                      const uint64_t *d_ct_in, const uint32_t *d_lut, uint64_t *d_out, char *ws,
-                     cudaStream_t st, u32 max_cluster = kMaxCluster) {
+                     cudaStream_t st, u32 max_cluster = kMaxCluster, const Fork *fork = nullptr) {
     const uint32_t count = (uint32_t)pl.dj.size();
     const DevJob *d_jobs = (const DevJob *)(ws + pl.jobs_off);
     u64 *ws_acc = (u64 *)(ws + pl.acc_off_bytes);
     bm_status s;
     if (n_persistent) {
-        s = bm_launch_persistent_br(d_jobs, n_persistent, steps, d_ct_in, d_lut, ws_acc, (u32 *)ws,
-                                    (u32 *)ws + BM_WS_COUNTER_WORD, device, st);
-        if (s != BM_OK) return s;
+        // class 0 (the longest jobs) on `st`, the others on side streams
+        // forked from it, so each later class fills SMs as the earlier ones
+        // run out of jobs; all join back into `st` before the key switch
+        const size_t nc = pl.classes.size();
+        if (nc > 1) BM_CUDA_TRY(cudaEventRecord(fork->ev[0], st));
+        for (size_t c = 0; c < nc; c++) {
+            const ClassRange &cr = pl.classes[c];
+            cudaStream_t cs = c == 0 ? st : fork->side[c - 1];
+            if (c > 0) BM_CUDA_TRY(cudaStreamWaitEvent(cs, fork->ev[0], 0));
+            s = bm_launch_persistent_class(cr.N, cr.variant, d_jobs + cr.first, cr.last - cr.first, steps, d_ct_in,
+                                           d_lut, ws_acc, (u32 *)ws, (u32 *)ws + BM_WS_COUNTER_WORD + c, device,
+                                           false, cs);
+            if (s != BM_OK) return s;
+            if (c > 0) BM_CUDA_TRY(cudaEventRecord(fork->ev[c], cs));
+        }
+        for (size_t c = 1; c < nc; c++) BM_CUDA_TRY(cudaStreamWaitEvent(st, fork->ev[c], 0));
     }
     if ((s = run_groups(pl, n_persistent, count, steps, d_ct_in, d_lut, ws, st, false, max_cluster)) != BM_OK)
         return s;
@@ -531,6 +640,9 @@ bm_status upload_plan(const Plan &pl, char *ws, cudaStream_t st) {
     if (!pl.dj.empty())
         BM_CUDA_TRY(cudaMemcpyAsync(ws + pl.jobs_off, pl.dj.data(), sizeof(DevJob) * pl.dj.size(),
                                     cudaMemcpyHostToDevice, st));
+    if (!pl.gen.empty())
+        BM_CUDA_TRY(cudaMemcpyAsync(ws + pl.jobs_off + sizeof(DevJob) * pl.dj.size(), pl.gen.data(),
+                                    4 * pl.gen.size(), cudaMemcpyHostToDevice, st));
     return BM_OK;
 }
 
@@ -561,14 +673,16 @@ extern "C" size_t bm_workspace_bytes(const bm_eval_key *const *keys, uint32_t n_
 static bm_status bootstrap_impl(const bm_eval_key *const *keys, uint32_t n_keys, const bm_job *jobs,
                                 uint32_t count, u32 steps, bool do_ks, const uint64_t *d_ct_in,
                                 const uint32_t *d_lut, uint64_t *d_out, void *d_ws, size_t ws_bytes,
-                                void *stream) {
+                                void *stream, const uint32_t *gens = nullptr,
+                                const uint64_t *gen_off = nullptr) {
     int dev = 0;
     bm_status s = validate_jobs(keys, n_keys, jobs, count, &dev);
     if (s != BM_OK) return s;
+    if ((s = validate_gens(keys, jobs, count, gens, gen_off)) != BM_OK) return s;
     if (!d_ws || ((uintptr_t)d_ws & 255)) return BM_EINVAL;
     if (count && (!d_ct_in || !d_lut || !d_out)) return BM_EINVAL;
     Plan pl;
-    make_plan(keys, jobs, count, pl);
+    make_plan(keys, jobs, count, pl, false, gens, gen_off);
     if (ws_bytes < pl.total) return BM_EWORKSPACE;
     if (count == 0) return BM_OK;
     DeviceGuard g(dev);
@@ -583,6 +697,24 @@ extern "C" bm_status bm_bootstrap_batch(const bm_eval_key *const *keys, uint32_t
                                         uint64_t *d_ct_out, void *d_ws, size_t ws_bytes, void *stream) {
     return bootstrap_impl(keys, n_keys, jobs, count, 0xffffffffu, true, d_ct_in, d_lut, d_ct_out, d_ws,
                           ws_bytes, stream);
+}
+
+extern "C" size_t bm_workspace_bytes_gen(const bm_eval_key *const *keys, uint32_t n_keys, const bm_job *jobs,
+                                         uint32_t count, const uint32_t *gens, const uint64_t *gen_off) {
+    int dev = 0;
+    if (validate_jobs(keys, n_keys, jobs, count, &dev) != BM_OK) return 0;
+    if (validate_gens(keys, jobs, count, gens, gen_off) != BM_OK) return 0;
+    Plan pl;
+    make_plan(keys, jobs, count, pl, false, gens, gen_off);
+    return pl.total;
+}
+
+extern "C" bm_status bm_bootstrap_batch_gen(const bm_eval_key *const *keys, uint32_t n_keys, const bm_job *jobs,
+                                            uint32_t count, const uint32_t *gens, const uint64_t *gen_off,
+                                            const uint64_t *d_ct_in, const uint32_t *d_lut, uint64_t *d_ct_out,
+                                            void *d_ws, size_t ws_bytes, void *stream) {
+    return bootstrap_impl(keys, n_keys, jobs, count, 0xffffffffu, true, d_ct_in, d_lut, d_ct_out, d_ws,
+                          ws_bytes, stream, gens, gen_off);
 }
 
 extern "C" bm_status bm_blind_rotate(const bm_eval_key *const *keys, uint32_t n_keys, const bm_job *jobs,
@@ -805,10 +937,13 @@ extern "C" bm_status bm_modmul_peak(int device, uint32_t iters, double *rate) {
 // Reusable batches: the plan is built and uploaded once; runs only launch.
 // ---------------------------------------------------------------------------
 
+extern "C" void bm_batch_free(bm_batch *b);
+
 struct bm_batch {
     int device;
     uint32_t flags, n_persistent;
     Plan pl;
+    Fork fork;
     KsShape ks;
     const uint64_t *d_ct_in;
     const uint32_t *d_lut;
@@ -851,9 +986,23 @@ extern "C" bm_status bm_batch_create(const bm_eval_key *const *keys, uint32_t n_
     if (e == cudaSuccess && run_groups(b->pl, b->n_persistent, count, 0, nullptr, nullptr, b->ws, nullptr,
                                        true, b->max_cluster()) != BM_OK)
         e = cudaErrorUnknown;
-    if (e == cudaSuccess && b->n_persistent && bm_prepare_persistent_br(dev) != BM_OK) e = cudaErrorUnknown;
+    for (const ClassRange &cr : b->pl.classes) {
+        if (e == cudaSuccess && bm_launch_persistent_class(cr.N, cr.variant, nullptr, 0, 0, nullptr, nullptr, nullptr,
+                                                           nullptr, nullptr, dev, true, nullptr) != BM_OK)
+            e = cudaErrorUnknown;
+    }
+    if (b->pl.classes.size() > BM_MAX_CLASSES) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess && b->pl.classes.size() > 1) {
+        const size_t nc = b->pl.classes.size();
+        b->fork.side.resize(nc - 1, nullptr);
+        b->fork.ev.resize(nc, nullptr);
+        for (auto &sd : b->fork.side)
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sd, cudaStreamNonBlocking);
+        for (auto &ev : b->fork.ev)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
-        delete b;
+        bm_batch_free(b);
         return BM_ECUDA;
     }
     *out = b;
@@ -866,13 +1015,13 @@ extern "C" bm_status bm_batch_run(bm_batch *b, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (!(b->flags & BM_BATCH_GRAPH))
         return launch_all(b->pl, b->n_persistent, b->ks, b->device, 0xffffffffu, true, b->d_ct_in, b->d_lut,
-                          b->d_out, b->ws, st, b->max_cluster());
+                          b->d_out, b->ws, st, b->max_cluster(), &b->fork);
     if (!st) return BM_EINVAL;   // the legacy default stream cannot be captured
     if (!b->exec) {
         cudaGraph_t graph = nullptr;
         BM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         bm_status s = launch_all(b->pl, b->n_persistent, b->ks, b->device, 0xffffffffu, true, b->d_ct_in,
-                                 b->d_lut, b->d_out, b->ws, st, b->max_cluster());
+                                 b->d_lut, b->d_out, b->ws, st, b->max_cluster(), &b->fork);
         cudaError_t e = cudaStreamEndCapture(st, &graph);
         if (s != BM_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -893,6 +1042,10 @@ extern "C" bm_status bm_batch_run(bm_batch *b, void *stream) {
 extern "C" void bm_batch_free(bm_batch *b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaStream_t sd : b->fork.side)
+        if (sd) cudaStreamDestroy(sd);
+    for (cudaEvent_t ev : b->fork.ev)
+        if (ev) cudaEventDestroy(ev);
     delete b;
 }
 

@@ -38,7 +38,11 @@ struct DevJob {
     u32 variant;       // arithmetic variant of the key's modulus (BR_V_* flags)
     u32 lbits;         // Karatsuba limb width (see limb_plan on the host)
     u32 fold_each;     // 1: a batch's limb products may exceed 64 bits, fold per combo
+    u32 gS;            // generator: 0 for P(1) of Example 1, else S = sum u mod 2N (odd)
+    u32 gSinv;         // S^-1 mod 2N
     u32 pad;
+    u64 gpre;          // u32 offset from the workspace start of the prefix sums
+                       // pre[k] = (u_0 + ... + u_{k-1}) mod 2N, k in [0, m] (gS != 0)
 };
 
 // Arithmetic variants of the blind rotation, chosen per key set on the host.
@@ -85,8 +89,9 @@ inline void limb_plan(const bm_key_params &p, u32 variant, u32 &lbits, u32 &fold
     fold_each = (u128)cpb * sx * sb >= ((u128)1 << 64);
 }
 
-// Workspace header: [0] status word, [1] job counter of the persistent kernel.
+// Workspace header: [0] status word, [1 + c] job counter of persistent class c.
 #define BM_WS_COUNTER_WORD 1
+#define BM_MAX_CLASSES 15
 
 // Host-side evaluation key.
 struct bm_eval_key {
@@ -118,13 +123,13 @@ struct bm_secret_key {
 // Workspace header: the device status word sits at offset 0.
 #define BM_WS_HEADER 256
 
-// Persistent blind rotation of all jobs (persistent.cu): one block per SM
-// pulls jobs from a counter in the workspace header.
-bm_status bm_launch_persistent_br(const DevJob *d_jobs, uint32_t count, uint32_t steps,
-                                  const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc,
-                                  u32 *status, u32 *counter, int device, cudaStream_t st);
-size_t bm_persistent_smem();
-bm_status bm_prepare_persistent_br(int device);
+// Persistent blind rotation of one class of jobs (same ring degree 1024..4096
+// and arithmetic variant; persistent.cu): one block per SM pulls the class's
+// jobs from `counter` (a word of the workspace header).  dry: only set the
+// kernel's attributes (before a stream capture).
+bm_status bm_launch_persistent_class(u32 N, u32 variant, const DevJob *d_jobs, uint32_t count, uint32_t steps,
+                                     const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status,
+                                     u32 *counter, int device, bool dry, cudaStream_t st);
 
 // Host helpers (keygen.cu)
 bm_status bm_check_key_params(const bm_key_params *p);
