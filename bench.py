@@ -505,6 +505,7 @@ def run_extras(args, api, dev, stream, flush, peak):
     from paper_2310_12441_gb300 import workload as wl
     from paper_2310_12441_gb300.params import JobShape
     out = {"workloads": []}
+    stream = torch.cuda.Stream(dev)     # graph capture needs a stream other than the legacy default
     for w2 in (P.LARGE_N2048, P.SINGLEPOLY_N4096):
         out["workloads"].append(run_workload(api, w2, dev, stream, flush, peak))
     # uneven mix: 8192 jobs over six parameter sets, Zipf(1.2) counts
@@ -520,7 +521,7 @@ def run_extras(args, api, dev, stream, flush, peak):
     d_out = torch.zeros(bu.out_words, dtype=torch.int64, device=dev)
     keys = [k.ek for k in ksets]
     ws = api.workspace(api.bm_workspace_bytes(keys, bu.jobs), dev)
-    choice, tune_ms = autotune.tune(ksets, bu.jobs, d_in, d_lut, d_out, ws, stream, use_cache=False)
+    tuned = autotune.tune(ksets, bu.jobs, d_in, d_lut, d_out, ws, stream, use_cache=False)
     modes = {}
     mm = sum(modmuls_per_bootstrap(ksets[int(j["key"])].kp, int(j["m"])) for j in bu.jobs)
     for name, fl in autotune.CANDIDATES.items():
@@ -543,7 +544,9 @@ def run_extras(args, api, dev, stream, flush, peak):
                        "frac_of_modmul_peak": mm / (ms * 1e-3) / peak}
     out["uneven"] = {"workload": "uneven 8192 jobs, sets S1..S6 (m 1..8, N 1024/2048), Zipf 1.2",
                      "counts": {n: int(c) for (n, _, _), c in zip(P.UNEVEN_SETS, counts)},
-                     "autotune": {"choice": choice, "ms": tune_ms}, "modes": modes}
+                     "autotune": tuned, "modes": modes}
+    for N in (1024, 2048, 4096):
+        api.set_kernel_shape(N, api.SHAPE_DEFAULT)
     del d_in, d_lut, d_out, ws, bu
     # served: single requests of the large-plaintext set at fractions of its batch capacity
     cap = out["workloads"][0]["value"]
@@ -660,14 +663,14 @@ def run_suite(args):
         d_lut = api.to_device_u32(bu.luts, dev)
         d_out = torch.zeros(bu.out_words, dtype=torch.int64, device=dev)
         ws = api.workspace(api.bm_workspace_bytes([k.ek for k in ksets], bu.jobs), dev)
-        best, tms = autotune.tune(ksets, bu.jobs, d_in, d_lut, d_out, ws, stream, use_cache=False)
+        tuned = autotune.tune(ksets, bu.jobs, d_in, d_lut, d_out, ws, stream, use_cache=False)
         res = {}
         for name, fl in autotune.CANDIDATES.items():
             ms, bad, _ = _run_batch_rate(api, wl, ksets, bu, stream, flush, flags=fl)
             res[name] = {"bootstraps_per_s": len(bu.jobs) / ms * 1e3, "ms": ms, "decrypt_failures": bad}
         emit({"workload": "uneven 8192 jobs, sets S1..S6, Zipf 1.2",
               "counts": {n: int(c) for (n, _, _), c in zip(P.UNEVEN_SETS, counts)},
-              "autotune_choice": best, "autotune_ms": tms, "modes": res})
+              "autotune": tuned, "modes": res})
     # (4) served stream over the t = 2^13, m = 8, N = 2048 set
     if "served" in args.suite:
         poolsz = 1024

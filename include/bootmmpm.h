@@ -320,6 +320,29 @@ bm_status bm_bootstrap_arbitrary(const bm_eval_key *key, uint32_t m, uint32_t t,
                                  const uint64_t *d_ct_in, uint64_t *d_ct_out,
                                  void *d_ws, size_t ws_bytes, void *stream);
 
+/* Kernel shapes of the blind rotation (the autotuner's candidates; the paper
+ * has no counterpart: they change how the GPU runs Algorithm 1, never a
+ * result bit).  Shape s runs each job on blocks of `threads` threads holding
+ * `radix` coefficients of a polynomial each in the transforms, with
+ * `blocks_per_sm` blocks resident per SM:
+ *   0: radix 16, 512 threads, 1 block/SM     (every ring degree)
+ *   1: radix 8, 1024 threads, 1 block/SM     (N = 1024..4096)
+ *   2: radix 16, 256 threads, 2 blocks/SM    (N = 1024)
+ *   3: radix 8, 512 threads, 2 blocks/SM     (N = 1024)
+ *   4: radix 8, 512 threads, 1 block/SM      (N = 1024, 2048)
+ * Shapes 1..4 are compiled for keys whose Q = c 2^32 + 1; other keys run
+ * shape 0.  bm_kernel_shape_info describes shape s at ring degree N
+ * (BM_EINVAL when it does not fit).  bm_set_kernel_shape selects the shape
+ * that later launches at ring degree N use (BM_SHAPE_DEFAULT: the built-in
+ * choice); reusable batches keep the shapes current at bm_batch_create.
+ * The setting is process-wide. */
+#define BM_NUM_SHAPES 5
+#define BM_SHAPE_DEFAULT 0xffffffffu
+bm_status bm_kernel_shape_info(uint32_t shape, uint32_t N, uint32_t *radix, uint32_t *threads,
+                               uint32_t *blocks_per_sm);
+bm_status bm_set_kernel_shape(uint32_t N, uint32_t shape);
+bm_status bm_get_kernel_shape(uint32_t N, uint32_t *shape);
+
 /* Reads (synchronising `stream`) and clears the device status word of a
  * workspace: BM_OK or the first device-side error recorded. */
 bm_status bm_workspace_status(void *d_ws, void *stream);

@@ -30,7 +30,8 @@ SYMBOLS = ["bm_keygen", "bm_free_secret_key", "bm_free_eval_key", "bm_eval_key_b
            "bm_batch_create", "bm_batch_run", "bm_batch_free", "bm_mod_switch",
            "bm_arbitrary_workspace_bytes", "bm_bootstrap_arbitrary", "bm_secret_key_seeded",
            "bm_keygen_seeded", "bm_secret_key_get", "bm_encrypt_seeded", "bm_workspace_bytes_gen",
-           "bm_bootstrap_batch_gen"]
+           "bm_bootstrap_batch_gen", "bm_kernel_shape_info", "bm_set_kernel_shape",
+           "bm_get_kernel_shape"]
 
 BATCH_PERSISTENT = 1
 BATCH_GRAPH = 2
@@ -135,6 +136,12 @@ def load(build_if_needed: bool = True) -> C.CDLL:
     L.bm_workspace_bytes_gen.restype = sz
     L.bm_bootstrap_batch_gen.argtypes = [vp, u32, vp, u32, vp, vp, vp, vp, vp, vp, sz, vp]
     L.bm_bootstrap_batch_gen.restype = i32
+    L.bm_kernel_shape_info.argtypes = [u32, u32, vp, vp, vp]
+    L.bm_kernel_shape_info.restype = i32
+    L.bm_set_kernel_shape.argtypes = [u32, u32]
+    L.bm_set_kernel_shape.restype = i32
+    L.bm_get_kernel_shape.argtypes = [u32, vp]
+    L.bm_get_kernel_shape.restype = i32
     L.bm_status_str.argtypes = [i32]
     L.bm_status_str.restype = C.c_char_p
     _lib = L
@@ -303,6 +310,30 @@ def bm_bootstrap_batch(keys, jobs: np.ndarray, d_ct_in, d_lut, d_ct_out, d_ws, s
     _check(load().bm_bootstrap_batch(karr, nk, _ptr(jobs), len(jobs), _ptr(d_ct_in), _ptr(d_lut),
                                      _ptr(d_ct_out), _ptr(d_ws), d_ws.numel() * d_ws.element_size(),
                                      _stream(stream)), "bm_bootstrap_batch")
+
+
+NUM_SHAPES = 5
+SHAPE_DEFAULT = 0xFFFFFFFF
+
+
+def kernel_shapes(N: int) -> dict:
+    """{shape: (radix, threads, blocks per SM)} of the shapes that fit ring degree N."""
+    out = {}
+    for sh in range(NUM_SHAPES):
+        r, t, b = C.c_uint32(), C.c_uint32(), C.c_uint32()
+        if load().bm_kernel_shape_info(sh, N, C.byref(r), C.byref(t), C.byref(b)) == BM_OK:
+            out[sh] = (r.value, t.value, b.value)
+    return out
+
+
+def set_kernel_shape(N: int, shape: int) -> None:
+    _check(load().bm_set_kernel_shape(N, shape), "bm_set_kernel_shape")
+
+
+def get_kernel_shape(N: int) -> int:
+    v = C.c_uint32()
+    _check(load().bm_get_kernel_shape(N, C.byref(v)), "bm_get_kernel_shape")
+    return v.value
 
 
 GEN_EXAMPLE1 = (1 << 64) - 1

@@ -1,16 +1,26 @@
-"""Autotuner for the execution of a bootstrapping batch.
+"""Autotuner of bootstrapping batches on one GPU.
 
-Candidates (all bit-identical in their results):
-  * "grouped":    one launch per run of equal ring degree and variant, one
-                  512-thread block per job;
-  * "persistent": one launch for every job of degree 1024..4096, one
-                  512-thread block per SM pulling jobs longest first.
-Both are recorded in a CUDA graph and replayed.  The tuner times each
-candidate on the batch itself and caches the winner in a JSON file keyed by
-the GPU name and the batch composition (ring degree, rows per job, share).
+Two choices, both bit-identical in their results (every candidate computes
+Algorithm 1 exactly; tests/test_gpu_shapes.py checks each against the
+oracle):
+
+  * the kernel shape of each ring degree in the batch (bm_kernel_shape_info:
+    NTT radix 16 or 8, 256 / 512 / 1024 threads per block, one or two blocks
+    per SM), timed on a sample of the batch's jobs of that degree;
+  * the launch mode: "grouped" (one launch per run of equal degree and
+    arithmetic variant, one after the other) or "persistent" (one persistent
+    kernel per such class, the classes running concurrently), timed on the
+    whole batch with the chosen shapes.
+
+Every candidate is recorded in a CUDA graph once and timed over `reps`
+replays (the minimum counts).  The winner is cached in a JSON file keyed by
+the GPU's name, the library's build (hash of libbootmmpm.so) and the batch
+composition (ring degree and rows per job, their shares, batch size bucket),
+and applied with bm_set_kernel_shape.
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 
@@ -18,13 +28,22 @@ import numpy as np
 
 from . import api
 
-CANDIDATES = {"grouped": api.BATCH_GRAPH,
-              "persistent": api.BATCH_GRAPH | api.BATCH_PERSISTENT}
+MODES = {"grouped": api.BATCH_GRAPH,
+         "persistent": api.BATCH_GRAPH | api.BATCH_PERSISTENT}
+# kept for callers that iterate over the launch modes
+CANDIDATES = MODES
 
 
 def cache_path() -> str:
     return os.environ.get("BM_AUTOTUNE_CACHE",
                           os.path.join(os.path.expanduser("~"), ".cache", "bootmmpm", "autotune.json"))
+
+
+def library_hash() -> str:
+    h = hashlib.sha256()
+    with open(api.library_path(), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def signature(keys, jobs: np.ndarray, gpu_name: str) -> str:
@@ -35,7 +54,7 @@ def signature(keys, jobs: np.ndarray, gpu_name: str) -> str:
     total = len(jobs)
     shares = ",".join(f"{k}:{round(v / total, 2)}" for k, v in sorted(comp.items()))
     size = 1 << int(np.log2(max(total, 1)))
-    return f"{gpu_name}|{size}|{shares}"
+    return f"{gpu_name}|{library_hash()}|{size}|{shares}"
 
 
 def _load() -> dict:
@@ -57,17 +76,10 @@ def _store(d: dict) -> None:
         pass
 
 
-def tune(keys, jobs, d_in, d_lut, d_out, ws, stream, reps: int = 1, use_cache: bool = True):
-    """Returns (best candidate name, {name: ms}) for this batch."""
+def _time_batch(keys, jobs, d_in, d_lut, d_out, ws, flags, stream, reps) -> float:
     import torch
-    gpu = torch.cuda.get_device_name(stream.device)
-    sig = signature(keys, jobs, gpu)
-    cache = _load() if use_cache else {}
-    if sig in cache:
-        return cache[sig]["best"], cache[sig]["ms"]
-    times = {}
-    for name, flags in CANDIDATES.items():
-        b = api.Batch([k.ek for k in keys], jobs, d_in, d_lut, d_out, ws, flags)
+    b = api.Batch(keys, jobs, d_in, d_lut, d_out, ws, flags)
+    try:
         b.run(stream)                      # records the graph
         stream.synchronize()
         best = None
@@ -79,10 +91,50 @@ def tune(keys, jobs, d_in, d_lut, d_out, ws, stream, reps: int = 1, use_cache: b
             e1.synchronize()
             ms = e0.elapsed_time(e1)
             best = ms if best is None else min(best, ms)
-        times[name] = best
+        return best
+    finally:
         b.free()
-    winner = min(times, key=times.get)
-    cache[sig] = {"best": winner, "ms": times}
+
+
+def apply(result: dict) -> None:
+    for N, d in result["shapes"].items():
+        api.set_kernel_shape(int(N), int(d["choice"]))
+
+
+def tune(keysets, jobs, d_in, d_lut, d_out, ws, stream, reps: int = 3, use_cache: bool = True,
+         sample: int = 608) -> dict:
+    """Tunes the batch (keysets: objects with .ek and .kp; jobs: api.JOB_DTYPE).
+    Returns {"shapes": {N: {"choice", "ms": {shape: ms}, "runner_up"}},
+    "mode": name, "mode_ms": {name: ms}} and applies the shapes."""
+    import torch
+    keys = [k.ek for k in keysets]
+    gpu = torch.cuda.get_device_name(stream.device)
+    sig = signature(keysets, jobs, gpu)
+    cache = _load() if use_cache else {}
+    if sig in cache:
+        apply(cache[sig])
+        return cache[sig]
+    Ns = np.array([keysets[int(k)].kp.N for k in jobs["key"]])
+    result = {"shapes": {}, "mode": None, "mode_ms": {}}
+    for N in sorted(set(int(x) for x in Ns)):
+        sel = np.nonzero(Ns == N)[0]
+        if len(sel) > sample:                   # an even sample of this degree's jobs
+            sel = sel[np.linspace(0, len(sel) - 1, sample).astype(int)]
+        sub = jobs[sel]
+        times = {}
+        for sh in api.kernel_shapes(N):
+            api.set_kernel_shape(N, sh)
+            times[sh] = _time_batch(keys, sub, d_in, d_lut, d_out, ws, api.BATCH_GRAPH, stream, reps)
+        order = sorted(times, key=times.get)
+        api.set_kernel_shape(N, order[0])
+        result["shapes"][N] = {"choice": order[0], "ms": times, "jobs_timed": int(len(sel)),
+                               "runner_up": order[1] if len(order) > 1 else None,
+                               "desc": {sh: api.kernel_shapes(N)[sh] for sh in times}}
+    for name, flags in MODES.items():
+        result["mode_ms"][name] = _time_batch(keys, jobs, d_in, d_lut, d_out, ws, flags, stream, reps)
+    result["mode"] = min(result["mode_ms"], key=result["mode_ms"].get)
     if use_cache:
+        cache = _load()
+        cache[sig] = json.loads(json.dumps(result))     # JSON keys: ring degrees and shapes as strings
         _store(cache)
-    return winner, times
+    return result

@@ -143,12 +143,25 @@ static __device__ void acc_init(u64 *__restrict__ acc, const u32 *__restrict__ l
 // next ACC buffer.
 // ---------------------------------------------------------------------------
 namespace brk {
-// Block shape for a ring of 2^LOGN coefficients run by THREADS threads.
-template <int LOGN, int THREADS>
+// Shared memory of one block (see Cfg): two exchange regions per polynomial
+// of a batch, the row differences when they fit, the forward twiddle pairs.
+__host__ __device__ constexpr size_t smem_regions(int logn, int threads, int rb) {
+    return 2ull * (threads / ((1 << logn) >> rb)) * (1ull << logn) * 8;
+}
+__host__ __device__ constexpr size_t smem_bytes(int logn, int threads, int rb) {
+    return smem_regions(logn, threads, rb) +
+           (smem_regions(logn, threads, rb) + 4ull * (1ull << logn) * 8 <= 200 * 1024 ? 4ull * (1ull << logn) * 8 : 0) +
+           16ull * (1ull << logn);
+}
+
+// Block shape for a ring of 2^LOGN coefficients run by THREADS threads,
+// each holding 2^RB coefficients of a polynomial in the transforms.
+template <int LOGN, int THREADS, int RB = 4>
 struct Cfg {
     static constexpr int kThreads = THREADS;
     static constexpr int N = 1 << LOGN;
-    static constexpr int T = N / 16;                               // threads per polynomial
+    static constexpr int R = 1 << RB;                              // coefficients per thread
+    static constexpr int T = N / R;                                // threads per polynomial
     static constexpr int P = kThreads / T;                         // polynomials per batch
     static constexpr int PPT = N >= kThreads ? N / kThreads : 1;   // positions per thread
     // rows per batch (every key word the multiply-accumulate loads would serve G
@@ -156,11 +169,16 @@ struct Cfg {
     // registers than the halved key loads save)
     static constexpr int G = 1;
     static constexpr int CPB = P / G;                              // combos per batch
+    // key words a thread holds at once in the multiply-accumulate (fewer
+    // where a 1024-thread block leaves 64 registers per thread)
+    static constexpr int KC = kThreads >= 1024 && CPB > 4 ? 4 : CPB;
     static constexpr size_t REGIONS = 2ull * P * N * 8;            // two regions per polynomial
     static constexpr bool DSM = REGIONS + 4ull * G * N * 8 <= 200 * 1024;   // row differences in smem
     static constexpr size_t DBYTES = DSM ? 4ull * G * N * 8 : 0;
     static constexpr size_t TWBYTES = 16ull * N;                    // forward twiddle pairs
     static constexpr size_t SMEM = REGIONS + DBYTES + TWBYTES;
+    static_assert(G != 1 || SMEM == smem_bytes(LOGN, THREADS, RB), "smem_bytes mirrors Cfg");
+    static_assert(P >= 1 && P * T == THREADS, "whole polynomials per batch");
     static_assert(SMEM <= 227 * 1024 - 1024, "shared memory per block");
 };
 
@@ -183,10 +201,11 @@ struct Cfg {
 // row sums go to the job's sum buffer; after the last row the 2m sums are
 // inverse-transformed (P per batch) and added to the rows of the next ACC
 // buffer.
-template <int LOGN, int THREADS, bool LAZY, bool SMALL0, bool QLOW1>
+template <int LOGN, int THREADS, int RB, bool LAZY, bool SMALL0, bool QLOW1>
 __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u64 *__restrict__ ct_in,
                                        const u32 *__restrict__ luts, u64 *ws, u32 *status, u64 *sm) {
-    using C = Cfg<LOGN, THREADS>;
+    using C = Cfg<LOGN, THREADS, RB>;
+    constexpr int R = C::R;
     constexpr int N = C::N, G = C::G, CPB = C::CPB;
     const KeyDev *K = J.key;
     const u32 lbits = J.lbits;
@@ -221,7 +240,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     // the transposed order of ntr::twiddle_slot
     u64 *tws = sm + (C::REGIONS + C::DBYTES) / 8;
     for (u32 pos = tid; pos < (u32)N; pos += C::kThreads) {
-        const u32 src = ntr::twiddle_slot<LOGN>(pos);
+        const u32 src = ntr::twiddle_slot<LOGN, RB>(pos);
         tws[2 * pos] = __ldg(twp + 2 * src);
         tws[2 * pos + 1] = __ldg(twp + 2 * src + 1);
     }
@@ -320,19 +339,19 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 // --- this thread's digit polynomial, transformed into shared memory
                 const u32 c = c0 + pc, r = r0 + pg;
                 const bool active = pc < (u32)CPB && c < ncomb && r < m;
-                u64 x[16];
+                u64 x[R];
                 if (active) {
                     const u32 pair = c / lB, sh = (c % lB) * log2B;
                     if constexpr (C::DSM) {
                         const u64 *dp = dbuf + ((size_t)pg * 4 + pair) * N;
 #pragma unroll
-                        for (int i = 0; i < 16; i++) x[i] = (u32)(dp[l + C::T * i] >> sh) & Bmask;
+                        for (int i = 0; i < R; i++) x[i] = (u32)(dp[l + C::T * i] >> sh) & Bmask;
                     } else {
                         const u32 sgn = pair >> 1, comp = pair & 1;
                         const u64 *srow = cur + ((size_t)rsrc[pg][sgn] * 2 + comp) * N;
                         const u64 *orow = cur + ((size_t)r * 2 + comp) * N;
 #pragma unroll
-                        for (int i = 0; i < 16; i++) {
+                        for (int i = 0; i < R; i++) {
                             const u32 idx = l + C::T * i;
                             const u64 D = sub_mod(rotated_coeff(srow, idx, rexp[pg][sgn], N, Q, split),
                                                   acc_load(orow + idx, split), Q);
@@ -340,7 +359,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                         }
                     }
                 }
-                u64 *out = ntr::fwd_to_smem<LOGN, LAZY, SMALL0, QLOW1, true>(x, sw, l, active, tws, Q, mq.one_sh, qb);
+                u64 *out = ntr::fwd_to_smem<LOGN, RB, LAZY, SMALL0, QLOW1, true>(x, sw, l, active, tws, Q, mq.one_sh, qb);
                 // regions of the other polynomials of the batch sit at stride N;
                 // polynomial cc G + g holds combo c0 + cc of row r0 + g
                 const u64 *slots = out - (size_t)p * N;
@@ -372,7 +391,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 for (int j = 0; j < C::PPT; j++) {
                     const u32 q = tid + C::kThreads * j;
                     if (q < (u32)N) {
-                        const u32 sq = ntr::swz(q);
+                        const u32 sq = ntr::swz<RB>(q);
                         u64 kh[G][2], kl[G][2], km[G][2];
 #pragma unroll
                         for (int g = 0; g < G; g++) kh[g][0] = kl[g][0] = km[g][0] = kh[g][1] = kl[g][1] = km[g][1] = 0;
@@ -408,6 +427,27 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                                         bnext[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q + C::kThreads);
                                     }
                                 }
+                            } else if constexpr (C::KC < CPB) {
+                                // KC combos' key words at a time (register budget)
+#pragma unroll
+                                for (int k0 = 0; k0 < CPB; k0 += C::KC) {
+                                    u64 kv[C::KC][2];
+#pragma unroll
+                                    for (int cc = 0; cc < C::KC; cc++) {
+                                        kv[cc][0] = __ldg(bsk_c0 + (size_t)(k0 + cc) * 2 * N + q);
+                                        kv[cc][1] = __ldg(bsk_c0 + (size_t)(k0 + cc) * 2 * N + N + q);
+                                    }
+#pragma unroll
+                                    for (int cc = 0; cc < C::KC; cc++)
+#pragma unroll
+                                        for (int g = 0; g < G; g++) {
+                                            if (G == 1 || r0 + g < m) {
+                                                const u64 xv = slots[(size_t)((k0 + cc) * G + g) * N + sq];
+                                                kara(xv, kv[cc][0], kh[g][0], kl[g][0], km[g][0]);
+                                                kara(xv, kv[cc][1], kh[g][1], kl[g][1], km[g][1]);
+                                            }
+                                        }
+                                }
                             } else {
 #pragma unroll
                                 for (int cc = 0; cc < CPB; cc++) {
@@ -415,6 +455,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                                     bv[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q);
                                 }
                             }
+                            if constexpr (PIPE || C::KC == CPB) {
 #pragma unroll
                             for (int cc = 0; cc < CPB; cc++)
 #pragma unroll
@@ -425,6 +466,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                                         kara(xv, bv[cc][1], kh[g][1], kl[g][1], km[g][1]);
                                     }
                                 }
+                            }
                         } else {
                             for (u32 cc = 0; cc < nc; cc++) {
                                 const u64 *brow = bsk_c0 + (size_t)cc * 2 * N + q;
@@ -466,7 +508,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
         const u64 *itw_use = itwp;
         if constexpr (C::DSM) {
             for (u32 pos = tid; pos < (u32)N; pos += C::kThreads) {
-                const u32 src = ntr::inv_twiddle_slot<LOGN>(pos);
+                const u32 src = ntr::inv_twiddle_slot<LOGN, RB>(pos);
                 dbuf[2 * pos] = __ldg(itwp + 2 * src);
                 dbuf[2 * pos + 1] = __ldg(itwp + 2 * src + 1);
             }
@@ -479,22 +521,22 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
             const u32 ui = u0 + p;
             const bool active = ui < 2 * mr;
             const u32 u = 2 * (crank + csize * (ui >> 1)) + (ui & 1);
-            u64 x[16];
+            u64 x[R];
             u64 *in = sw.take();
             if (active) {
                 const u64 *sp = sums + (size_t)u * N;
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
+                for (int i = 0; i < R; i++) {
                     const u32 idx = l + C::T * i;
-                    in[ntr::swz(idx)] = sp[idx];
+                    in[ntr::swz<RB>(idx)] = sp[idx];
                 }
             }
             __syncthreads();
-            ntr::inv_from_smem<LOGN, QLOW1, C::DSM, LAZY && QLOW1>(x, in, sw, l, active, itw_use, Q, mq.one_sh);
+            ntr::inv_from_smem<LOGN, RB, QLOW1, C::DSM, LAZY && QLOW1>(x, in, sw, l, active, itw_use, Q, mq.one_sh);
             if (active) {
                 const size_t base = (size_t)u * N;
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
+                for (int i = 0; i < R; i++) {
                     const size_t o = base + l + C::T * i;
                     nxt[o] = add_mod(cur[o], x[i], Q);
                 }

@@ -24,7 +24,7 @@
 #include "ntt.cuh"
 #include "ntt_reg.cuh"
 
-#include "blind_rotate.cuh"
+#include "br_launch.cuh"
 
 // ---------------------------------------------------------------------------
 // Sample extraction + key switching
@@ -42,50 +42,96 @@ __device__ __forceinline__ u64 ks_round(u64 a, const KeyDev &K) {
     return q & ((1ull << sh) - 1);
 }
 
-// out = (0^n, b) - sum_{i,j} KSK(i, j, d_ij) for the LWE_{N,Q} sample given
-// by get_a(i) (i < N) and b.  Threads own output columns; digits of all N
-// coefficients are precomputed into shared memory (one byte each).
-template <typename GetA>
-__device__ void key_switch_block(const KeyDev &K, GetA get_a, u64 b, u64 *__restrict__ out) {
-    extern __shared__ unsigned char dsm[];
+// Address of `p` (this block's shared memory) in the shared memory of block
+// `rank` of the cluster (distributed shared memory), and a load from it.
+__device__ __forceinline__ u64 ld_peer_smem(const u64 *p, u32 rank) {
+    const u32 local = (u32)__cvta_generic_to_shared(p);
+    u32 remote;
+    u64 v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(remote) : "memory");
+    return v;
+}
+
+// Key switching (Eq. (equ-key-swi)) of the LWE_{N,Q} sample given by
+// get_a(i) (i < N) and b: out = (0^n, b) - sum_{i,j} KSK(i, j, d_ij).
+// The S blocks of a thread-block cluster split the coefficients i (block
+// `rank` takes the rank-th slice of N/S); each thread owns columns
+// c = tid + q blockDim (q < CPT) and keeps four key rows' loads in flight;
+// block 0 then adds the partial sums it reads from its peers' shared memory
+// and writes the output.  Shared memory: digits (one byte each) of the
+// block's slice, then its n + 1 partial sums.
+template <int CPT, typename GetA>
+__device__ void key_switch_block(const KeyDev &K, GetA get_a, u64 b, u64 *__restrict__ out, u32 rank, u32 S) {
+    extern __shared__ __align__(16) unsigned char dsm[];
     const u32 N = K.N, n = K.n, lks = K.l_ks, B1 = (1u << K.log2_Bks) - 1;
-    for (u32 i = threadIdx.x; i < N; i += blockDim.x) {
+    const u32 i0 = rank * (N / S), i1 = i0 + N / S;
+    u64 *part = (u64 *)(dsm + (((size_t)(N / S) * lks + 15) & ~(size_t)15));
+    for (u32 i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const u64 at = ks_round(get_a(i), K);
-        for (u32 j = 0; j < lks; j++) dsm[i * lks + j] = (unsigned char)((at >> (K.log2_Bks * j)) & B1);
+        for (u32 j = 0; j < lks; j++)
+            dsm[(i - i0) * lks + j] = (unsigned char)((at >> (K.log2_Bks * j)) & B1);
     }
     __syncthreads();
-    constexpr int CPT = 8;   // columns per thread (n + 1 <= 8 * blockDim)
     u64 lo[CPT], hi[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; q++) lo[q] = hi[q] = 0;
     const size_t rowlen = n + 1;
-    for (u32 i = 0; i < N; i++) {
-        for (u32 j = 0; j < lks; j++) {
-            const u32 d = dsm[i * lks + j];
-            if (!d) continue;
-            const u64 *row = K.ksk + (((size_t)i * lks + j) * B1 + (d - 1)) * rowlen;
+    const u32 rows = (i1 - i0) * lks;
+    constexpr int KR = CPT == 4 ? 4 : 2;
+    for (u32 r0 = 0; r0 < rows; r0 += KR) {
+        const u64 *rp[KR];
+        bool ok[KR];
+#pragma unroll
+        for (int k = 0; k < KR; k++) {
+            const u32 rr = r0 + k;
+            const u32 d = rr < rows ? dsm[rr] : 0;    // digit d_ij of row rr = (i - i0) lks + j
+            ok[k] = d != 0;
+            const u32 i = i0 + rr / lks, j = rr % lks;
+            rp[k] = K.ksk + (((size_t)i * lks + j) * B1 + (ok[k] ? d - 1 : 0)) * rowlen;
+        }
+        u64 v[KR][CPT];
+#pragma unroll
+        for (int k = 0; k < KR; k++)
 #pragma unroll
             for (int q = 0; q < CPT; q++) {
                 const u32 c = threadIdx.x + q * blockDim.x;
-                if (c <= n) add128(lo[q], hi[q], __ldg(row + c));
+                v[k][q] = (ok[k] && c <= n) ? __ldg(rp[k] + c) : 0;
             }
-        }
+#pragma unroll
+        for (int k = 0; k < KR; k++)
+#pragma unroll
+            for (int q = 0; q < CPT; q++) add128(lo[q], hi[q], v[k][q]);
     }
     const u64 Q = K.mq.Q;
 #pragma unroll
     for (int q = 0; q < CPT; q++) {
         const u32 c = threadIdx.x + q * blockDim.x;
-        if (c <= n) {
-            const u64 sum = reduce128(lo[q], hi[q], K.mq);
+        if (c <= n) part[c] = reduce128(lo[q], hi[q], K.mq);
+    }
+    if (S > 1) cluster_sync(); else __syncthreads();
+    if (rank == 0) {
+        for (u32 c = threadIdx.x; c <= n; c += blockDim.x) {
+            u64 sum = part[c];
+            for (u32 r = 1; r < S; r++) sum = add_mod(sum, ld_peer_smem(part + c, r), Q);
             out[c] = sub_mod(c == n ? b : 0, sum, Q);
         }
     }
+    // peers keep their shared memory until block 0 has read it
+    if (S > 1) cluster_sync();
 }
 
-// Row 0 of the final ACC -> LWE_{N,Q} (Eq. (equ-sam-extr)) -> key switch.
-__global__ void k_extract_keyswitch(const DevJob *__restrict__ jobs, u32 steps_limit,
+// Row 0 of the final ACC -> LWE_{N,Q} (Eq. (equ-sam-extr)) -> key switch;
+// a cluster of S blocks per job (S = 1: plain launch, one block per job).
+// Launch bounds: 256 threads with 4 columns each (n < 1024), else up to 640
+// threads with 8 columns each (n < 5120).
+#define BM_KS_BOUNDS(CPT) __launch_bounds__((CPT) == 4 ? 256 : 640)
+
+template <int CPT>
+__global__ void BM_KS_BOUNDS(CPT) k_extract_keyswitch(const DevJob *__restrict__ jobs, u32 steps_limit,
                                     const u64 *__restrict__ ws, u64 *__restrict__ ct_out) {
-    const DevJob J = jobs[blockIdx.x];
+    const u32 S = cluster_size(), rank = cluster_rank();
+    const DevJob J = jobs[blockIdx.x / S];
     const KeyDev &K = *J.key;
     const u32 N = K.N;
     const u32 steps = steps_limit < K.n ? steps_limit : K.n;
@@ -96,14 +142,17 @@ __global__ void k_extract_keyswitch(const DevJob *__restrict__ jobs, u32 steps_l
         const u64 v = acc[N - i];
         return v ? Q - v : 0;
     };
-    key_switch_block(K, get_a, acc[N], ct_out + J.out_off);
+    key_switch_block<CPT>(K, get_a, acc[N], ct_out + J.out_off, rank, S);
 }
 
-__global__ void k_key_switch(const KeyDev *Kp, const u64 *__restrict__ lwe_in, u64 *__restrict__ out) {
+template <int CPT>
+__global__ void BM_KS_BOUNDS(CPT) k_key_switch(const KeyDev *Kp, const u64 *__restrict__ lwe_in, u64 *__restrict__ out) {
     const KeyDev &K = *Kp;
-    const u64 *in = lwe_in + (size_t)blockIdx.x * (K.N + 1);
+    const u32 S = cluster_size(), rank = cluster_rank();
+    const size_t job = blockIdx.x / S;
+    const u64 *in = lwe_in + job * (K.N + 1);
     auto get_a = [&](u32 i) -> u64 { return in[i]; };
-    key_switch_block(K, get_a, in[K.N], out + (size_t)blockIdx.x * (K.n + 1));
+    key_switch_block<CPT>(K, get_a, in[K.N], out + job * (K.n + 1), rank, S);
 }
 
 __global__ void k_sample_extract(const KeyDev *Kp, const u64 *__restrict__ rlwe, u64 *__restrict__ lwe) {
@@ -401,141 +450,55 @@ bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t
     return BM_OK;
 }
 
-// One block of 512 threads per job.
-template <int LOGN>
-__host__ __device__ constexpr int group_threads() { return 512; }
+// Kernel shape per ring degree (log2 N = 8..12) used by launches that do
+// not carry their own: the autotuner's choice once it has run, else the
+// measured best of each degree (radix 8 with 1024 threads for N = 1024 and
+// 4096, radix 16 with 512 threads for N = 2048).
+constexpr u32 kDefaultShape[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 1};
+std::atomic<u32> g_shape[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 1};
 
-template <int LOGN, bool LAZY, bool SMALL0, bool QLOW1>
-__global__ void __launch_bounds__(group_threads<LOGN>(), 512 / group_threads<LOGN>())
-    k_blind_rotate(const DevJob *__restrict__ jobs, u32 steps_limit, const u64 *__restrict__ ct_in,
-                   const u32 *__restrict__ luts, u64 *ws, u32 *status) {
-    extern __shared__ __align__(16) u64 sm[];
-    // a cluster of blocks shares one job (rows split); plain launches: 1 block
-    brk::br_job<LOGN, group_threads<LOGN>(), LAZY, SMALL0, QLOW1>(jobs[blockIdx.x / cluster_size()],
-                                                                   steps_limit, ct_in, luts, ws, status, sm);
-}
-
-// Sets the dynamic shared-memory limit of a kernel once per device.
-template <typename K>
-bm_status ensure_smem(K kern, size_t smem, std::atomic<uint64_t> &done) {
-    int dev = 0;
-    BM_CUDA_TRY(cudaGetDevice(&dev));
-    const uint64_t bit = 1ull << (dev & 63);
-    if (!(done.load() & bit)) {
-        BM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        done.fetch_or(bit);
+struct Shapes {
+    u32 s[13];
+    static Shapes current() {
+        Shapes x;
+        for (int i = 0; i < 13; i++) x.s[i] = g_shape[i].load();
+        return x;
     }
-    return BM_OK;
+};
+
+u32 log2u(u32 N) {
+    u32 l = 0;
+    while ((1u << l) < N) l++;
+    return l;
 }
 
-// Blocks per job (thread-block cluster size, rows split) for a launch of
-// `cnt` jobs of at most `mmax` rows: the smallest S in {1, 2, 4, 8}, S <=
-// min(mmax, max_cluster), that minimises waves(S) x ceil(mmax / S), where
-// waves(S) = ceil(cnt / clusters resident at once).  A full batch keeps one
-// block per job; a batch of fewer jobs than SMs spreads each job's rows over
-// a cluster, cutting its latency by up to S.
-template <typename K>
-u32 pick_cluster(K kern, u32 threads, size_t smem, u32 cnt, u32 mmax, u32 max_cluster) {
-    struct Occ { const void *k; u32 s; int dev; int slots; };
-    static std::mutex mu;
-    static std::vector<Occ> cache;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-    auto slots = [&](u32 S) -> int {
-        std::lock_guard<std::mutex> lk(mu);
-        for (const Occ &o : cache)
-            if (o.k == (const void *)kern && o.s == S && o.dev == dev) return o.slots;
-        int n = 0;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(S);
-        cfg.blockDim = dim3(threads);
-        cfg.dynamicSmemBytes = smem;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = S;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
-            cudaGetLastError();
-            n = 0;
-        }
-        cache.push_back({(const void *)kern, S, dev, n});
-        return n;
-    };
-    u32 best = 1;
-    const int s1 = slots(1);
-    if (s1 <= 0) return 1;
-    u64 best_cost = (u64)((cnt + s1 - 1) / s1) * mmax;
-    for (u32 S = 2; S <= 8 && S <= max_cluster && S <= mmax; S *= 2) {
-        const int sl = slots(S);
-        if (sl <= 0) break;
-        const u64 cost = (u64)((cnt + sl - 1) / sl) * ((mmax + S - 1) / S);
-        if (cost < best_cost) {
-            best_cost = cost;
-            best = S;
-        }
-    }
-    return best;
-}
-
-// dry: only set the kernel's attributes and occupancy (done before a
-// CUDA-graph capture).
-template <int LOGN, bool LAZY, bool SMALL0, bool QLOW1>
-bm_status launch_br_v(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 mmax, u32 max_cluster, u32 steps,
-                      const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status, cudaStream_t st,
-                      bool dry) {
-    using C = brk::Cfg<LOGN, group_threads<LOGN>()>;
-    static std::atomic<uint64_t> attr_done{0};
-    auto kern = k_blind_rotate<LOGN, LAZY, SMALL0, QLOW1>;
-    bm_status s = ensure_smem(kern, C::SMEM, attr_done);
-    if (s != BM_OK) return s;
-    const u32 S = max_cluster > 1 ? pick_cluster(kern, C::kThreads, C::SMEM, cnt, mmax, max_cluster) : 1;
-    if (dry) return BM_OK;
-    const DevJob *jobs = d_jobs + first;
-    if (S == 1) {
-        kern<<<cnt, C::kThreads, C::SMEM, st>>>(jobs, steps, ct_in, lut, ws_acc, status);
-    } else {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(cnt * S);
-        cfg.blockDim = dim3(C::kThreads);
-        cfg.dynamicSmemBytes = C::SMEM;
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = S;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        BM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, jobs, steps, ct_in, lut, ws_acc, status));
-    }
-    BM_CUDA_TRY(cudaGetLastError());
-    return BM_OK;
-}
-
-template <int LOGN>
-bm_status launch_br(const DevJob *d_jobs, uint32_t first, uint32_t cnt, u32 mmax, u32 max_cluster, u32 steps,
-                    const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status, u32 variant,
+bm_status launch_br_any(u32 N, u32 variant, u32 shape, const DevJob *jobs, uint32_t cnt, u32 mmax, u32 max_cluster,
+                    u32 steps, const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status,
                     cudaStream_t st, bool dry) {
-#define BM_LAUNCH(LZ, S0, QL)                                                                          \
-    return launch_br_v<LOGN, LZ, S0, QL>(d_jobs, first, cnt, mmax, max_cluster, steps, ct_in, lut, ws_acc, \
-                                         status, st, dry)
-    switch (variant) {
-        case BR_V_LAZY | BR_V_QLOW1: BM_LAUNCH(true, true, true);
-        case BR_V_LAZY: BM_LAUNCH(true, true, false);
-        case BR_V_QLOW1: BM_LAUNCH(false, false, true);
-        default: BM_LAUNCH(false, false, false);
+    switch (N) {
+        case 256:
+        case 512:
+            return bm_launch_br_small(N, variant, shape, jobs, cnt, mmax, max_cluster, steps, ct_in, lut, ws_acc,
+                                      status, st, dry);
+        case 1024:
+            return bm_launch_br_n1024(variant, shape, jobs, cnt, mmax, max_cluster, steps, ct_in, lut, ws_acc,
+                                      status, st, dry);
+        case 2048:
+            return bm_launch_br_n2048(variant, shape, jobs, cnt, mmax, max_cluster, steps, ct_in, lut, ws_acc,
+                                      status, st, dry);
+        case 4096:
+            return bm_launch_br_n4096(variant, shape, jobs, cnt, mmax, max_cluster, steps, ct_in, lut, ws_acc,
+                                      status, st, dry);
+        default: return BM_EINVAL;
     }
-#undef BM_LAUNCH
 }
 
 // Blind rotation of jobs [first, last) of the plan, one launch per run of
 // equal ring degree and variant; each job takes one block, or a cluster of up
 // to max_cluster blocks when the run has fewer jobs than the GPU has room for.
 bm_status run_groups(const Plan &pl, uint32_t first, uint32_t last, u32 steps, const uint64_t *d_ct_in,
-                     const uint32_t *d_lut, char *ws, cudaStream_t st, bool dry, u32 max_cluster) {
+                     const uint32_t *d_lut, char *ws, cudaStream_t st, bool dry, u32 max_cluster,
+                     const Shapes &shapes) {
     const DevJob *d_jobs = (const DevJob *)(ws + pl.jobs_off);
     u64 *ws_acc = (u64 *)(ws + pl.acc_off_bytes);
     u32 *status = (u32 *)ws;
@@ -549,19 +512,8 @@ bm_status run_groups(const Plan &pl, uint32_t first, uint32_t last, u32 steps, c
             mmax = pl.dj[j].m > mmax ? pl.dj[j].m : mmax;
             j++;
         }
-        bm_status s = BM_OK;
-#define BM_GRP(L)                                                                                       \
-    s = launch_br<L>(d_jobs, i, j - i, mmax, max_cluster, steps, d_ct_in, d_lut, ws_acc, status, variant, st, \
-                     dry)
-        switch (N) {
-            case 256: BM_GRP(8); break;
-            case 512: BM_GRP(9); break;
-            case 1024: BM_GRP(10); break;
-            case 2048: BM_GRP(11); break;
-            case 4096: BM_GRP(12); break;
-            default: return BM_EINVAL;
-        }
-#undef BM_GRP
+        bm_status s = launch_br_any(N, variant, shapes.s[log2u(N)], d_jobs + i, j - i, mmax, max_cluster, steps,
+                                d_ct_in, d_lut, ws_acc, status, st, dry);
         if (s != BM_OK) return s;
         i = j;
     }
@@ -581,8 +533,8 @@ struct Fork {
 };
 
 struct KsShape {
-    u32 threads;
-    size_t smem;
+    u32 threads, cpt;
+    size_t smem;   // digits of all N coefficients (one block per job) + partial sums
 };
 
 KsShape ks_shape(const bm_eval_key *const *keys, uint32_t n_keys) {
@@ -592,8 +544,55 @@ KsShape ks_shape(const bm_eval_key *const *keys, uint32_t n_keys) {
         maxn = keys[i]->p.n > maxn ? keys[i]->p.n : maxn;
         maxlks = keys[i]->p.l_ks > maxlks ? keys[i]->p.l_ks : maxlks;
     }
-    const u32 threads = (maxn + 1 + 7) / 8 < 128 ? 128 : ((maxn + 1 + 7) / 8 + 31) / 32 * 32;
-    return {threads, (size_t)maxN * maxlks};
+    KsShape k;
+    k.cpt = maxn + 1 <= 1024 ? 4 : 8;
+    k.threads = k.cpt == 4 ? 256 : ((maxn + 1 + 7) / 8 + 31) / 32 * 32;
+    k.smem = align_up((size_t)maxN * maxlks, 16) + 8 * (size_t)(maxn + 1);
+    return k;
+}
+
+// Blocks per job of the key switch: the largest S in {1, 2, 4, 8} with
+// count S <= SMs (one block per job once the batch fills the GPU).
+u32 ks_split(uint32_t count, int device) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 1;
+    u32 S = 1;
+    while (S < 8 && (u64)count * (2 * S) <= (u64)sms) S *= 2;
+    return S;
+}
+
+template <typename Kern, typename... Args>
+bm_status launch_ks_kernel(Kern kern, uint32_t count, u32 S, const KsShape &ks, cudaStream_t st, Args... args) {
+    static std::atomic<uint64_t> attr_done{0};
+    bm_status s = ensure_smem(kern, 96 * 1024, attr_done);
+    if (s != BM_OK) return s;
+    if (ks.smem > 96 * 1024) return BM_EINVAL;
+    if (S == 1) {
+        kern<<<count, ks.threads, ks.smem, st>>>(args...);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(count * S);
+        cfg.blockDim = dim3(ks.threads);
+        cfg.dynamicSmemBytes = ks.smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = S;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        BM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, args...));
+    }
+    BM_CUDA_TRY(cudaGetLastError());
+    return BM_OK;
+}
+
+bm_status launch_extract_ks(const KsShape &ks, uint32_t count, u32 S, cudaStream_t st, const DevJob *d_jobs,
+                            u32 steps, const u64 *ws_acc, uint64_t *d_out) {
+    if (ks.cpt == 4)
+        return launch_ks_kernel(k_extract_keyswitch<4>, count, S, ks, st, d_jobs, steps, ws_acc, d_out);
+    return launch_ks_kernel(k_extract_keyswitch<8>, count, S, ks, st, d_jobs, steps, ws_acc, d_out);
 }
 
 // Every launch of one batch (the plan is already in the workspace).
@@ -602,7 +601,8 @@ constexpr u32 kMaxCluster = 8;
 
 bm_status launch_all(const Plan &pl, uint32_t n_persistent, const KsShape &ks, int device, u32 steps, bool do_ks,
                      const uint64_t *d_ct_in, const uint32_t *d_lut, uint64_t *d_out, char *ws,
-                     cudaStream_t st, u32 max_cluster = kMaxCluster, const Fork *fork = nullptr) {
+                     cudaStream_t st, const Shapes &shapes, u32 max_cluster = kMaxCluster,
+                     const Fork *fork = nullptr) {
     const uint32_t count = (uint32_t)pl.dj.size();
     const DevJob *d_jobs = (const DevJob *)(ws + pl.jobs_off);
     u64 *ws_acc = (u64 *)(ws + pl.acc_off_bytes);
@@ -617,18 +617,19 @@ bm_status launch_all(const Plan &pl, uint32_t n_persistent, const KsShape &ks, i
             const ClassRange &cr = pl.classes[c];
             cudaStream_t cs = c == 0 ? st : fork->side[c - 1];
             if (c > 0) BM_CUDA_TRY(cudaStreamWaitEvent(cs, fork->ev[0], 0));
-            s = bm_launch_persistent_class(cr.N, cr.variant, d_jobs + cr.first, cr.last - cr.first, steps, d_ct_in,
-                                           d_lut, ws_acc, (u32 *)ws, (u32 *)ws + BM_WS_COUNTER_WORD + c, device,
-                                           false, cs);
+            s = bm_launch_persistent_class(cr.N, cr.variant, shapes.s[log2u(cr.N)], d_jobs + cr.first,
+                                           cr.last - cr.first, steps, d_ct_in, d_lut, ws_acc, (u32 *)ws,
+                                           (u32 *)ws + BM_WS_COUNTER_WORD + c, device, false, cs);
             if (s != BM_OK) return s;
             if (c > 0) BM_CUDA_TRY(cudaEventRecord(fork->ev[c], cs));
         }
         for (size_t c = 1; c < nc; c++) BM_CUDA_TRY(cudaStreamWaitEvent(st, fork->ev[c], 0));
     }
-    if ((s = run_groups(pl, n_persistent, count, steps, d_ct_in, d_lut, ws, st, false, max_cluster)) != BM_OK)
+    if ((s = run_groups(pl, n_persistent, count, steps, d_ct_in, d_lut, ws, st, false, max_cluster, shapes)) != BM_OK)
         return s;
     if (do_ks) {
-        k_extract_keyswitch<<<count, ks.threads, ks.smem, st>>>(d_jobs, steps, ws_acc, d_out);
+        if ((s = launch_extract_ks(ks, count, ks_split(count, device), st, d_jobs, steps, ws_acc, d_out)) != BM_OK)
+            return s;
     } else {
         k_copy_acc<<<count, 256, 0, st>>>(d_jobs, steps, ws_acc, d_out);
     }
@@ -689,7 +690,8 @@ static bm_status bootstrap_impl(const bm_eval_key *const *keys, uint32_t n_keys,
     cudaStream_t st = (cudaStream_t)stream;
     char *ws = (char *)d_ws;
     if ((s = upload_plan(pl, ws, st)) != BM_OK) return s;
-    return launch_all(pl, 0, ks_shape(keys, n_keys), dev, steps, do_ks, d_ct_in, d_lut, d_out, ws, st);
+    return launch_all(pl, 0, ks_shape(keys, n_keys), dev, steps, do_ks, d_ct_in, d_lut, d_out, ws, st,
+                      Shapes::current());
 }
 
 extern "C" bm_status bm_bootstrap_batch(const bm_eval_key *const *keys, uint32_t n_keys, const bm_job *jobs,
@@ -788,12 +790,12 @@ extern "C" bm_status bm_key_switch(const bm_eval_key *key, const uint64_t *d_lwe
     if (!key || (count && (!d_lwe_in || !d_out))) return BM_EINVAL;
     if (!count) return BM_OK;
     DeviceGuard g(key->device);
-    const u32 n = key->p.n;
-    const u32 threads = (n + 1 + 7) / 8 < 128 ? 128 : ((n + 1 + 7) / 8 + 31) / 32 * 32;
-    const size_t smem = (size_t)key->p.N * key->p.l_ks;
-    k_key_switch<<<count, threads, smem, (cudaStream_t)stream>>>(key->d_view, d_lwe_in, d_out);
-    BM_CUDA_TRY(cudaGetLastError());
-    return BM_OK;
+    const bm_eval_key *keys[1] = {key};
+    const KsShape ks = ks_shape(keys, 1);
+    const u32 S = ks_split(count, key->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ks.cpt == 4) return launch_ks_kernel(k_key_switch<4>, count, S, ks, st, key->d_view, d_lwe_in, d_out);
+    return launch_ks_kernel(k_key_switch<8>, count, S, ks, st, key->d_view, d_lwe_in, d_out);
 }
 
 extern "C" bm_status bm_poly_mul(const bm_eval_key *key, const uint64_t *d_a, const uint64_t *d_b,
@@ -944,6 +946,7 @@ struct bm_batch {
     uint32_t flags, n_persistent;
     Plan pl;
     Fork fork;
+    Shapes shapes;     // the kernel shapes current when the batch was created
     KsShape ks;
     const uint64_t *d_ct_in;
     const uint32_t *d_lut;
@@ -973,6 +976,7 @@ extern "C" bm_status bm_batch_create(const bm_eval_key *const *keys, uint32_t n_
     }
     b->n_persistent = (flags & BM_BATCH_PERSISTENT) ? persistent_prefix(b->pl) : 0;
     b->ks = ks_shape(keys, n_keys);
+    b->shapes = Shapes::current();
     b->d_ct_in = d_ct_in;
     b->d_lut = d_lut;
     b->d_out = d_ct_out;
@@ -984,11 +988,12 @@ extern "C" bm_status bm_batch_create(const bm_eval_key *const *keys, uint32_t n_
     if (e == cudaSuccess) e = cudaMemset(b->ws, 0, BM_WS_HEADER);
     // kernel attributes are set now, outside any later stream capture
     if (e == cudaSuccess && run_groups(b->pl, b->n_persistent, count, 0, nullptr, nullptr, b->ws, nullptr,
-                                       true, b->max_cluster()) != BM_OK)
+                                       true, b->max_cluster(), b->shapes) != BM_OK)
         e = cudaErrorUnknown;
     for (const ClassRange &cr : b->pl.classes) {
-        if (e == cudaSuccess && bm_launch_persistent_class(cr.N, cr.variant, nullptr, 0, 0, nullptr, nullptr, nullptr,
-                                                           nullptr, nullptr, dev, true, nullptr) != BM_OK)
+        if (e == cudaSuccess && bm_launch_persistent_class(cr.N, cr.variant, b->shapes.s[log2u(cr.N)], nullptr, 0, 0,
+                                                           nullptr, nullptr, nullptr, nullptr, nullptr, dev, true,
+                                                           nullptr) != BM_OK)
             e = cudaErrorUnknown;
     }
     if (b->pl.classes.size() > BM_MAX_CLASSES) e = cudaErrorInvalidValue;
@@ -1015,13 +1020,13 @@ extern "C" bm_status bm_batch_run(bm_batch *b, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (!(b->flags & BM_BATCH_GRAPH))
         return launch_all(b->pl, b->n_persistent, b->ks, b->device, 0xffffffffu, true, b->d_ct_in, b->d_lut,
-                          b->d_out, b->ws, st, b->max_cluster(), &b->fork);
+                          b->d_out, b->ws, st, b->shapes, b->max_cluster(), &b->fork);
     if (!st) return BM_EINVAL;   // the legacy default stream cannot be captured
     if (!b->exec) {
         cudaGraph_t graph = nullptr;
         BM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         bm_status s = launch_all(b->pl, b->n_persistent, b->ks, b->device, 0xffffffffu, true, b->d_ct_in,
-                                 b->d_lut, b->d_out, b->ws, st, b->max_cluster(), &b->fork);
+                                 b->d_lut, b->d_out, b->ws, st, b->shapes, b->max_cluster(), &b->fork);
         cudaError_t e = cudaStreamEndCapture(st, &graph);
         if (s != BM_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -1047,6 +1052,36 @@ extern "C" void bm_batch_free(bm_batch *b) {
     for (cudaEvent_t ev : b->fork.ev)
         if (ev) cudaEventDestroy(ev);
     delete b;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel shapes
+// ---------------------------------------------------------------------------
+
+extern "C" bm_status bm_kernel_shape_info(uint32_t shape, uint32_t N, uint32_t *radix, uint32_t *threads,
+                                          uint32_t *blocks_per_sm) {
+    if (N < 256 || N > 4096 || (N & (N - 1)) || shape >= BM_NUM_SHAPES) return BM_EINVAL;
+    if (shape != 0 && (N < 1024 || !br_shape_fits((int)log2u(N), (int)shape))) return BM_EINVAL;
+    const BrShape b = br_shape((int)shape);
+    if (radix) *radix = 1u << b.rb;
+    if (threads) *threads = (uint32_t)b.threads;
+    if (blocks_per_sm) *blocks_per_sm = (uint32_t)b.blocks;
+    return BM_OK;
+}
+
+extern "C" bm_status bm_set_kernel_shape(uint32_t N, uint32_t shape) {
+    if (N < 256 || N > 4096 || (N & (N - 1))) return BM_EINVAL;
+    const u32 l = log2u(N);
+    if (shape == BM_SHAPE_DEFAULT) shape = kDefaultShape[l];
+    if (bm_kernel_shape_info(shape, N, nullptr, nullptr, nullptr) != BM_OK) return BM_EINVAL;
+    g_shape[l].store(shape);
+    return BM_OK;
+}
+
+extern "C" bm_status bm_get_kernel_shape(uint32_t N, uint32_t *shape) {
+    if (N < 256 || N > 4096 || (N & (N - 1)) || !shape) return BM_EINVAL;
+    *shape = g_shape[log2u(N)].load();
+    return BM_OK;
 }
 
 // ---------------------------------------------------------------------------

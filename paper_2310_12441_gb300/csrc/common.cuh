@@ -127,9 +127,26 @@ struct bm_secret_key {
 // and arithmetic variant; persistent.cu): one block per SM pulls the class's
 // jobs from `counter` (a word of the workspace header).  dry: only set the
 // kernel's attributes (before a stream capture).
-bm_status bm_launch_persistent_class(u32 N, u32 variant, const DevJob *d_jobs, uint32_t count, uint32_t steps,
-                                     const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status,
-                                     u32 *counter, int device, bool dry, cudaStream_t st);
+bm_status bm_launch_persistent_class(u32 N, u32 variant, u32 shape, const DevJob *d_jobs, uint32_t count,
+                                     uint32_t steps, const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc,
+                                     u32 *status, u32 *counter, int device, bool dry, cudaStream_t st);
+
+// Blind-rotation launches per ring degree (br_n*.cu): jobs [0, cnt) of
+// `jobs`, all of ring degree N and arithmetic variant `variant`, with kernel
+// shape `shape` (br_launch.cuh); dry: only set the kernel's attributes.
+#define BM_NUM_SHAPES 5
+bm_status bm_launch_br_small(u32 N, u32 variant, u32 shape, const DevJob *jobs, uint32_t cnt, u32 mmax,
+                             u32 max_cluster, u32 steps, const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc,
+                             u32 *status, cudaStream_t st, bool dry);
+bm_status bm_launch_br_n1024(u32 variant, u32 shape, const DevJob *jobs, uint32_t cnt, u32 mmax, u32 max_cluster,
+                             u32 steps, const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status,
+                             cudaStream_t st, bool dry);
+bm_status bm_launch_br_n2048(u32 variant, u32 shape, const DevJob *jobs, uint32_t cnt, u32 mmax, u32 max_cluster,
+                             u32 steps, const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status,
+                             cudaStream_t st, bool dry);
+bm_status bm_launch_br_n4096(u32 variant, u32 shape, const DevJob *jobs, uint32_t cnt, u32 mmax, u32 max_cluster,
+                             u32 steps, const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status,
+                             cudaStream_t st, bool dry);
 
 // Host helpers (keygen.cu)
 bm_status bm_check_key_params(const bm_key_params *p);

@@ -2,41 +2,47 @@
 //
 // Same transform as ntt.cuh (Cooley-Tukey forward with psi^bitrev twiddles,
 // bit-reversed output; Gentleman-Sande inverse without the N^-1 factor), but
-// each thread holds R = 16 coefficients of one polynomial in registers and
-// performs up to four butterfly stages on them (a radix-16 phase); between
+// each thread holds R = 2^RB coefficients of one polynomial in registers and
+// performs up to RB butterfly stages on them (a radix-R phase); between
 // phases the block exchanges values through shared memory.  A polynomial of
-// N = 2^LOGN coefficients takes T = N/16 threads and ceil(LOGN/4) phases.
+// N = 2^LOGN coefficients takes T = N/R threads and ceil(LOGN/RB) phases.
+// The radix is a template parameter (R = 16 or 8): fewer values per thread
+// need fewer registers, so more threads fit on an SM, at the price of more
+// exchanges.
 //
-// Phase layouts: a thread of a phase whose 4-bit field sits at bits
-// [F, F+4) of the coefficient index holds the 16 indices that differ only in
-// that field; its thread number l supplies the other bits (the bits below F
-// first).  Forward phases take the fields from the top down
-// (F = LOGN-4, LOGN-8, ..., 0), inverse phases from the bottom up.  Stage s
-// of the forward transform acts on index bit LOGN-1-s, stage s of the
-// inverse on bit s; a butterfly group is the index shifted right past that
-// bit.
+// Phase layouts: a thread of a phase whose RB-bit field sits at bits
+// [F, F+RB) of the coefficient index holds the R indices that differ only
+// in that field; its thread number l supplies the other bits (the bits below
+// F first).  Forward phases take the fields from the top down
+// (F = LOGN-RB, LOGN-2RB, ..., then 0), inverse phases from the bottom up
+// (F = 0, RB, 2RB, ..., then LOGN-RB).  Stage s of the forward transform
+// acts on index bit LOGN-1-s, stage s of the inverse on bit s; a butterfly
+// group is the index shifted right past that bit.
 //
 // Butterflies are Harvey's lazy ones (D. Harvey, "Faster arithmetic for
 // number-theoretic transforms", J. Symb. Comp. 2014): forward values stay in
 // [0, 4Q), inverse values in [0, 2Q); twiddle products use the three-product
-// Shoup quotient of modarith.cuh (with a one-multiply q Q when Q = c 2^32 + 1).  Twiddles come as (w, w') pairs.
+// Shoup quotient of modarith.cuh (with a one-multiply q Q when Q = c 2^32 + 1).
+// Twiddles come as (w, w') pairs.
 //
 // Shared memory: every polynomial owns two regions of N words and the
 // exchanges alternate between them (Swap), so a region is never rewritten
 // while a slower thread may still read it and each exchange needs a single
-// barrier.  Index idx is stored at word idx ^ ((idx >> 4) & 15), which keeps
+// barrier.  Index idx is stored at word idx ^ ((idx >> RB) & 15), which keeps
 // every phase's accesses (and position-major accesses) free of bank
-// conflicts.
+// conflicts for R = 8 and 16 (each half-warp touches 16 distinct words
+// modulo 16).
 #pragma once
 #include "modarith.cuh"
 
 namespace ntr {
 
-__device__ __forceinline__ u32 swz(u32 idx) { return idx ^ ((idx >> 4) & 15u); }
+template <int RB>
+__device__ __forceinline__ u32 swz(u32 idx) { return idx ^ ((idx >> RB) & 15u); }
 
-template <int F>
+template <int RB, int F>
 __device__ __forceinline__ u32 fidx(u32 l, u32 i) {
-    return ((l >> F) << (F + 4)) | (i << F) | (l & ((1u << F) - 1u));
+    return ((l >> F) << (F + RB)) | (i << F) | (l & ((1u << F) - 1u));
 }
 
 // The two shared regions of one polynomial; `next` is the one written next.
@@ -63,7 +69,7 @@ __device__ __forceinline__ void twiddle(const u64 *__restrict__ tp, u32 ti, u64 
     Wsh = v.y;
 }
 
-// Forward phase: NST stages starting at global stage S0, field [F, F+4).
+// Forward phase: NST stages starting at global stage S0, field [F, F+RB).
 // LAZY: no per-stage corrections.  Products lie in [0, 4Q) and the sum and
 // difference X + T, X - T + 4Q each grow the bound by 4Q, so inputs below Q
 // leave the last stage below (1 + 4 LOGN) Q, which the caller guarantees
@@ -74,24 +80,26 @@ __device__ __forceinline__ void twiddle(const u64 *__restrict__ tp, u32 ti, u64 
 // W * Y is formed exactly (a 64 x 32-bit product) and left unreduced:
 // X + W Y and X - W Y + Q B, both below B + Q B.  The caller guarantees
 // B + Q B + 4 Q (LOGN - 1) < 2^64.
-template <int LOGN, int F, int S0, int NST, bool LAZY, bool SMALL0 = false, bool QLOW1 = false, bool TWS = false>
-__device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__restrict__ twp, u64 Q,
+template <int LOGN, int RB, int F, int S0, int NST, bool LAZY, bool SMALL0 = false, bool QLOW1 = false,
+          bool TWS = false>
+__device__ __forceinline__ void fwd_phase(u64 (&x)[1 << RB], u32 l, const u64 *__restrict__ twp, u64 Q,
                                           u64 twoQ, u64 qb = 0) {
+    constexpr int R = 1 << RB;
     const u32 high = l >> F;
 #pragma unroll
     for (int st = 0; st < NST; st++) {
         const int s = S0 + st;
         const int lb = LOGN - 1 - s - F;
 #pragma unroll
-        for (int i = 0; i < 16; i++) {
+        for (int i = 0; i < R; i++) {
             if (i & (1 << lb)) continue;
             const int i2 = i | (1 << lb);
-            const u32 g = (high << (3 - lb)) | (u32)(i >> (lb + 1));
+            const u32 g = (high << (RB - 1 - lb)) | (u32)(i >> (lb + 1));
             u64 W, Wsh;
             if constexpr (TWS) {
                 // shared table in the per-stage transposed order of
                 // twiddle_slot(): the thread part of g runs fastest
-                twiddle<true>(twp, (1u << s) + ((u32)(i >> (lb + 1)) << (LOGN - 4 - F)) + high, W, Wsh);
+                twiddle<true>(twp, (1u << s) + ((u32)(i >> (lb + 1)) << (LOGN - RB - F)) + high, W, Wsh);
             } else {
                 twiddle<false>(twp, (1u << s) + g, W, Wsh);
             }
@@ -121,24 +129,25 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[16], u32 l, const u64 *__rest
     }
 }
 
-// Inverse phase: NST stages acting on bits SB, SB+1, ..., field [F, F+4).
-template <int LOGN, int F, int SB, int NST, bool QLOW1 = false, bool TWS = false, bool LZI = false>
-__device__ __forceinline__ void inv_phase(u64 (&x)[16], u32 l, const u64 *__restrict__ itwp, u64 Q,
+// Inverse phase: NST stages acting on bits SB, SB+1, ..., field [F, F+RB).
+template <int LOGN, int RB, int F, int SB, int NST, bool QLOW1 = false, bool TWS = false, bool LZI = false>
+__device__ __forceinline__ void inv_phase(u64 (&x)[1 << RB], u32 l, const u64 *__restrict__ itwp, u64 Q,
                                           u64 twoQ) {
+    constexpr int R = 1 << RB;
     const u32 high = l >> F;
 #pragma unroll
     for (int st = 0; st < NST; st++) {
         const int b = SB + st;
         const int lb = b - F;
 #pragma unroll
-        for (int i = 0; i < 16; i++) {
+        for (int i = 0; i < R; i++) {
             if (i & (1 << lb)) continue;
             const int i2 = i | (1 << lb);
-            const u32 g = (high << (3 - lb)) | (u32)(i >> (lb + 1));
+            const u32 g = (high << (RB - 1 - lb)) | (u32)(i >> (lb + 1));
             u64 W, Wsh;
             if constexpr (TWS) {
                 // shared table in the transposed order of inv_twiddle_slot()
-                twiddle<true>(itwp, (1u << (LOGN - 1 - b)) + ((u32)(i >> (lb + 1)) << (LOGN - 4 - F)) + high, W,
+                twiddle<true>(itwp, (1u << (LOGN - 1 - b)) + ((u32)(i >> (lb + 1)) << (LOGN - RB - F)) + high, W,
                               Wsh);
             } else {
                 twiddle<false>(itwp, (1u << (LOGN - 1 - b)) + g, W, Wsh);
@@ -161,17 +170,18 @@ __device__ __forceinline__ void inv_phase(u64 (&x)[16], u32 l, const u64 *__rest
 // Index into the plain forward table (psi^bitrev(k) at k = 2^s + g) of slot
 // `pos` of the transposed shared-memory copy read by fwd_phase<..., TWS>.
 // Stage s sits in the phase whose field starts at F; there g = (high << a) | j
-// with the thread part high = l >> F below 2^(LOGN-4-F) and the register part
-// j below 2^a, a = s - (LOGN-4-F); slot 2^s + j 2^(LOGN-4-F) + high holds it,
-// so the threads of a warp read consecutive slots (no bank conflicts).
-template <int LOGN>
+// with the thread part high = l >> F below 2^(LOGN-RB-F) and the register
+// part j below 2^a, a = s - (LOGN-RB-F); slot 2^s + j 2^(LOGN-RB-F) + high
+// holds it, so the threads of a warp read consecutive slots (no bank
+// conflicts).
+template <int LOGN, int RB>
 __device__ __forceinline__ u32 twiddle_slot(u32 pos) {
     if (pos == 0) return 0;
-    constexpr u32 NPH = (LOGN + 3) / 4;
+    constexpr u32 NPH = (LOGN + RB - 1) / RB;
     const u32 s = 31 - __clz(pos);
-    const u32 ph = s / 4;
-    const u32 F = ph < NPH - 1 ? LOGN - 4 - 4 * ph : 0;
-    const u32 sh = LOGN - 4 - F;
+    const u32 ph = s / RB;
+    const u32 F = ph < NPH - 1 ? LOGN - RB - RB * ph : 0;
+    const u32 sh = LOGN - RB - F;
     const u32 r = pos - (1u << s);
     const u32 j = r >> sh, high = r & ((1u << sh) - 1);
     return (1u << s) + ((high << (s - sh)) | j);
@@ -179,64 +189,79 @@ __device__ __forceinline__ u32 twiddle_slot(u32 pos) {
 
 // The same for the inverse table (psi^-bitrev(k) at k = 2^s + g, used by the
 // inverse stage on bit LOGN-1-s, which sits in the inverse phase with field F).
-template <int LOGN>
+template <int LOGN, int RB>
 __device__ __forceinline__ u32 inv_twiddle_slot(u32 pos) {
     if (pos == 0) return 0;
-    constexpr u32 NPH = (LOGN + 3) / 4;
+    constexpr u32 NPH = (LOGN + RB - 1) / RB;
     const u32 s = 31 - __clz(pos);
-    const u32 q = (LOGN - 1 - s) / 4;
-    const u32 F = q < NPH - 1 ? 4 * q : LOGN - 4;
-    const u32 sh = LOGN - 4 - F;
+    const u32 q = (LOGN - 1 - s) / RB;
+    const u32 F = q < NPH - 1 ? RB * q : LOGN - RB;
+    const u32 sh = LOGN - RB - F;
     const u32 r = pos - (1u << s);
     const u32 j = r >> sh, high = r & ((1u << sh) - 1);
     return (1u << s) + ((high << (s - sh)) | j);
 }
 
-template <int F>
-__device__ __forceinline__ void store_field(const u64 (&x)[16], u64 *reg, u32 l) {
+template <int RB, int F>
+__device__ __forceinline__ void store_field(const u64 (&x)[1 << RB], u64 *reg, u32 l) {
 #pragma unroll
-    for (int i = 0; i < 16; i++) reg[swz(fidx<F>(l, i))] = x[i];
+    for (int i = 0; i < (1 << RB); i++) reg[swz<RB>(fidx<RB, F>(l, i))] = x[i];
 }
 
-template <int F>
-__device__ __forceinline__ void load_field(u64 (&x)[16], const u64 *reg, u32 l) {
+template <int RB, int F>
+__device__ __forceinline__ void load_field(u64 (&x)[1 << RB], const u64 *reg, u32 l) {
 #pragma unroll
-    for (int i = 0; i < 16; i++) x[i] = reg[swz(fidx<F>(l, i))];
+    for (int i = 0; i < (1 << RB); i++) x[i] = reg[swz<RB>(fidx<RB, F>(l, i))];
 }
 
-// Forward NTT.  On entry x holds indices l + T i (field [LOGN-4, LOGN)) of
+// Middle forward phases PH = 1 .. NPH-2 (field LOGN - RB (PH + 1)); `r` holds
+// the previous phase's layout and the block has passed a barrier since it was
+// written.  Returns the region holding the last middle phase's output.
+template <int LOGN, int RB, int PH, bool LAZY, bool QLOW1, bool TWS>
+__device__ __forceinline__ u64 *fwd_middle(u64 (&x)[1 << RB], Swap &sw, u64 *r, u32 l, bool active,
+                                           const u64 *__restrict__ twp, u64 Q, u64 twoQ) {
+    constexpr int NPH = (LOGN + RB - 1) / RB;
+    if constexpr (PH < NPH - 1) {
+        constexpr int F = LOGN - RB * (PH + 1);
+        if (active) {
+            load_field<RB, F>(x, r, l);
+            fwd_phase<LOGN, RB, F, RB * PH, RB, LAZY, false, QLOW1, TWS>(x, l, twp, Q, twoQ);
+        }
+        u64 *r2 = sw.take();
+        if (active) store_field<RB, F>(x, r2, l);
+        __syncthreads();
+        return fwd_middle<LOGN, RB, PH + 1, LAZY, QLOW1, TWS>(x, sw, r2, l, active, twp, Q, twoQ);
+    } else {
+        return r;
+    }
+}
+
+// Forward NTT.  On entry x holds indices l + T i (field [LOGN-RB, LOGN)) of
 // this thread's polynomial, values below 4Q.  TWS: twp points to a copy of
 // the twiddle pairs in shared memory.  Returns the region that holds
 // the transform in bit-reversed positions, values in [0, Q), or with LAZY
 // only partly reduced for the multiply-accumulate: [0, 3Q) when QLOW1, else
-// [0, 2Q)
-// (swizzled); the caller must __syncthreads() before reading it.  Every
-// thread of the block calls this (it contains barriers); threads with
+// [0, 2Q) (swizzled); the caller must __syncthreads() before reading it.
+// Every thread of the block calls this (it contains barriers); threads with
 // active == false only take part in the barriers.
-template <int LOGN, bool LAZY, bool SMALL0 = false, bool QLOW1 = false, bool TWS = false>
-__device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool active,
+template <int LOGN, int RB, bool LAZY, bool SMALL0 = false, bool QLOW1 = false, bool TWS = false>
+__device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[1 << RB], Swap &sw, u32 l, bool active,
                                             const u64 *__restrict__ twp, u64 Q, u64 one_sh, u64 qb = 0) {
-    constexpr int NPH = (LOGN + 3) / 4;
+    constexpr int R = 1 << RB;
+    constexpr int NPH = (LOGN + RB - 1) / RB;
     static_assert(LOGN >= 8 && LOGN <= 12, "ring degree 256..4096");
+    static_assert(RB == 3 || RB == 4, "radix 8 or 16");
     const u64 twoQ = 2 * Q;
-    if (active) fwd_phase<LOGN, LOGN - 4, 0, 4, LAZY, SMALL0, QLOW1, TWS>(x, l, twp, Q, twoQ, qb);
+    if (active) fwd_phase<LOGN, RB, LOGN - RB, 0, RB, LAZY, SMALL0, QLOW1, TWS>(x, l, twp, Q, twoQ, qb);
     u64 *r = sw.take();
-    if (active) store_field<LOGN - 4>(x, r, l);
+    if (active) store_field<RB, LOGN - RB>(x, r, l);
     __syncthreads();
-    if constexpr (NPH == 3) {
-        if (active) {
-            load_field<LOGN - 8>(x, r, l);
-            fwd_phase<LOGN, LOGN - 8, 4, 4, LAZY, false, QLOW1, TWS>(x, l, twp, Q, twoQ);
-        }
-        r = sw.take();
-        if (active) store_field<LOGN - 8>(x, r, l);
-        __syncthreads();
-    }
+    r = fwd_middle<LOGN, RB, 1, LAZY, QLOW1, TWS>(x, sw, r, l, active, twp, Q, twoQ);
     if (active) {
-        load_field<0>(x, r, l);
-        fwd_phase<LOGN, 0, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), LAZY, false, QLOW1, TWS>(x, l, twp, Q, twoQ);
+        load_field<RB, 0>(x, r, l);
+        fwd_phase<LOGN, RB, 0, RB * (NPH - 1), LOGN - RB * (NPH - 1), LAZY, false, QLOW1, TWS>(x, l, twp, Q, twoQ);
 #pragma unroll
-        for (int i = 0; i < 16; i++) {
+        for (int i = 0; i < R; i++) {
             u64 v = x[i];
             if constexpr (LAZY && QLOW1) {
                 // Q = c 2^32 + 1 > 2^32, so floor(2^64 / Q) < 2^32 and the
@@ -254,8 +279,32 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
         }
     }
     r = sw.take();
-    if (active) store_field<0>(x, r, l);
+    if (active) store_field<RB, 0>(x, r, l);
     return r;
+}
+
+// Middle inverse phases Qp = 1 .. NPH-2 (field RB Qp).
+template <int LOGN, int RB, int QP, bool QLOW1, bool TWS, bool LZI>
+__device__ __forceinline__ u64 *inv_middle(u64 (&x)[1 << RB], Swap &sw, u64 *r, u32 l, bool active,
+                                           const u64 *__restrict__ itwp, u64 Q, u64 twoQ, u64 one_sh) {
+    constexpr int NPH = (LOGN + RB - 1) / RB;
+    if constexpr (QP < NPH - 1) {
+        constexpr int F = RB * QP;
+        if (active) {
+            load_field<RB, F>(x, r, l);
+            inv_phase<LOGN, RB, F, F, RB, QLOW1, TWS, LZI>(x, l, itwp, Q, twoQ);
+            if constexpr (LZI) {
+#pragma unroll
+                for (int i = 0; i < (1 << RB); i++) x[i] = reduce_est_qlow1(x[i], (u32)one_sh, (u32)(Q >> 32));
+            }
+        }
+        u64 *r2 = sw.take();
+        if (active) store_field<RB, F>(x, r2, l);
+        __syncthreads();
+        return inv_middle<LOGN, RB, QP + 1, QLOW1, TWS, LZI>(x, sw, r2, l, active, itwp, Q, twoQ, one_sh);
+    } else {
+        return r;
+    }
 }
 
 // Inverse NTT (without N^-1).  On entry region `in` holds the bit-reversed
@@ -265,44 +314,38 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[16], Swap &sw, u32 l, bool 
 // Q = c 2^32 + 1 the butterflies keep [0, 4Q) with one correction each
 // (bfly_gs_qlow1), or with LZI (Q = c 2^32 + 1 and 128 Q < 2^64) none
 // (bfly_gs_lazy_qlow1 with q64 = 64 Q).  A phase of four stages takes values
-// below 3Q to below 48Q (3Q, 6Q, 12Q, 24Q, 48Q; inputs below Q reach 32Q),
-// so U - V + 64Q < 112Q < 2^64; between phases the values are brought back
-// below 3Q by reduce_est_qlow1 (one_sh = floor(2^64 / Q)).
-template <int LOGN, bool QLOW1 = false, bool TWS = false, bool LZI = false>
-__device__ __forceinline__ void inv_from_smem(u64 (&x)[16], const u64 *in, Swap &sw, u32 l, bool active,
+// below 3Q to below 48Q (3Q, 6Q, 12Q, 24Q, 48Q; inputs below Q reach 32Q;
+// three stages stop at 24Q), so U - V + 64Q < 112Q < 2^64; between phases
+// the values are brought back below 3Q by reduce_est_qlow1
+// (one_sh = floor(2^64 / Q)).
+template <int LOGN, int RB, bool QLOW1 = false, bool TWS = false, bool LZI = false>
+__device__ __forceinline__ void inv_from_smem(u64 (&x)[1 << RB], const u64 *in, Swap &sw, u32 l, bool active,
                                               const u64 *__restrict__ itwp, u64 Q, u64 one_sh = 0) {
-    constexpr int NPH = (LOGN + 3) / 4;
+    constexpr int R = 1 << RB;
+    constexpr int NPH = (LOGN + RB - 1) / RB;
     const u64 twoQ = 2 * Q;
     auto between = [&]() {
         if constexpr (LZI) {
 #pragma unroll
-            for (int i = 0; i < 16; i++) x[i] = reduce_est_qlow1(x[i], (u32)one_sh, (u32)(Q >> 32));
+            for (int i = 0; i < R; i++) x[i] = reduce_est_qlow1(x[i], (u32)one_sh, (u32)(Q >> 32));
         }
     };
     if (active) {
-        load_field<0>(x, in, l);
-        inv_phase<LOGN, 0, 0, 4, QLOW1, TWS, LZI>(x, l, itwp, Q, twoQ);
+        load_field<RB, 0>(x, in, l);
+        inv_phase<LOGN, RB, 0, 0, RB, QLOW1, TWS, LZI>(x, l, itwp, Q, twoQ);
         between();
     }
     u64 *r = sw.take();
-    if (active) store_field<0>(x, r, l);
+    if (active) store_field<RB, 0>(x, r, l);
     __syncthreads();
-    if constexpr (NPH == 3) {
-        if (active) {
-            load_field<4>(x, r, l);
-            inv_phase<LOGN, 4, 4, 4, QLOW1, TWS, LZI>(x, l, itwp, Q, twoQ);
-            between();
-        }
-        r = sw.take();
-        if (active) store_field<4>(x, r, l);
-        __syncthreads();
-    }
+    r = inv_middle<LOGN, RB, 1, QLOW1, TWS, LZI>(x, sw, r, l, active, itwp, Q, twoQ, one_sh);
     if (active) {
-        load_field<LOGN - 4>(x, r, l);
-        inv_phase<LOGN, LOGN - 4, 4 * (NPH - 1), LOGN - 4 * (NPH - 1), QLOW1, TWS, LZI>(x, l, itwp, Q, twoQ);
+        load_field<RB, LOGN - RB>(x, r, l);
+        inv_phase<LOGN, RB, LOGN - RB, RB * (NPH - 1), LOGN - RB * (NPH - 1), QLOW1, TWS, LZI>(x, l, itwp, Q,
+                                                                                             twoQ);
         between();
 #pragma unroll
-        for (int i = 0; i < 16; i++)
+        for (int i = 0; i < R; i++)
             x[i] = (LZI || QLOW1) ? csub64(csub64(x[i], twoQ), Q) : csub64(x[i], Q);
     }
 }

@@ -9,14 +9,18 @@
 // few bytes.  The host launches the classes concurrently (forked streams,
 // longest class first), so the blocks of a later class take over each SM as
 // the earlier class runs out of jobs.
-#include "blind_rotate.cuh"
+#include "br_launch.cuh"
 
 namespace {
 
-constexpr int kPThreads = 512;
+// Persistent shapes: those of one block per SM (0: radix 16 x 512 threads,
+// 1: radix 8 x 1024 threads, 4: radix 8 x 512 threads).
+__host__ __device__ constexpr bool persistent_shape(int logn, int sh) {
+    return br_shape(sh).blocks == 1 && br_shape_fits(logn, sh);
+}
 
-template <int LOGN, u32 V>
-__global__ void __launch_bounds__(kPThreads, 1)
+template <int LOGN, u32 V, int SH>
+__global__ void __launch_bounds__(br_shape(SH).threads, 1)
     k_blind_rotate_persistent(const DevJob *__restrict__ jobs, u32 count, u32 steps,
                               const u64 *__restrict__ ct_in, const u32 *__restrict__ luts, u64 *ws,
                               u32 *status, u32 *counter) {
@@ -34,50 +38,62 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const u32 idx = s_next[slot];
         if (idx >= count) break;
         if (threadIdx.x == 0) s_next[slot ^ 1] = atomicAdd(counter, 1u);
-        brk::br_job<LOGN, kPThreads, lazy, lazy, q1>(jobs[idx], steps, ct_in, luts, ws, status, sm);
+        brk::br_job<LOGN, br_shape(SH).threads, br_shape(SH).rb, lazy, lazy, q1>(jobs[idx], steps, ct_in, luts,
+                                                                                 ws, status, sm);
         __syncthreads();
         slot ^= 1;
     }
 }
 
-template <int LOGN, u32 V>
+template <int LOGN, u32 V, int SH>
 bm_status launch_class(const DevJob *d_jobs, uint32_t count, uint32_t steps, const uint64_t *ct_in,
                        const uint32_t *lut, u64 *ws_acc, u32 *status, u32 *counter, int sms, bool dry,
                        cudaStream_t st) {
-    constexpr size_t smem = brk::Cfg<LOGN, kPThreads>::SMEM;
-    auto kern = k_blind_rotate_persistent<LOGN, V>;
+    using C = brk::Cfg<LOGN, br_shape(SH).threads, br_shape(SH).rb>;
+    auto kern = k_blind_rotate_persistent<LOGN, V, SH>;
     static std::atomic<uint64_t> attr_done{0};
-    int dev = 0;
-    BM_CUDA_TRY(cudaGetDevice(&dev));
-    const uint64_t bit = 1ull << (dev & 63);
-    if (!(attr_done.load() & bit)) {
-        BM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_done.fetch_or(bit);
-    }
+    bm_status s = ensure_smem(kern, C::SMEM, attr_done);
+    if (s != BM_OK) return s;
     if (dry) return BM_OK;
     const u32 grid = (u32)sms < count ? (u32)sms : count;
     BM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(u32), st));
-    kern<<<grid, kPThreads, smem, st>>>(d_jobs, count, steps, (const u64 *)ct_in, lut, ws_acc, status, counter);
+    kern<<<grid, C::kThreads, C::SMEM, st>>>(d_jobs, count, steps, (const u64 *)ct_in, lut, ws_acc, status, counter);
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
 }
 
+// Shapes other than 0 for the variants of Q = c 2^32 + 1 only (as the
+// grouped launches).
+template <int LOGN, u32 V>
+bm_status launch_class_shape(u32 shape, const DevJob *d_jobs, uint32_t count, uint32_t steps, const uint64_t *ct_in,
+                             const uint32_t *lut, u64 *ws_acc, u32 *status, u32 *counter, int sms, bool dry,
+                             cudaStream_t st) {
+    if constexpr ((V & BR_V_QLOW1) && persistent_shape(LOGN, 1))
+        if (shape == 1)
+            return launch_class<LOGN, V, 1>(d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms, dry, st);
+    if constexpr ((V & BR_V_QLOW1) && persistent_shape(LOGN, 4))
+        if (shape == 4)
+            return launch_class<LOGN, V, 4>(d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms, dry, st);
+    return launch_class<LOGN, V, 0>(d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms, dry, st);
+}
+
 template <int LOGN>
-bm_status launch_variant(u32 variant, const DevJob *d_jobs, uint32_t count, uint32_t steps, const uint64_t *ct_in,
-                         const uint32_t *lut, u64 *ws_acc, u32 *status, u32 *counter, int sms, bool dry,
-                         cudaStream_t st) {
+bm_status launch_variant(u32 variant, u32 shape, const DevJob *d_jobs, uint32_t count, uint32_t steps,
+                         const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status, u32 *counter, int sms,
+                         bool dry, cudaStream_t st) {
     switch (variant) {
         case BR_V_LAZY | BR_V_QLOW1:
-            return launch_class<LOGN, BR_V_LAZY | BR_V_QLOW1>(d_jobs, count, steps, ct_in, lut, ws_acc, status,
-                                                             counter, sms, dry, st);
+            return launch_class_shape<LOGN, BR_V_LAZY | BR_V_QLOW1>(shape, d_jobs, count, steps, ct_in, lut, ws_acc,
+                                                                   status, counter, sms, dry, st);
         case BR_V_LAZY:
-            return launch_class<LOGN, BR_V_LAZY>(d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms,
-                                                 dry, st);
+            return launch_class_shape<LOGN, BR_V_LAZY>(shape, d_jobs, count, steps, ct_in, lut, ws_acc, status,
+                                                       counter, sms, dry, st);
         case BR_V_QLOW1:
-            return launch_class<LOGN, BR_V_QLOW1>(d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms,
-                                                  dry, st);
+            return launch_class_shape<LOGN, BR_V_QLOW1>(shape, d_jobs, count, steps, ct_in, lut, ws_acc, status,
+                                                        counter, sms, dry, st);
         default:
-            return launch_class<LOGN, 0>(d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms, dry, st);
+            return launch_class_shape<LOGN, 0>(shape, d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms,
+                                               dry, st);
     }
 }
 
@@ -85,15 +101,21 @@ bm_status launch_variant(u32 variant, const DevJob *d_jobs, uint32_t count, uint
 
 // Ring degrees 1024..4096 only; the host routes other degrees elsewhere.
 // dry: only set the kernel's shared-memory limit (before a stream capture).
-bm_status bm_launch_persistent_class(u32 N, u32 variant, const DevJob *d_jobs, uint32_t count, uint32_t steps,
-                                     const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status,
-                                     u32 *counter, int device, bool dry, cudaStream_t st) {
+bm_status bm_launch_persistent_class(u32 N, u32 variant, u32 shape, const DevJob *d_jobs, uint32_t count,
+                                     uint32_t steps, const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc,
+                                     u32 *status, u32 *counter, int device, bool dry, cudaStream_t st) {
     int sms = 0;
     BM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     switch (N) {
-        case 1024: return launch_variant<10>(variant, d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms, dry, st);
-        case 2048: return launch_variant<11>(variant, d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms, dry, st);
-        case 4096: return launch_variant<12>(variant, d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms, dry, st);
+        case 1024:
+            return launch_variant<10>(variant, shape, d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms,
+                                      dry, st);
+        case 2048:
+            return launch_variant<11>(variant, shape, d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms,
+                                      dry, st);
+        case 4096:
+            return launch_variant<12>(variant, shape, d_jobs, count, steps, ct_in, lut, ws_acc, status, counter, sms,
+                                      dry, st);
         default: return BM_EINVAL;
     }
 }

@@ -50,3 +50,23 @@ def test_job_struct_layout_matches_header():
     from paper_2310_12441_gb300 import api
     assert api.JOB_DTYPE.itemsize == 40
     assert api.JOB_DTYPE.fields["in_off"][1] == 16
+
+
+def test_kernel_shape_table():
+    """The autotuner's kernel shapes that fit each ring degree (host-side
+    query), and refusal of shapes that do not fit."""
+    from paper_2310_12441_gb300 import api
+    api.load()
+    assert set(api.kernel_shapes(1024)) == {0, 1, 2, 3, 4}
+    assert set(api.kernel_shapes(2048)) == {0, 1, 4}
+    assert set(api.kernel_shapes(4096)) == {0, 1}
+    assert set(api.kernel_shapes(256)) == {0}
+    assert api.kernel_shapes(1024)[1] == (8, 1024, 1)
+    with pytest.raises(api.BMError):
+        api.set_kernel_shape(4096, 2)
+    with pytest.raises(api.BMError):
+        api.set_kernel_shape(1000, 0)
+    api.set_kernel_shape(2048, 4)
+    assert api.get_kernel_shape(2048) == 4
+    api.set_kernel_shape(2048, api.SHAPE_DEFAULT)
+    assert api.get_kernel_shape(2048) == 0
