@@ -48,10 +48,8 @@ METRIC = "bootstraps/s on 1 GB300 (batched vs plain, bit-exact); p50/p99 served 
 # the workload (command: bench.py --workload <name> --count 152 under
 # `ncu --set full -k regex:k_blind_rotate`), valid while the kernel sources
 # hash to the captured version.
-KERNEL_SOURCES = ["blind_rotate.cuh", "ntt_reg.cuh", "modarith.cuh", "common.cuh", "bootstrap.cu"]
-CAPTURED_TRAFFIC = {
-    P.BATCH_N1024.name: {"hash": "420eedf6f471f001", "bytes_per_job": (255.315456e6 + 5.345536e6) / 152},
-}
+KERNEL_SOURCES = ["blind_rotate.cuh", "ntt_reg.cuh", "modarith.cuh", "common.cuh", "br_launch.cuh"]
+CAPTURED_TRAFFIC = {}
 
 
 def kernel_hash():
@@ -273,8 +271,11 @@ def kernel_roofline(api, ek, w, jobs, batch, ws, stream, flush, dev, peak, reps=
     cap = CAPTURED_TRAFFIC.get(w.name)
     if cap and kernel_hash() == cap["hash"]:
         traffic = cap["bytes_per_job"] * count
+    shape = api.get_kernel_shape(kp.N)
+    radix, threads, blocks = api.kernel_shapes(kp.N)[shape]
     return {"bound": "alu", "achieved": mm / rot_s / 1e9, "peak": peak / 1e9, "unit": "Gmodmul/s",
             "frac": (mm / rot_s) / peak, "traffic": traffic, "kernel": "k_blind_rotate",
+            "shape": {"id": shape, "ntt_radix": radix, "threads": threads, "blocks_per_sm": blocks},
             "kernel_ms": rot_s * 1e3, "modmuls_per_launch": mm,
             "peak_kind": "measured: the blind rotation's own modular product in a throughput loop"}
 
