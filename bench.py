@@ -49,7 +49,9 @@ METRIC = "bootstraps/s on 1 GB300 (batched vs plain, bit-exact); p50/p99 served 
 # `ncu --set full -k regex:k_blind_rotate`), valid while the kernel sources
 # hash to the captured version.
 KERNEL_SOURCES = ["blind_rotate.cuh", "ntt_reg.cuh", "modarith.cuh", "common.cuh", "br_launch.cuh"]
-CAPTURED_TRAFFIC = {}
+CAPTURED_TRAFFIC = {
+    P.BATCH_N1024.name: {"hash": "99f901e48e20ff91", "bytes_per_job": (255.003392e6 + 5.690112e6) / 152},
+}
 
 
 def kernel_hash():
