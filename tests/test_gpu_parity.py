@@ -130,6 +130,21 @@ def test_key_switch(api, orc, request, fixture):
         assert np.array_equal(got[i], orc.key_switch(kp, lwe[i], ks.ksk)), i
 
 
+@pytest.mark.parametrize("cnt", [1, 30, 40, 77, 160])
+def test_key_switch_every_cluster_split(api, orc, n1024, cnt):
+    """The key switch splits a job over a cluster of S = 8, 4, 2 or 1 blocks,
+    the largest S with cnt S <= SMs (152 SMs: 1 -> 8, 30 -> 4, 40 -> 2,
+    77 and 160 -> 1); every split gives the oracle's words."""
+    kp = n1024.kp
+    rng = np.random.default_rng(cnt)
+    lwe = rng.integers(0, kp.Q, (cnt, kp.N + 1), dtype=np.uint64)
+    d_out = torch.zeros(cnt * (kp.n + 1), dtype=torch.int64, device="cuda")
+    api.bm_key_switch(n1024.ek, api.to_device_u64(lwe), cnt, d_out)
+    got = api.from_device_u64(d_out).reshape(cnt, kp.n + 1)
+    for i in sorted({0, cnt // 2, cnt - 1}):
+        assert np.array_equal(got[i], orc.key_switch(kp, lwe[i], n1024.ksk)), (cnt, i)
+
+
 # --- blind rotation ----------------------------------------------------------------------
 
 def _blind_rotate_gpu(api, ks, jobs, ct, luts, steps):
