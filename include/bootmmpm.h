@@ -334,7 +334,7 @@ bm_status bm_bootstrap_arbitrary(const bm_eval_key *key, uint32_t m, uint32_t t,
  * shape 0.  bm_kernel_shape_info describes shape s at ring degree N
  * (BM_EINVAL when it does not fit).  bm_set_kernel_shape selects the shape
  * that later launches at ring degree N use (BM_SHAPE_DEFAULT: the built-in
- * choice); reusable batches keep the shapes current at bm_batch_create.
+ * choice, shape 1 for N = 1024..4096 and 0 below); reusable batches keep the shapes current at bm_batch_create.
  * The setting is process-wide. */
 #define BM_NUM_SHAPES 5
 #define BM_SHAPE_DEFAULT 0xffffffffu

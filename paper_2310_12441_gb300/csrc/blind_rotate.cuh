@@ -251,7 +251,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     const u32 pc = p / G, pg = p % G;  // its combo within the batch and row within the group
     ntr::Swap sw{sm + (size_t)p * N, sm + (size_t)(C::P + p) * N, 0};
     u64 *dbuf = sm + (size_t)2 * C::P * N;     // [G][4][N] row differences (DSM only)
-    const u64 qb = Q << log2B;                 // Q * B, used when SMALL0
+    const u64 qb = Q << log2B;                 // Q * B, for the exact small first stage (LAZY, not QLOW1)
     const u64 lmask = (1ull << lbits) - 1;     // Karatsuba limb mask
     const u32 ncomb = 4 * lB;
     const size_t rgsw = (size_t)2 * lB * 2 * N;
@@ -375,7 +375,9 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 // The next position's key words for the first PRE combos (all of a
                 // batch of at most 4, half of a larger one) are loaded while the
                 // current position is multiplied.
-                constexpr bool PIPE = C::PPT > 1 && (int)C::kThreads * C::PPT == N;
+                // (not with 1024 threads: at 64 registers the extra words spilled and measured
+                // 4% slower at N = 2048 and 4096)
+                constexpr bool PIPE = C::PPT > 1 && (int)C::kThreads * C::PPT == N && C::kThreads < 1024;
                 constexpr int PRE = CPB <= 4 ? CPB : CPB / 2;
                 u64 bnext[PIPE ? PRE : 1][2];
                 if constexpr (PIPE) {

@@ -452,10 +452,10 @@ bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t
 
 // Kernel shape per ring degree (log2 N = 8..12) used by launches that do
 // not carry their own: the autotuner's choice once it has run, else the
-// measured best of each degree (radix 8 with 1024 threads for N = 1024 and
-// 4096, radix 16 with 512 threads for N = 2048).
-constexpr u32 kDefaultShape[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 1};
-std::atomic<u32> g_shape[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 1};
+// measured best of each degree (radix 8 with 1024 threads for N = 1024,
+// 2048 and 4096; radix 16 with 512 threads below).
+constexpr u32 kDefaultShape[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1};
+std::atomic<u32> g_shape[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1};
 
 struct Shapes {
     u32 s[13];

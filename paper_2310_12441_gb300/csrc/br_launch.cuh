@@ -172,7 +172,7 @@ bm_status launch_br(u32 variant, u32 shape, const DevJob *jobs, uint32_t cnt, u3
     switch (variant) {
         case BR_V_LAZY | BR_V_QLOW1: BM_LAUNCH(true, true, true);
         case BR_V_LAZY: BM_LAUNCH(true, true, false);
-        case BR_V_QLOW1: BM_LAUNCH(false, false, true);
+        case BR_V_QLOW1: BM_LAUNCH(false, true, true);
         default: BM_LAUNCH(false, false, false);
     }
 #undef BM_LAUNCH

@@ -50,21 +50,26 @@ struct DevJob {
 #define BR_V_LAZY 2u    // correction-free forward NTT with an exact first stage
 
 // Arithmetic variant of a key set (BR_V_* flags):
-//  - BR_V_LAZY: the correction-free forward transform needs
-//    (1 + 4 log2 N) Q < 2^64 and its exact first stage
-//    B + Q B + 4 Q (log2 N - 1) < 2^64 with B < 2^32; the correction-free
-//    inverse (with Q = c 2^32 + 1) needs 128 Q < 2^64;
-//  - BR_V_QLOW1: Q = c 2^32 + 1.
+//  - BR_V_QLOW1: Q = c 2^32 + 1;
+//  - BR_V_LAZY: the correction-free forward transform.  With Q = c 2^32 + 1
+//    it needs (1 + 4 log2 N) Q < 2^62 (its outputs go unreduced into the
+//    multiply-accumulate, whose limbs then stay at most 31 bits) and the
+//    correction-free inverse 128 Q < 2^64; otherwise (1 + 4 log2 N) Q < 2^64
+//    and the exact first stage B + Q B + 4 Q (log2 N - 1) < 2^64 with B < 2^32.
 inline u32 choose_variant(const bm_key_params &p) {
     typedef unsigned __int128 u128;
     u32 logN = 0;
     while ((1u << logN) < p.N) logN++;
     const u128 lim = (u128)1 << 64, Q = p.Q, B = (u128)1 << p.log2_B;
     u32 v = 0;
-    if ((1 + 4 * (u128)logN) * Q < lim && p.log2_B <= 31 && B + Q * B + 4 * Q * (logN - 1) < lim &&
-        128 * Q < lim)
+    const bool qlow1 = (p.Q & 0xffffffffull) == 1;
+    if (qlow1) {
+        if ((1 + 4 * (u128)logN) * Q < ((u128)1 << 62) && 128 * Q < lim) v |= BR_V_LAZY;
+        v |= BR_V_QLOW1;
+    } else if ((1 + 4 * (u128)logN) * Q < lim && p.log2_B <= 31 && B + Q * B + 4 * Q * (logN - 1) < lim &&
+               128 * Q < lim) {
         v |= BR_V_LAZY;
-    if ((p.Q & 0xffffffffull) == 1) v |= BR_V_QLOW1;
+    }
     return v;
 }
 
@@ -72,20 +77,25 @@ inline u32 choose_variant(const bm_key_params &p) {
 // value x < xmax and a key word b < Q are split at `lbits` bits, and the
 // products x1 b1, x0 b0, (x0 + x1)(b0 + b1) of a batch of CPB combos are
 // summed in 64-bit registers.  xmax is where the forward transform leaves
-// its outputs (ntr::fwd_to_smem): 3Q (lazy, Q = c 2^32 + 1), 2Q (lazy), Q.
-// lbits = ceil(bits(xmax - 1) / 2); fold_each when CPB times the largest
-// middle product could reach 2^64 (then each combo is folded at once).  The
-// key stores every BSK word b pre-split as (b mod 2^lbits) | (b >> lbits) 2^32.
+// its outputs (ntr::fwd_to_smem): (1 + 4 log2 N) Q (lazy, Q = c 2^32 + 1,
+// unreduced), 2Q (lazy), Q.  lbits = ceil(bits(xmax - 1) / 2); fold_each when
+// CPB times the largest middle product could reach 2^64 (then each combo is
+// folded at once).  The key stores every BSK word b pre-split as
+// (b mod 2^lbits) | (b >> lbits) 2^32.
 inline void limb_plan(const bm_key_params &p, u32 variant, u32 &lbits, u32 &fold_each) {
     typedef unsigned __int128 u128;
-    const u128 xmax = (variant & BR_V_LAZY) ? (u128)((variant & BR_V_QLOW1) ? 3 : 2) * p.Q : (u128)p.Q;
+    u32 logN = 0;
+    while ((1u << logN) < p.N) logN++;
+    const u128 xmax = (variant & BR_V_LAZY) ? ((variant & BR_V_QLOW1) ? (1 + 4 * (u128)logN) : 2) * (u128)p.Q
+                                            : (u128)p.Q;
     u32 bits = 0;
     while (bits < 66 && ((xmax - 1) >> bits)) bits++;
     lbits = (bits + 1) / 2;
     const u128 lim = (u128)1 << lbits;
     const u128 sx = (lim - 1) + ((xmax - 1) >> lbits), sb = (lim - 1) + ((u128)(p.Q - 1) >> lbits);
-    const u32 cpb = 512u / (p.N / 16u);     // brk::Cfg<LOGN, 512>::CPB
-    // (Q < 2^61 keeps sx and sb, the limb sums, below 2^32)
+    const u32 cpb = 512u / (p.N / 16u);     // the largest CPB of any kernel shape
+    // (the variant rules keep xmax and Q below 2^62, so the limb sums sx and
+    // sb stay below 2^32)
     fold_each = (u128)cpb * sx * sb >= ((u128)1 << 64);
 }
 

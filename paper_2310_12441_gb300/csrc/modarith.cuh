@@ -291,6 +291,25 @@ __device__ __forceinline__ void small_bfly(u64 &X, u64 &Y, u64 W, u64 qb) {
         : "l"(W), "l"(qb));
 }
 
+// y W mod Q for a digit y < 2^32 and Q = c 2^32 + 1, in [0, 3Q): the Shoup
+// quotient floor(y W' / 2^64) of W' = s1 2^32 + s0 is floor(y s1 / 2^32) or
+// one more (y s0 / 2^64 < 1), so q = hi(y s1) leaves y W - q Q in [0, 3Q);
+// q < 2^32, so q Q mod 2^64 = q + (q c mod 2^32) 2^32.
+__device__ __forceinline__ u64 small_mul_qlow1(u64 y, u64 W, u64 Wsh, u32 c) {
+    u64 T;
+    asm("{\n\t.reg .u32 y0, w0, w1, s0, s1, q, t0, t1, qc;\n\t.reg .u64 t;\n\t"
+        "cvt.u32.u64 y0, %1;\n\t"
+        "mov.b64 {w0, w1}, %2;\n\tmov.b64 {s0, s1}, %3;\n\t"
+        "mul.hi.u32 q, y0, s1;\n\t"
+        "mul.wide.u32 t, y0, w0;\n\tmov.b64 {t0, t1}, t;\n\t"
+        "mad.lo.u32 t1, y0, w1, t1;\n\t"
+        "mul.lo.u32 qc, q, %4;\n\t"
+        "sub.cc.u32 t0, t0, q;\n\tsubc.u32 t1, t1, qc;\n\t"
+        "mov.b64 %0, {t0, t1};\n\t}"
+        : "=l"(T) : "l"(y), "l"(W), "l"(Wsh), "r"(c));
+    return T;
+}
+
 // v - qe Q with qe = floor((v >> 32) s / 2^32), s = floor(2^64 / Q) < 2^32,
 // Q = c 2^32 + 1: qe is at most 2 below floor(v / Q), result in [0, 3Q).
 __device__ __forceinline__ u64 reduce_est_qlow1(u64 v, u32 s, u32 c) {

@@ -76,10 +76,12 @@ __device__ __forceinline__ void twiddle(const u64 *__restrict__ tp, u32 ti, u64 
 // fits in 64 bits.  Otherwise Harvey's [0, 4Q) invariant is kept, widened to
 // [0, 8Q) with a single correction per butterfly when Q = c 2^32 + 1
 // (bfly_ct_qlow1).
-// SMALL0 (with LAZY): the first stage's inputs are digits below B < 2^32, so
-// W * Y is formed exactly (a 64 x 32-bit product) and left unreduced:
-// X + W Y and X - W Y + Q B, both below B + Q B.  The caller guarantees
-// B + Q B + 4 Q (LOGN - 1) < 2^64.
+// SMALL0: the first stage's inputs are digits below B <= 2^32.  With
+// Q = c 2^32 + 1 the product W Y takes the one-high-product quotient of
+// small_mul_qlow1 ([0, 3Q)), and X + T, X - T + 4Q stay below B + 4Q (within
+// both invariants).  Otherwise (LAZY only) W * Y is formed exactly (a
+// 64 x 32-bit product) and left unreduced: X + W Y and X - W Y + Q B, both
+// below B + Q B; the caller guarantees B + Q B + 4 Q (LOGN - 1) < 2^64.
 template <int LOGN, int RB, int F, int S0, int NST, bool LAZY, bool SMALL0 = false, bool QLOW1 = false,
           bool TWS = false>
 __device__ __forceinline__ void fwd_phase(u64 (&x)[1 << RB], u32 l, const u64 *__restrict__ twp, u64 Q,
@@ -103,7 +105,16 @@ __device__ __forceinline__ void fwd_phase(u64 (&x)[1 << RB], u32 l, const u64 *_
             } else {
                 twiddle<false>(twp, (1u << s) + g, W, Wsh);
             }
-            if constexpr (LAZY && SMALL0 && S0 == 0) {
+            if constexpr (SMALL0 && QLOW1 && S0 == 0) {
+                if (st == 0) {
+                    // digits below B <= 2^32: one high product for the quotient
+                    const u64 X = x[i];
+                    const u64 T = small_mul_qlow1(x[i2], W, Wsh, (u32)(Q >> 32));
+                    x[i] = add64c(X, T);
+                    x[i2] = sub64c(add64c(X, 2 * twoQ), T);
+                    continue;
+                }
+            } else if constexpr (LAZY && SMALL0 && S0 == 0) {
                 if (st == 0) {
                     small_bfly(x[i], x[i2], W, qb);
                     continue;
@@ -240,8 +251,9 @@ __device__ __forceinline__ u64 *fwd_middle(u64 (&x)[1 << RB], Swap &sw, u64 *r, 
 // this thread's polynomial, values below 4Q.  TWS: twp points to a copy of
 // the twiddle pairs in shared memory.  Returns the region that holds
 // the transform in bit-reversed positions, values in [0, Q), or with LAZY
-// only partly reduced for the multiply-accumulate: [0, 3Q) when QLOW1, else
-// [0, 2Q) (swizzled); the caller must __syncthreads() before reading it.
+// left for the multiply-accumulate (whose limbs are planned for it): below
+// (1 + 4 LOGN) Q unreduced when QLOW1, else [0, 2Q) (swizzled); the caller
+// must __syncthreads() before reading it.
 // Every thread of the block calls this (it contains barriers); threads with
 // active == false only take part in the barriers.
 template <int LOGN, int RB, bool LAZY, bool SMALL0 = false, bool QLOW1 = false, bool TWS = false>
@@ -264,10 +276,7 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[1 << RB], Swap &sw, u32 l, 
         for (int i = 0; i < R; i++) {
             u64 v = x[i];
             if constexpr (LAZY && QLOW1) {
-                // Q = c 2^32 + 1 > 2^32, so floor(2^64 / Q) < 2^32 and the
-                // estimate floor((v >> 32) floor(2^64/Q) / 2^32) lies at most
-                // 2 below floor(v / Q): one 32-bit high product, [0, 3Q)
-                v = reduce_est_qlow1(v, (u32)one_sh, (u32)(Q >> 32));
+                // left below (1 + 4 LOGN) Q for the multiply-accumulate
             } else if constexpr (LAZY) {
                 v = v - __umul64hi(v, one_sh) * Q;     // Shoup with w = 1: [0, 2Q)
             } else if constexpr (QLOW1) {

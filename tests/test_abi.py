@@ -69,4 +69,6 @@ def test_kernel_shape_table():
     api.set_kernel_shape(2048, 4)
     assert api.get_kernel_shape(2048) == 4
     api.set_kernel_shape(2048, api.SHAPE_DEFAULT)
-    assert api.get_kernel_shape(2048) == 0
+    assert api.get_kernel_shape(2048) == 1
+    api.set_kernel_shape(256, api.SHAPE_DEFAULT)
+    assert api.get_kernel_shape(256) == 0
