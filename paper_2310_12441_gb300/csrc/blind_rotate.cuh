@@ -179,6 +179,7 @@ struct Cfg {
     static constexpr size_t SMEM = REGIONS + DBYTES + TWBYTES;
     static_assert(G != 1 || SMEM == smem_bytes(LOGN, THREADS, RB), "smem_bytes mirrors Cfg");
     static_assert(P >= 1 && P * T == THREADS, "whole polynomials per batch");
+    static_assert(T <= 32 || P <= 15, "a named barrier per polynomial (ids 1..15)");
     static_assert(SMEM <= 227 * 1024 - 1024, "shared memory per block");
 };
 

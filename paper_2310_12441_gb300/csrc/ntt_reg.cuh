@@ -26,12 +26,23 @@
 // Twiddles come as (w, w') pairs.
 //
 // Shared memory: every polynomial owns two regions of N words and the
-// exchanges alternate between them (Swap), so a region is never rewritten
-// while a slower thread may still read it and each exchange needs a single
-// barrier.  Index idx is stored at word idx ^ ((idx >> RB) & 15), which keeps
-// every phase's accesses (and position-major accesses) free of bank
-// conflicts for R = 8 and 16 (each half-warp touches 16 distinct words
-// modulo 16).
+// exchanges alternate between them (Swap): the store ending phase p goes to
+// the region phase p-1 loaded from.  Index idx is stored at word
+// idx ^ ((idx >> RB) & 15), which keeps every phase's accesses (and
+// position-major accesses) free of bank conflicts for R = 8 and 16 (each
+// half-warp touches 16 distinct words modulo 16).
+//
+// Synchronisation between phases: thread bit t of layout F carries index bit
+// t (t < F) or t + RB (t >= F).  When no warp bit (t >= 5) changes its index
+// bit between the storing and the loading layout (max(F, G) <= 5, or the
+// polynomial fits in one warp), every warp reads back exactly the words it
+// wrote, and __syncwarp() orders the exchange; then no other warp read those
+// words in the previous phase either, so the store after next may reuse the
+// region.  Otherwise the T threads of the polynomial meet at a named barrier
+// (bar.sync 1 + polynomial, T).  The first exchange of a forward transform
+// is always a block barrier: the regions alternate across batches too, and
+// the multiply-accumulate of the previous batch reads the result region of
+// every polynomial, which the second store of the next batch rewrites.
 #pragma once
 #include "modarith.cuh"
 
@@ -55,6 +66,44 @@ struct Swap {
         return d;
     }
 };
+
+// Exchange between a phase storing in layout F and one loading in layout G
+// stays within each warp (see the header).
+template <int LOGN, int RB, int F, int G>
+__host__ __device__ constexpr bool warp_local() {
+    return LOGN - RB <= 5 || (F > G ? F : G) <= 5;
+}
+
+// Barrier of the T = 2^(LOGN-RB) threads of this thread's polynomial
+// (T > 32; polynomial g = threadIdx.x / T uses barrier 1 + g).
+template <int LOGN, int RB>
+__device__ __forceinline__ void group_sync() {
+    constexpr int T = 1 << (LOGN - RB);
+    static_assert(T % 32 == 0, "whole warps per polynomial");
+    asm volatile("bar.sync %0, %1;" ::"r"(1u + threadIdx.x / T), "n"(T) : "memory");
+}
+
+// Orders the exchange from layout F to layout G (BLOCK: a block barrier).
+template <int LOGN, int RB, int F, int G, bool BLOCK = false>
+__device__ __forceinline__ void phase_sync() {
+    if constexpr (BLOCK) {
+        __syncthreads();
+    } else if constexpr (warp_local<LOGN, RB, F, G>()) {
+        __syncwarp();
+    } else {
+        group_sync<LOGN, RB>();
+    }
+}
+
+// Field start of forward phase t (t = 0 .. NPH-1) and of inverse phase t.
+template <int LOGN, int RB>
+__host__ __device__ constexpr int fwd_field(int t) {
+    return t < (LOGN + RB - 1) / RB - 1 ? LOGN - RB * (t + 1) : 0;
+}
+template <int LOGN, int RB>
+__host__ __device__ constexpr int inv_field(int t) {
+    return t < (LOGN + RB - 1) / RB - 1 ? RB * t : LOGN - RB;
+}
 
 // Twiddle pair ti from a table in global memory, or in shared memory (SH).
 template <bool SH = false>
@@ -226,21 +275,21 @@ __device__ __forceinline__ void load_field(u64 (&x)[1 << RB], const u64 *reg, u3
 }
 
 // Middle forward phases PH = 1 .. NPH-2 (field LOGN - RB (PH + 1)); `r` holds
-// the previous phase's layout and the block has passed a barrier since it was
-// written.  Returns the region holding the last middle phase's output.
+// the previous phase's layout and its exchange has been ordered.  Returns the
+// region holding the last middle phase's output.
 template <int LOGN, int RB, int PH, bool LAZY, bool QLOW1, bool TWS>
 __device__ __forceinline__ u64 *fwd_middle(u64 (&x)[1 << RB], Swap &sw, u64 *r, u32 l, bool active,
                                            const u64 *__restrict__ twp, u64 Q, u64 twoQ) {
     constexpr int NPH = (LOGN + RB - 1) / RB;
     if constexpr (PH < NPH - 1) {
-        constexpr int F = LOGN - RB * (PH + 1);
+        constexpr int F = fwd_field<LOGN, RB>(PH), G = fwd_field<LOGN, RB>(PH + 1);
         if (active) {
             load_field<RB, F>(x, r, l);
             fwd_phase<LOGN, RB, F, RB * PH, RB, LAZY, false, QLOW1, TWS>(x, l, twp, Q, twoQ);
         }
         u64 *r2 = sw.take();
         if (active) store_field<RB, F>(x, r2, l);
-        __syncthreads();
+        phase_sync<LOGN, RB, F, G>();
         return fwd_middle<LOGN, RB, PH + 1, LAZY, QLOW1, TWS>(x, sw, r2, l, active, twp, Q, twoQ);
     } else {
         return r;
@@ -255,7 +304,7 @@ __device__ __forceinline__ u64 *fwd_middle(u64 (&x)[1 << RB], Swap &sw, u64 *r, 
 // (1 + 4 LOGN) Q unreduced when QLOW1, else [0, 2Q) (swizzled); the caller
 // must __syncthreads() before reading it.
 // Every thread of the block calls this (it contains barriers); threads with
-// active == false only take part in the barriers.
+// active == false (whole polynomials) only take part in the barriers.
 template <int LOGN, int RB, bool LAZY, bool SMALL0 = false, bool QLOW1 = false, bool TWS = false>
 __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[1 << RB], Swap &sw, u32 l, bool active,
                                             const u64 *__restrict__ twp, u64 Q, u64 one_sh, u64 qb = 0) {
@@ -267,7 +316,7 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[1 << RB], Swap &sw, u32 l, 
     if (active) fwd_phase<LOGN, RB, LOGN - RB, 0, RB, LAZY, SMALL0, QLOW1, TWS>(x, l, twp, Q, twoQ, qb);
     u64 *r = sw.take();
     if (active) store_field<RB, LOGN - RB>(x, r, l);
-    __syncthreads();
+    __syncthreads();      // also orders the previous batch's reads of the result regions
     r = fwd_middle<LOGN, RB, 1, LAZY, QLOW1, TWS>(x, sw, r, l, active, twp, Q, twoQ);
     if (active) {
         load_field<RB, 0>(x, r, l);
@@ -292,13 +341,13 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[1 << RB], Swap &sw, u32 l, 
     return r;
 }
 
-// Middle inverse phases Qp = 1 .. NPH-2 (field RB Qp).
+// Middle inverse phases QP = 1 .. NPH-2 (field RB QP).
 template <int LOGN, int RB, int QP, bool QLOW1, bool TWS, bool LZI>
 __device__ __forceinline__ u64 *inv_middle(u64 (&x)[1 << RB], Swap &sw, u64 *r, u32 l, bool active,
                                            const u64 *__restrict__ itwp, u64 Q, u64 twoQ, u64 one_sh) {
     constexpr int NPH = (LOGN + RB - 1) / RB;
     if constexpr (QP < NPH - 1) {
-        constexpr int F = RB * QP;
+        constexpr int F = inv_field<LOGN, RB>(QP), G = inv_field<LOGN, RB>(QP + 1);
         if (active) {
             load_field<RB, F>(x, r, l);
             inv_phase<LOGN, RB, F, F, RB, QLOW1, TWS, LZI>(x, l, itwp, Q, twoQ);
@@ -309,7 +358,7 @@ __device__ __forceinline__ u64 *inv_middle(u64 (&x)[1 << RB], Swap &sw, u64 *r, 
         }
         u64 *r2 = sw.take();
         if (active) store_field<RB, F>(x, r2, l);
-        __syncthreads();
+        phase_sync<LOGN, RB, F, G>();
         return inv_middle<LOGN, RB, QP + 1, QLOW1, TWS, LZI>(x, sw, r2, l, active, itwp, Q, twoQ, one_sh);
     } else {
         return r;
@@ -318,14 +367,15 @@ __device__ __forceinline__ u64 *inv_middle(u64 (&x)[1 << RB], Swap &sw, u64 *r, 
 
 // Inverse NTT (without N^-1).  On entry region `in` holds the bit-reversed
 // transform (swizzled, values below 2Q) and the block has passed a barrier
-// since it was written; `in` must be the region sw wrote last.  On exit x
-// holds natural-order coefficients l + T i, reduced to [0, Q).  With
-// Q = c 2^32 + 1 the butterflies keep [0, 4Q) with one correction each
-// (bfly_gs_qlow1), or with LZI (Q = c 2^32 + 1 and 128 Q < 2^64) none
-// (bfly_gs_lazy_qlow1 with q64 = 64 Q).  A phase of four stages takes values
-// below 3Q to below 48Q (3Q, 6Q, 12Q, 24Q, 48Q; inputs below Q reach 32Q;
-// three stages stop at 24Q), so U - V + 64Q < 112Q < 2^64; between phases
-// the values are brought back below 3Q by reduce_est_qlow1
+// since it was written; `in` must be the region sw wrote last, and no other
+// polynomial's threads read this polynomial's regions until the caller's next
+// block barrier.  On exit x holds natural-order coefficients l + T i, reduced
+// to [0, Q).  With Q = c 2^32 + 1 the butterflies keep [0, 4Q) with one
+// correction each (bfly_gs_qlow1), or with LZI (Q = c 2^32 + 1 and
+// 128 Q < 2^64) none (bfly_gs_lazy_qlow1 with q64 = 64 Q).  A phase of four
+// stages takes values below 3Q to below 48Q (3Q, 6Q, 12Q, 24Q, 48Q; inputs
+// below Q reach 32Q; three stages stop at 24Q), so U - V + 64Q < 112Q < 2^64;
+// between phases the values are brought back below 3Q by reduce_est_qlow1
 // (one_sh = floor(2^64 / Q)).
 template <int LOGN, int RB, bool QLOW1 = false, bool TWS = false, bool LZI = false>
 __device__ __forceinline__ void inv_from_smem(u64 (&x)[1 << RB], const u64 *in, Swap &sw, u32 l, bool active,
@@ -346,7 +396,7 @@ __device__ __forceinline__ void inv_from_smem(u64 (&x)[1 << RB], const u64 *in, 
     }
     u64 *r = sw.take();
     if (active) store_field<RB, 0>(x, r, l);
-    __syncthreads();
+    phase_sync<LOGN, RB, inv_field<LOGN, RB>(0), inv_field<LOGN, RB>(1)>();
     r = inv_middle<LOGN, RB, 1, QLOW1, TWS, LZI>(x, sw, r, l, active, itwp, Q, twoQ, one_sh);
     if (active) {
         load_field<RB, LOGN - RB>(x, r, l);
