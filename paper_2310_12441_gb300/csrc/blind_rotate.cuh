@@ -529,10 +529,8 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
             if (active) {
                 const u64 *sp = sums + (size_t)u * N;
 #pragma unroll
-                for (int i = 0; i < R; i++) {
-                    const u32 idx = l + C::T * i;
-                    in[ntr::swz<RB>(idx)] = sp[idx];
-                }
+                for (int i = 0; i < R; i++) x[i] = sp[l + C::T * i];
+                ntr::store_field<RB, LOGN - RB>(x, in, l);    // index l + T i
             }
             __syncthreads();
             ntr::inv_from_smem<LOGN, RB, QLOW1, C::DSM, LAZY && QLOW1>(x, in, sw, l, active, itw_use, Q, mq.one_sh);

@@ -262,16 +262,27 @@ __device__ __forceinline__ u32 inv_twiddle_slot(u32 pos) {
     return (1u << s) + ((high << (s - sh)) | j);
 }
 
+// Field accesses.  fidx(l, i) = fidx(l, 0) | (i << F) with disjoint bits, and
+// the swizzle is linear over XOR on disjoint bits, so word
+// swz(fidx(l, i)) = swz(fidx(l, 0)) ^ swz(i << F): one byte offset per thread
+// XOR a compile-time constant per register (the address arithmetic stays on
+// the integer ALU, off the multiplier the butterflies need).
 template <int RB, int F>
 __device__ __forceinline__ void store_field(const u64 (&x)[1 << RB], u64 *reg, u32 l) {
+    char *b = reinterpret_cast<char *>(reg);
+    const u32 sb = swz<RB>(fidx<RB, F>(l, 0)) << 3;
 #pragma unroll
-    for (int i = 0; i < (1 << RB); i++) reg[swz<RB>(fidx<RB, F>(l, i))] = x[i];
+    for (int i = 0; i < (1 << RB); i++)
+        *reinterpret_cast<u64 *>(b + (sb ^ (swz<RB>((u32)i << F) << 3))) = x[i];
 }
 
 template <int RB, int F>
 __device__ __forceinline__ void load_field(u64 (&x)[1 << RB], const u64 *reg, u32 l) {
+    const char *b = reinterpret_cast<const char *>(reg);
+    const u32 sb = swz<RB>(fidx<RB, F>(l, 0)) << 3;
 #pragma unroll
-    for (int i = 0; i < (1 << RB); i++) x[i] = reg[swz<RB>(fidx<RB, F>(l, i))];
+    for (int i = 0; i < (1 << RB); i++)
+        x[i] = *reinterpret_cast<const u64 *>(b + (sb ^ (swz<RB>((u32)i << F) << 3)));
 }
 
 // Middle forward phases PH = 1 .. NPH-2 (field LOGN - RB (PH + 1)); `r` holds
