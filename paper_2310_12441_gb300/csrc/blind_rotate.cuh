@@ -257,19 +257,28 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     const u32 ncomb = 4 * lB;
     const size_t rgsw = (size_t)2 * lB * 2 * N;
 
-    // bv: a key word stored pre-split, low limb | high limb << 32.  The three
-    // limb products accumulate with mad.wide.u32 (one multiplier instruction
-    // each, the addition included).
-    auto kara = [&](u64 xv, u64 bv, u64 &kh, u64 &kl, u64 &km) {
-        const u32 x0 = (u32)(xv & lmask), x1 = (u32)(xv >> lbits);
-        asm("{\n\t.reg .u32 b0, b1, xs, bs;\n\t"
-            "mov.b64 {b0, b1}, %5;\n\t"
-            "add.u32 xs, %3, %4;\n\tadd.u32 bs, b0, b1;\n\t"
-            "mad.wide.u32 %0, %4, b1, %0;\n\t"
-            "mad.wide.u32 %1, %3, b0, %1;\n\t"
-            "mad.wide.u32 %2, xs, bs, %2;\n\t}"
-            : "+l"(kh), "+l"(kl), "+l"(km)
-            : "r"(x0), "r"(x1), "l"(bv));
+    // Limb products of a transform value xv with the key words bv0, bv1 of
+    // the two columns (each stored pre-split, low limb | high limb << 32):
+    // x1 b1, x0 b0 and (x0 + x1)(b0 + b1) accumulate with mad.wide.u32 (one
+    // multiplier instruction each, the addition included).  xv's limbs are
+    // split once (funnel shift: lbits <= 31 and xv < 2^(lbits + 32)) for both.
+    const u32 lmask32 = (u32)lmask;
+    auto kara2 = [&](u64 xv, u64 bv0, u64 bv1, u64 (&kh)[2], u64 (&kl)[2], u64 (&km)[2]) {
+        asm("{\n\t.reg .u32 v0, v1, x0, x1, xs, a0, a1, as, c0, c1, cs;\n\t"
+            "mov.b64 {v0, v1}, %6;\n\t"
+            "shf.r.clamp.b32 x1, v0, v1, %9;\n\t"
+            "and.b32 x0, v0, %10;\n\t"
+            "add.u32 xs, x0, x1;\n\t"
+            "mov.b64 {a0, a1}, %7;\n\tadd.u32 as, a0, a1;\n\t"
+            "mov.b64 {c0, c1}, %8;\n\tadd.u32 cs, c0, c1;\n\t"
+            "mad.wide.u32 %0, x1, a1, %0;\n\t"
+            "mad.wide.u32 %1, x0, a0, %1;\n\t"
+            "mad.wide.u32 %2, xs, as, %2;\n\t"
+            "mad.wide.u32 %3, x1, c1, %3;\n\t"
+            "mad.wide.u32 %4, x0, c0, %4;\n\t"
+            "mad.wide.u32 %5, xs, cs, %5;\n\t}"
+            : "+l"(kh[0]), "+l"(kl[0]), "+l"(km[0]), "+l"(kh[1]), "+l"(kl[1]), "+l"(km[1])
+            : "l"(xv), "l"(bv0), "l"(bv1), "r"(lbits), "r"(lmask32));
     };
 
     u64 *cur = acc0, *nxt = acc1;
@@ -446,8 +455,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                                         for (int g = 0; g < G; g++) {
                                             if (G == 1 || r0 + g < m) {
                                                 const u64 xv = slots[(size_t)((k0 + cc) * G + g) * N + sq];
-                                                kara(xv, kv[cc][0], kh[g][0], kl[g][0], km[g][0]);
-                                                kara(xv, kv[cc][1], kh[g][1], kl[g][1], km[g][1]);
+                                                kara2(xv, kv[cc][0], kv[cc][1], kh[g], kl[g], km[g]);
                                             }
                                         }
                                 }
@@ -465,8 +473,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                                 for (int g = 0; g < G; g++) {
                                     if (G == 1 || r0 + g < m) {
                                         const u64 xv = slots[(size_t)(cc * G + g) * N + sq];
-                                        kara(xv, bv[cc][0], kh[g][0], kl[g][0], km[g][0]);
-                                        kara(xv, bv[cc][1], kh[g][1], kl[g][1], km[g][1]);
+                                        kara2(xv, bv[cc][0], bv[cc][1], kh[g], kl[g], km[g]);
                                     }
                                 }
                             }
@@ -478,8 +485,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                                 for (int g = 0; g < G; g++) {
                                     if (G == 1 || r0 + g < m) {
                                         const u64 xv = slots[(size_t)(cc * G + g) * N + sq];
-                                        kara(xv, b0, kh[g][0], kl[g][0], km[g][0]);
-                                        kara(xv, b1, kh[g][1], kl[g][1], km[g][1]);
+                                        kara2(xv, b0, b1, kh[g], kl[g], km[g]);
                                     }
                                 }
                                 if (fold_each) fold();
