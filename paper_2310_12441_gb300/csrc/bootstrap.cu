@@ -253,11 +253,11 @@ __global__ void k_lwe_sub(const u64 *__restrict__ x, const u64 *__restrict__ y, 
     }
 }
 
-// Throughput probe: independent Shoup multiplication chains per thread.
 // Throughput probe of the blind rotation's own modular product: the
-// three-product Shoup multiplication for Q = c 2^32 + 1 on 32-bit
-// add-with-carry chains (shoup3_qlow1_lazy), eight independent chains per
-// thread; every output in [0, 4Q) is a valid next input.
+// three-product Shoup multiplication for Q = c 2^32 + 1 (shoup3_qlow1_lazy:
+// seven multiplier instructions, 22 multiplier-pipe cycles per warp), eight
+// independent chains per thread; every output in [0, 4Q) is a valid next
+// input.
 __global__ void k_modmul_probe(u64 *out, u32 iters, u32 c, u64 w, u64 wsh) {
     u64 x0 = threadIdx.x + 1, x1 = x0 + 7, x2 = x0 + 13, x3 = x0 + 29;
     u64 x4 = x0 + 31, x5 = x0 + 37, x6 = x0 + 41, x7 = x0 + 43;

@@ -63,27 +63,18 @@ __device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 wsh, u64 Q) {
     return reduce_2q(mul_shoup_lazy(a, w, wsh, Q), Q);
 }
 
-// 64-bit additions written on 32-bit halves with add-with-carry, so that
-// they run on the integer ALU (left to itself the compiler may form the high
-// word with a multiply-add, which takes the multiplier pipe the modular
-// products need).
+// 64-bit additions as single 64-bit integer instructions (sm_103a adds 64-bit
+// words in one integer-ALU instruction; written out so that they stay off
+// the multiplier pipe the modular products need).
 __device__ __forceinline__ u64 add64c(u64 a, u64 b) {
     u64 r;
-    asm("{\n\t.reg .u32 a0, a1, b0, b1;\n\t"
-        "mov.b64 {a0, a1}, %1;\n\tmov.b64 {b0, b1}, %2;\n\t"
-        "add.cc.u32 a0, a0, b0;\n\taddc.u32 a1, a1, b1;\n\t"
-        "mov.b64 %0, {a0, a1};\n\t}"
-        : "=l"(r) : "l"(a), "l"(b));
+    asm("add.u64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
 
 __device__ __forceinline__ u64 sub64c(u64 a, u64 b) {
     u64 r;
-    asm("{\n\t.reg .u32 a0, a1, b0, b1;\n\t"
-        "mov.b64 {a0, a1}, %1;\n\tmov.b64 {b0, b1}, %2;\n\t"
-        "sub.cc.u32 a0, a0, b0;\n\tsubc.u32 a1, a1, b1;\n\t"
-        "mov.b64 %0, {a0, a1};\n\t}"
-        : "=l"(r) : "l"(a), "l"(b));
+    asm("sub.u64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
 
@@ -102,15 +93,12 @@ __device__ __forceinline__ u64 csub64(u64 x, u64 c) {
 
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 Q) { return csub64(add64c(a, b), Q); }
 
-// a - b mod Q for a, b in [0, Q): a - b, plus Q when it borrowed.
+// a - b mod Q for a, b in [0, Q): a - b, plus Q when a < b (a 64-bit
+// compare and select; no borrow word, which would take a multiplier slot).
 __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 Q) {
     u64 r;
-    asm("{\n\t.reg .u32 a0, a1, b0, b1, q0, q1, m;\n\t"
-        "mov.b64 {a0, a1}, %1;\n\tmov.b64 {b0, b1}, %2;\n\tmov.b64 {q0, q1}, %3;\n\t"
-        "sub.cc.u32 a0, a0, b0;\n\tsubc.cc.u32 a1, a1, b1;\n\tsubc.u32 m, 0, 0;\n\t"
-        "and.b32 q0, q0, m;\n\tand.b32 q1, q1, m;\n\t"
-        "add.cc.u32 a0, a0, q0;\n\taddc.u32 a1, a1, q1;\n\t"
-        "mov.b64 %0, {a0, a1};\n\t}"
+    asm("{\n\t.reg .u64 d, q;\n\t.reg .pred p;\n\t"
+        "setp.lo.u64 p, %1, %2;\n\tsub.u64 d, %1, %2;\n\tselp.b64 q, %3, 0, p;\n\tadd.u64 %0, d, q;\n\t}"
         : "=l"(r) : "l"(a), "l"(b), "l"(Q));
     return r;
 }
@@ -123,29 +111,16 @@ __device__ __forceinline__ void mac128(u64 &lo, u64 &hi, u64 a, u64 b) {
         : "l"(a), "l"(b));
 }
 
-// (hi:lo) += a, exact 128-bit accumulation of a 64-bit value (a 32-bit
-// add-with-carry chain).
+// (hi:lo) += a, exact 128-bit accumulation of a 64-bit value (64-bit
+// add-with-carry on the integer ALU).
 __device__ __forceinline__ void add128(u64 &lo, u64 &hi, u64 a) {
-    asm("{\n\t.reg .u32 l0, l1, h0, h1, a0, a1;\n\t"
-        "mov.b64 {l0, l1}, %0;\n\tmov.b64 {h0, h1}, %1;\n\tmov.b64 {a0, a1}, %2;\n\t"
-        "add.cc.u32 l0, l0, a0;\n\taddc.cc.u32 l1, l1, a1;\n\t"
-        "addc.cc.u32 h0, h0, 0;\n\taddc.u32 h1, h1, 0;\n\t"
-        "mov.b64 %0, {l0, l1};\n\tmov.b64 %1, {h0, h1};\n\t}"
-        : "+l"(lo), "+l"(hi)
-        : "l"(a));
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(a));
 }
 
 // (hi:lo) += v << sh for 0 < sh < 64.
 __device__ __forceinline__ void add128_shl(u64 &lo, u64 &hi, u64 v, u32 sh) {
     const u64 vl = v << sh, vh = v >> (64 - sh);
-    asm("{\n\t.reg .u32 l0, l1, h0, h1, a0, a1, b0, b1;\n\t"
-        "mov.b64 {l0, l1}, %0;\n\tmov.b64 {h0, h1}, %1;\n\t"
-        "mov.b64 {a0, a1}, %2;\n\tmov.b64 {b0, b1}, %3;\n\t"
-        "add.cc.u32 l0, l0, a0;\n\taddc.cc.u32 l1, l1, a1;\n\t"
-        "addc.cc.u32 h0, h0, b0;\n\taddc.u32 h1, h1, b1;\n\t"
-        "mov.b64 %0, {l0, l1};\n\tmov.b64 %1, {h0, h1};\n\t}"
-        : "+l"(lo), "+l"(hi)
-        : "l"(vl), "l"(vh));
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(vl), "l"(vh));
 }
 
 // (hi 2^64 + lo) mod Q, any hi, lo < 2^64:  hi * (2^64 mod Q) + lo, each term
@@ -180,75 +155,46 @@ __device__ __forceinline__ u64 reduce128q(u64 lo, u64 hi, const ModQ &m) {
     }
 }
 
-// Lazy forward (Cooley-Tukey) butterfly for Q = c 2^32 + 1, written on 32-bit
-// halves so that the additions run as add-with-carry on the integer ALU and
-// only the seven products of the three-product Shoup quotient, the low word of
-// Y W and q Q use the multiplier:
+// Lazy forward (Cooley-Tukey) butterfly for Q = c 2^32 + 1: the seven
+// products of the three-product Shoup quotient, the low word of Y W and q Q
+// take the multiplier; the additions are single 64-bit ALU instructions:
 //   q = y1 s1 + hi(y1 s0) + hi(y0 s1)           (Wsh = s1:s0, Y = y1:y0)
 //   T = Y W - q Q  mod 2^64, in [0, 4Q)          (q Q = q + (q0 c) 2^32)
 //   X <- X + T,  Y <- X + 4Q - T.
 __device__ __forceinline__ void bfly_lazy_qlow1(u64 &X, u64 &Y, u64 W, u64 Wsh, u32 c, u64 fourQ) {
     asm("{\n\t"
-        ".reg .u32 x0, x1, y0, y1, w0, w1, s0, s1, h1, h2, q0, q1, t0, t1, u0, u1, f0, f1, qc;\n\t"
-        ".reg .u64 q, t, hw;\n\t"
-        "mov.b64 {x0, x1}, %0;\n\t"
-        "mov.b64 {y0, y1}, %1;\n\t"
-        "mov.b64 {w0, w1}, %2;\n\t"
-        "mov.b64 {s0, s1}, %3;\n\t"
-        "mov.b64 {f0, f1}, %5;\n\t"
-        "mul.hi.u32 h1, y1, s0;\n\t"
-        "mul.hi.u32 h2, y0, s1;\n\t"
-        "mov.b64 hw, {h1, 0};\n\t"
-        "mad.wide.u32 q, y1, s1, hw;\n\t"
+        ".reg .u32 y0, y1, w0, w1, s0, s1, h1, h2, q0, q1, t0, t1, qc;\n\t"
+        ".reg .u64 q, t, hw, h2w, qq, x;\n\t"
+        "mov.b64 {y0, y1}, %1;\n\tmov.b64 {w0, w1}, %2;\n\tmov.b64 {s0, s1}, %3;\n\t"
+        "mul.hi.u32 h1, y1, s0;\n\tmul.hi.u32 h2, y0, s1;\n\t"
+        "mov.b64 hw, {h1, 0};\n\tmad.wide.u32 q, y1, s1, hw;\n\t"
+        "mov.b64 h2w, {h2, 0};\n\tadd.u64 q, q, h2w;\n\t"
         "mov.b64 {q0, q1}, q;\n\t"
-        "add.cc.u32 q0, q0, h2;\n\t"
-        "addc.u32 q1, q1, 0;\n\t"
-        "mul.wide.u32 t, y0, w0;\n\t"
-        "mov.b64 {t0, t1}, t;\n\t"
-        "mad.lo.u32 t1, y0, w1, t1;\n\t"
-        "mad.lo.u32 t1, y1, w0, t1;\n\t"
+        "mul.wide.u32 t, y0, w0;\n\tmov.b64 {t0, t1}, t;\n\t"
+        "mad.lo.u32 t1, y0, w1, t1;\n\tmad.lo.u32 t1, y1, w0, t1;\n\t"
         "mad.lo.u32 qc, q0, %4, q1;\n\t"
-        "sub.cc.u32 t0, t0, q0;\n\t"
-        "subc.u32 t1, t1, qc;\n\t"
-        "add.cc.u32 u0, x0, t0;\n\t"
-        "addc.u32 u1, x1, t1;\n\t"
-        "add.cc.u32 x0, x0, f0;\n\t"
-        "addc.u32 x1, x1, f1;\n\t"
-        "sub.cc.u32 x0, x0, t0;\n\t"
-        "subc.u32 x1, x1, t1;\n\t"
-        "mov.b64 %0, {u0, u1};\n\t"
-        "mov.b64 %1, {x0, x1};\n\t"
-        "}"
+        "mov.b64 t, {t0, t1};\n\tmov.b64 qq, {q0, qc};\n\tsub.u64 t, t, qq;\n\t"
+        "mov.b64 x, %0;\n\tadd.u64 %0, x, t;\n\tadd.u64 x, x, %5;\n\tsub.u64 %1, x, t;\n\t}"
         : "+l"(X), "+l"(Y)
         : "l"(W), "l"(Wsh), "r"(c), "l"(fourQ));
 }
 
-// Three-product Shoup product for Q = c 2^32 + 1 on 32-bit halves (see
-// bfly_lazy_qlow1): Y W - q Q mod 2^64 in [0, 4Q).
+// Three-product Shoup product for Q = c 2^32 + 1 (see bfly_lazy_qlow1):
+// Y W - q Q mod 2^64 in [0, 4Q).
 __device__ __forceinline__ u64 shoup3_qlow1_lazy(u64 Y, u64 W, u64 Wsh, u32 c) {
     u64 T;
     asm("{\n\t"
         ".reg .u32 y0, y1, w0, w1, s0, s1, h1, h2, q0, q1, t0, t1, qc;\n\t"
-        ".reg .u64 q, t, hw;\n\t"
-        "mov.b64 {y0, y1}, %1;\n\t"
-        "mov.b64 {w0, w1}, %2;\n\t"
-        "mov.b64 {s0, s1}, %3;\n\t"
-        "mul.hi.u32 h1, y1, s0;\n\t"
-        "mul.hi.u32 h2, y0, s1;\n\t"
-        "mov.b64 hw, {h1, 0};\n\t"
-        "mad.wide.u32 q, y1, s1, hw;\n\t"
+        ".reg .u64 q, t, hw, h2w, qq;\n\t"
+        "mov.b64 {y0, y1}, %1;\n\tmov.b64 {w0, w1}, %2;\n\tmov.b64 {s0, s1}, %3;\n\t"
+        "mul.hi.u32 h1, y1, s0;\n\tmul.hi.u32 h2, y0, s1;\n\t"
+        "mov.b64 hw, {h1, 0};\n\tmad.wide.u32 q, y1, s1, hw;\n\t"
+        "mov.b64 h2w, {h2, 0};\n\tadd.u64 q, q, h2w;\n\t"
         "mov.b64 {q0, q1}, q;\n\t"
-        "add.cc.u32 q0, q0, h2;\n\t"
-        "addc.u32 q1, q1, 0;\n\t"
-        "mul.wide.u32 t, y0, w0;\n\t"
-        "mov.b64 {t0, t1}, t;\n\t"
-        "mad.lo.u32 t1, y0, w1, t1;\n\t"
-        "mad.lo.u32 t1, y1, w0, t1;\n\t"
+        "mul.wide.u32 t, y0, w0;\n\tmov.b64 {t0, t1}, t;\n\t"
+        "mad.lo.u32 t1, y0, w1, t1;\n\tmad.lo.u32 t1, y1, w0, t1;\n\t"
         "mad.lo.u32 qc, q0, %4, q1;\n\t"
-        "sub.cc.u32 t0, t0, q0;\n\t"
-        "subc.u32 t1, t1, qc;\n\t"
-        "mov.b64 %0, {t0, t1};\n\t"
-        "}"
+        "mov.b64 t, {t0, t1};\n\tmov.b64 qq, {q0, qc};\n\tsub.u64 %0, t, qq;\n\t}"
         : "=l"(T)
         : "l"(Y), "l"(W), "l"(Wsh), "r"(c));
     return T;
@@ -278,15 +224,11 @@ __device__ __forceinline__ void bfly_gs_qlow1(u64 &U, u64 &V, u64 W, u64 Wsh, u3
 // formed exactly, W y = w0 y + (w1 y) 2^32, and left unreduced:
 // X <- X + W y, Y <- X - W y + qb (qb = Q B >= W y).
 __device__ __forceinline__ void small_bfly(u64 &X, u64 &Y, u64 W, u64 qb) {
-    asm("{\n\t.reg .u32 x0, x1, y0, y1, w0, w1, t0, t1, b0, b1, u0, u1;\n\t.reg .u64 t;\n\t"
-        "mov.b64 {x0, x1}, %0;\n\tmov.b64 {y0, y1}, %1;\n\t"
-        "mov.b64 {w0, w1}, %2;\n\tmov.b64 {b0, b1}, %3;\n\t"
+    asm("{\n\t.reg .u32 y0, w0, w1, t0, t1;\n\t.reg .u64 t, x;\n\t"
+        "cvt.u32.u64 y0, %1;\n\tmov.b64 {w0, w1}, %2;\n\t"
         "mul.wide.u32 t, w0, y0;\n\tmov.b64 {t0, t1}, t;\n\t"
-        "mad.lo.u32 t1, w1, y0, t1;\n\t"
-        "add.cc.u32 u0, x0, t0;\n\taddc.u32 u1, x1, t1;\n\t"
-        "add.cc.u32 x0, x0, b0;\n\taddc.u32 x1, x1, b1;\n\t"
-        "sub.cc.u32 x0, x0, t0;\n\tsubc.u32 x1, x1, t1;\n\t"
-        "mov.b64 %0, {u0, u1};\n\tmov.b64 %1, {x0, x1};\n\t}"
+        "mad.lo.u32 t1, w1, y0, t1;\n\tmov.b64 t, {t0, t1};\n\t"
+        "mov.b64 x, %0;\n\tadd.u64 %0, x, t;\n\tadd.u64 x, x, %3;\n\tsub.u64 %1, x, t;\n\t}"
         : "+l"(X), "+l"(Y)
         : "l"(W), "l"(qb));
 }
@@ -297,15 +239,14 @@ __device__ __forceinline__ void small_bfly(u64 &X, u64 &Y, u64 W, u64 qb) {
 // q < 2^32, so q Q mod 2^64 = q + (q c mod 2^32) 2^32.
 __device__ __forceinline__ u64 small_mul_qlow1(u64 y, u64 W, u64 Wsh, u32 c) {
     u64 T;
-    asm("{\n\t.reg .u32 y0, w0, w1, s0, s1, q, t0, t1, qc;\n\t.reg .u64 t;\n\t"
+    asm("{\n\t.reg .u32 y0, w0, w1, s0, s1, q, t0, t1, qc;\n\t.reg .u64 t, qq;\n\t"
         "cvt.u32.u64 y0, %1;\n\t"
         "mov.b64 {w0, w1}, %2;\n\tmov.b64 {s0, s1}, %3;\n\t"
         "mul.hi.u32 q, y0, s1;\n\t"
         "mul.wide.u32 t, y0, w0;\n\tmov.b64 {t0, t1}, t;\n\t"
         "mad.lo.u32 t1, y0, w1, t1;\n\t"
         "mul.lo.u32 qc, q, %4;\n\t"
-        "sub.cc.u32 t0, t0, q;\n\tsubc.u32 t1, t1, qc;\n\t"
-        "mov.b64 %0, {t0, t1};\n\t}"
+        "mov.b64 t, {t0, t1};\n\tmov.b64 qq, {q, qc};\n\tsub.u64 %0, t, qq;\n\t}"
         : "=l"(T) : "l"(y), "l"(W), "l"(Wsh), "r"(c));
     return T;
 }
@@ -314,12 +255,11 @@ __device__ __forceinline__ u64 small_mul_qlow1(u64 y, u64 W, u64 Wsh, u32 c) {
 // Q = c 2^32 + 1: qe is at most 2 below floor(v / Q), result in [0, 3Q).
 __device__ __forceinline__ u64 reduce_est_qlow1(u64 v, u32 s, u32 c) {
     u64 r;
-    asm("{\n\t.reg .u32 v0, v1, qe, qc;\n\t"
+    asm("{\n\t.reg .u32 v0, v1, qe, qc;\n\t.reg .u64 qq;\n\t"
         "mov.b64 {v0, v1}, %1;\n\t"
         "mul.hi.u32 qe, v1, %2;\n\t"
         "mul.lo.u32 qc, qe, %3;\n\t"
-        "sub.cc.u32 v0, v0, qe;\n\tsubc.u32 v1, v1, qc;\n\t"
-        "mov.b64 %0, {v0, v1};\n\t}"
+        "mov.b64 qq, {qe, qc};\n\tsub.u64 %0, %1, qq;\n\t}"
         : "=l"(r) : "l"(v), "r"(s), "r"(c));
     return r;
 }
