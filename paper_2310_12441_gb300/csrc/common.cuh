@@ -50,7 +50,7 @@ struct DevJob {
 #define BR_V_LAZY 2u    // correction-free forward NTT with an exact first stage
 
 // Arithmetic variant of a key set (BR_V_* flags):
-//  - BR_V_QLOW1: Q = c 2^32 + 1;
+//  - BR_V_QLOW1: Q = c 2^32 + 1 < 2^60;
 //  - BR_V_LAZY: the correction-free forward transform.  With Q = c 2^32 + 1
 //    it needs (1 + 4 log2 N) Q < 2^62 (its outputs go unreduced into the
 //    multiply-accumulate, whose limbs then stay at most 31 bits) and the
@@ -62,7 +62,8 @@ inline u32 choose_variant(const bm_key_params &p) {
     while ((1u << logN) < p.N) logN++;
     const u128 lim = (u128)1 << 64, Q = p.Q, B = (u128)1 << p.log2_B;
     u32 v = 0;
-    const bool qlow1 = (p.Q & 0xffffffffull) == 1;
+    // (Q < 2^60 keeps every value the Q = c 2^32 + 1 butterflies correct below 2^63)
+    const bool qlow1 = (p.Q & 0xffffffffull) == 1 && p.Q < (1ull << 60);
     if (qlow1) {
         if ((1 + 4 * (u128)logN) * Q < ((u128)1 << 62) && 128 * Q < lim) v |= BR_V_LAZY;
         v |= BR_V_QLOW1;

@@ -93,6 +93,20 @@ __device__ __forceinline__ u64 csub64(u64 x, u64 c) {
 
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 Q) { return csub64(add64c(a, b), Q); }
 
+// csub64 for x, c < 2^63: the sign of x - c decides (Q = c 2^32 + 1 keys have
+// Q < 2^60, so every value their butterflies correct is below 8Q <= 2^63).
+__device__ __forceinline__ u64 csub63(u64 x, u64 c) {
+    u64 r;
+    asm("{\n\t.reg .u32 x0, x1, c0, c1, d0, d1;\n\t.reg .pred p;\n\t"
+        "mov.b64 {x0, x1}, %1;\n\tmov.b64 {c0, c1}, %2;\n\t"
+        "sub.cc.u32 d0, x0, c0;\n\tsubc.u32 d1, x1, c1;\n\t"
+        "setp.lt.s32 p, d1, 0;\n\t"
+        "selp.b32 x0, x0, d0, p;\n\tselp.b32 x1, x1, d1, p;\n\t"
+        "mov.b64 %0, {x0, x1};\n\t}"
+        : "=l"(r) : "l"(x), "l"(c));
+    return r;
+}
+
 // a - b mod Q for a, b in [0, Q): a - b, plus Q when a < b (a 64-bit
 // compare and select; no borrow word, which would take a multiplier slot).
 __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 Q) {
@@ -146,9 +160,9 @@ __device__ __forceinline__ u64 reduce128q(u64 lo, u64 hi, const ModQ &m) {
         const u64 x = shoup3_lazy<true>(hi, m.r64, m.r64_sh, Q);
         const u32 qe = __umulhi((u32)(lo >> 32), (u32)m.one_sh);
         u64 s = x + (lo - times_q<true>(qe, Q));
-        if (s >= 2 * m.two_Q) s -= 2 * m.two_Q;
-        if (s >= m.two_Q) s -= m.two_Q;
-        if (s >= Q) s -= Q;
+        s = csub63(s, 2 * m.two_Q);
+        s = csub63(s, m.two_Q);
+        s = csub63(s, Q);
         return s;
     } else {
         return reduce128(lo, hi, m);
@@ -201,11 +215,11 @@ __device__ __forceinline__ u64 shoup3_qlow1_lazy(u64 Y, u64 W, u64 Wsh, u32 c) {
 }
 
 // Forward butterfly with one correction for Q = c 2^32 + 1 (Harvey's method
-// with the invariant widened to [0, 8Q), which Q < 2^61 allows):
+// with the invariant widened to [0, 8Q), which Q < 2^60 keeps below 2^63):
 // X' = X mod 4Q in [0, 4Q), T = Y W mod Q in [0, 4Q) uncorrected;
 // X <- X' + T, Y <- X' + 4Q - T, both in [0, 8Q).
 __device__ __forceinline__ void bfly_ct_qlow1(u64 &X, u64 &Y, u64 W, u64 Wsh, u32 c, u64 fourQ) {
-    const u64 Xr = csub64(X, fourQ);
+    const u64 Xr = csub63(X, fourQ);
     const u64 T = shoup3_qlow1_lazy(Y, W, Wsh, c);
     X = add64c(Xr, T);
     Y = sub64c(add64c(Xr, fourQ), T);
@@ -215,7 +229,7 @@ __device__ __forceinline__ void bfly_ct_qlow1(u64 &X, u64 &Y, u64 W, u64 Wsh, u3
 // values in [0, 4Q): U <- (U + V) mod 4Q, V <- (U - V + 4Q) W mod Q in
 // [0, 4Q) uncorrected (the Shoup input stays below 8Q < 2^64).
 __device__ __forceinline__ void bfly_gs_qlow1(u64 &U, u64 &V, u64 W, u64 Wsh, u32 c, u64 fourQ) {
-    const u64 u = csub64(add64c(U, V), fourQ);
+    const u64 u = csub63(add64c(U, V), fourQ);
     V = shoup3_qlow1_lazy(sub64c(add64c(U, fourQ), V), W, Wsh, c);
     U = u;
 }

@@ -340,7 +340,7 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[1 << RB], Swap &sw, u32 l, 
             } else if constexpr (LAZY) {
                 v = v - __umul64hi(v, one_sh) * Q;     // Shoup with w = 1: [0, 2Q)
             } else if constexpr (QLOW1) {
-                v = csub64(csub64(csub64(v, 2 * twoQ), twoQ), Q);     // [0, 8Q) -> [0, Q)
+                v = csub63(csub63(csub63(v, 2 * twoQ), twoQ), Q);     // [0, 8Q) -> [0, Q)
             } else {
                 v = csub64(csub64(v, twoQ), Q);
             }
@@ -416,7 +416,7 @@ __device__ __forceinline__ void inv_from_smem(u64 (&x)[1 << RB], const u64 *in, 
         between();
 #pragma unroll
         for (int i = 0; i < R; i++)
-            x[i] = (LZI || QLOW1) ? csub64(csub64(x[i], twoQ), Q) : csub64(x[i], Q);
+            x[i] = (LZI || QLOW1) ? csub63(csub63(x[i], twoQ), Q) : csub64(x[i], Q);
     }
 }
 
