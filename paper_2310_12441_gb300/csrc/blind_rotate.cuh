@@ -48,6 +48,36 @@ __device__ __forceinline__ void set_status(u32 *status, bm_status code) {
     atomicCAS(status, 0u, (u32)(-code));
 }
 
+// Shared-memory mbarrier (arrive/wait split barrier of the block's threads).
+__device__ __forceinline__ u32 smem_u32(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(u64 *bar, u32 count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Arrival (release: this thread's earlier shared-memory reads are ordered
+// before any access that a waiter makes after its wait).
+__device__ __forceinline__ void mbar_arrive(u64 *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// Waits (acquire) for the completion of the phase with this parity.  Bounded:
+// after 2^24 polls (each may suspend the thread for a while) it sets
+// BM_ETIMEDOUT in the status word and returns, so a missing arrival can
+// never hang the GPU (every thread of the block arrives once per phase, so
+// this does not happen in a correct launch).
+__device__ __forceinline__ void mbar_wait(u64 *bar, u32 parity, u32 *status) {
+    const u32 a = smem_u32(bar);
+    for (u32 it = 0; it < (1u << 24); it++) {
+        u32 ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (ok) return;
+    }
+    set_status(status, BM_ETIMEDOUT);
+}
+
 // Negacyclic table check: entries in [0, t) and f(k + t/2) = -f(k) mod t.
 static __device__ bool lut_is_negacyclic(const u32 *__restrict__ lut, u32 t) {
     __shared__ int bad;
@@ -236,6 +266,17 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
         return;
     }
     const u32 *gpre = J.gS ? status + J.gpre : nullptr;
+    // Split barrier between a batch's multiply-accumulate and the next
+    // transform's second store.  Every thread arrives once after the
+    // barrier below (completing phase 0, as if a multiply-accumulate had
+    // preceded the first batch) and once after each multiply-accumulate, and
+    // waits once per batch, on the parity of the phase its previous arrival
+    // belongs to; the block barrier before each multiply-accumulate keeps
+    // every thread within one phase of the others.
+    __shared__ __align__(8) u64 mac_bar_word;
+    u64 *const mac_bar = &mac_bar_word;
+    if (tid == 0) mbar_init(mac_bar, blockDim.x);
+    u32 mac_parity = 0;
     acc_init(acc0, lut, ct[n] % qp, m, t, N, Q, J.gS, J.gSinv, gpre, crank, csize);
     // forward twiddle pairs to shared memory (read by every transform), in
     // the transposed order of ntr::twiddle_slot
@@ -246,6 +287,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
         tws[2 * pos + 1] = __ldg(twp + 2 * src + 1);
     }
     if (split) cluster_sync(); else __syncthreads();
+    mbar_arrive(mac_bar);
 
     const u32 p = tid / C::T;          // polynomial slot within a batch
     const u32 l = tid % C::T;          // thread within the polynomial
@@ -369,11 +411,20 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                         }
                     }
                 }
-                u64 *out = ntr::fwd_to_smem<LOGN, RB, LAZY, SMALL0, QLOW1, true>(x, sw, l, active, tws, Q, mq.one_sh, qb);
+                // The second store of the transform rewrites the region every
+                // thread read in the previous batch's multiply-accumulate: wait
+                // for all of the block's arrivals after those reads (a split
+                // barrier, so a thread that has finished its multiply-accumulate
+                // goes on with this batch's digits and first transform phase).
+                auto wait_mac = [&]() {
+                    mbar_wait(mac_bar, mac_parity, status);
+                    mac_parity ^= 1u;
+                };
+                u64 *out = ntr::fwd_to_smem<LOGN, RB, LAZY, SMALL0, QLOW1, true>(x, sw, l, active, tws, Q,
+                                                                                 mq.one_sh, qb, wait_mac);
                 // regions of the other polynomials of the batch sit at stride N;
                 // polynomial cc G + g holds combo c0 + cc of row r0 + g
                 const u64 *slots = out - (size_t)p * N;
-                __syncthreads();
                 // --- multiply-accumulate against the key rows of the batch's combos
                 // (combo c = (sign, component, digit) is key row c of the step).
                 // Limb products x1 b1, x0 b0 and (x0 + x1)(b0 + b1) are summed over
@@ -390,6 +441,10 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 constexpr bool PIPE = C::PPT > 1 && (int)C::kThreads * C::PPT == N && C::kThreads < 1024;
                 constexpr int PRE = CPB <= 4 ? CPB : CPB / 2;
                 u64 bnext[PIPE ? PRE : 1][2];
+                // (Requesting the first key words before the barrier below, to
+                // overlap their latency with the wait, measured slower with 1024
+                // threads: the held words spilled.)
+                __syncthreads();
                 if constexpr (PIPE) {
                     if (full) {
 #pragma unroll
@@ -494,6 +549,8 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                         fold();
                     }
                 }
+                // this thread's reads of the batch's results are done
+                mbar_arrive(mac_bar);
             }
             // --- reduced row sums (NTT domain) to the sum buffer
 #pragma unroll

@@ -39,10 +39,11 @@
 // wrote, and __syncwarp() orders the exchange; then no other warp read those
 // words in the previous phase either, so the store after next may reuse the
 // region.  Otherwise the T threads of the polynomial meet at a named barrier
-// (bar.sync 1 + polynomial, T).  The first exchange of a forward transform
-// is always a block barrier: the regions alternate across batches too, and
+// (bar.sync 1 + polynomial, T).  The regions alternate across batches too:
 // the multiply-accumulate of the previous batch reads the result region of
-// every polynomial, which the second store of the next batch rewrites.
+// every polynomial, which the second store of the next forward transform
+// rewrites, so the caller orders those reads before that store (the
+// before2 hook of fwd_to_smem).
 #pragma once
 #include "modarith.cuh"
 
@@ -288,12 +289,13 @@ __device__ __forceinline__ void load_field(u64 (&x)[1 << RB], const u64 *reg, u3
 // Middle forward phases PH = 1 .. NPH-2 (field LOGN - RB (PH + 1)); `r` holds
 // the previous phase's layout and its exchange has been ordered.  Returns the
 // region holding the last middle phase's output.
-template <int LOGN, int RB, int PH, bool LAZY, bool QLOW1, bool TWS>
+template <int LOGN, int RB, int PH, bool LAZY, bool QLOW1, bool TWS, class Before2>
 __device__ __forceinline__ u64 *fwd_middle(u64 (&x)[1 << RB], Swap &sw, u64 *r, u32 l, bool active,
-                                           const u64 *__restrict__ twp, u64 Q, u64 twoQ) {
+                                           const u64 *__restrict__ twp, u64 Q, u64 twoQ, Before2 &before2) {
     constexpr int NPH = (LOGN + RB - 1) / RB;
     if constexpr (PH < NPH - 1) {
         constexpr int F = fwd_field<LOGN, RB>(PH), G = fwd_field<LOGN, RB>(PH + 1);
+        if constexpr (PH == 1) before2();
         if (active) {
             load_field<RB, F>(x, r, l);
             fwd_phase<LOGN, RB, F, RB * PH, RB, LAZY, false, QLOW1, TWS>(x, l, twp, Q, twoQ);
@@ -301,7 +303,7 @@ __device__ __forceinline__ u64 *fwd_middle(u64 (&x)[1 << RB], Swap &sw, u64 *r, 
         u64 *r2 = sw.take();
         if (active) store_field<RB, F>(x, r2, l);
         phase_sync<LOGN, RB, F, G>();
-        return fwd_middle<LOGN, RB, PH + 1, LAZY, QLOW1, TWS>(x, sw, r2, l, active, twp, Q, twoQ);
+        return fwd_middle<LOGN, RB, PH + 1, LAZY, QLOW1, TWS>(x, sw, r2, l, active, twp, Q, twoQ, before2);
     } else {
         return r;
     }
@@ -314,11 +316,20 @@ __device__ __forceinline__ u64 *fwd_middle(u64 (&x)[1 << RB], Swap &sw, u64 *r, 
 // left for the multiply-accumulate (whose limbs are planned for it): below
 // (1 + 4 LOGN) Q unreduced when QLOW1, else [0, 2Q) (swizzled); the caller
 // must __syncthreads() before reading it.
+// The regions alternate across transforms, so the second store of this
+// transform goes to the region that held the previous transform's result.
+// before2() runs in every thread before that store, between the first
+// exchange and the second phase (where the thread holds no values in
+// registers): the caller makes it wait until every reader of the previous
+// results is done.  The first store goes to the other region, which only
+// this polynomial's threads used last, before the caller's barrier that
+// precedes its reads.
 // Every thread of the block calls this (it contains barriers); threads with
 // active == false (whole polynomials) only take part in the barriers.
-template <int LOGN, int RB, bool LAZY, bool SMALL0 = false, bool QLOW1 = false, bool TWS = false>
+template <int LOGN, int RB, bool LAZY, bool SMALL0, bool QLOW1, bool TWS, class Before2>
 __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[1 << RB], Swap &sw, u32 l, bool active,
-                                            const u64 *__restrict__ twp, u64 Q, u64 one_sh, u64 qb = 0) {
+                                            const u64 *__restrict__ twp, u64 Q, u64 one_sh, u64 qb,
+                                            Before2 &&before2) {
     constexpr int R = 1 << RB;
     constexpr int NPH = (LOGN + RB - 1) / RB;
     static_assert(LOGN >= 8 && LOGN <= 12, "ring degree 256..4096");
@@ -327,8 +338,9 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[1 << RB], Swap &sw, u32 l, 
     if (active) fwd_phase<LOGN, RB, LOGN - RB, 0, RB, LAZY, SMALL0, QLOW1, TWS>(x, l, twp, Q, twoQ, qb);
     u64 *r = sw.take();
     if (active) store_field<RB, LOGN - RB>(x, r, l);
-    __syncthreads();      // also orders the previous batch's reads of the result regions
-    r = fwd_middle<LOGN, RB, 1, LAZY, QLOW1, TWS>(x, sw, r, l, active, twp, Q, twoQ);
+    phase_sync<LOGN, RB, fwd_field<LOGN, RB>(0), fwd_field<LOGN, RB>(1)>();
+    r = fwd_middle<LOGN, RB, 1, LAZY, QLOW1, TWS>(x, sw, r, l, active, twp, Q, twoQ, before2);
+    if constexpr (NPH == 2) before2();
     if (active) {
         load_field<RB, 0>(x, r, l);
         fwd_phase<LOGN, RB, 0, RB * (NPH - 1), LOGN - RB * (NPH - 1), LAZY, false, QLOW1, TWS>(x, l, twp, Q, twoQ);
