@@ -57,7 +57,7 @@ typedef int32_t bm_status;
  * shape (m, t) with the same N. */
 typedef struct bm_key_params {
     uint32_t n;         /* LWE dimension */
-    uint32_t N;         /* ring degree, power of two, 256..4096 */
+    uint32_t N;         /* ring degree, power of two, 256..8192 */
     uint32_t log2_B;    /* blind-rotation gadget base B = 2^log2_B */
     uint32_t l_B;       /* gadget digits, B^l_B >= Q, 2 <= l_B <= 8 */
     uint32_t log2_Bks;  /* key-switching base B_ks = 2^log2_Bks, <= 8 */
@@ -88,7 +88,7 @@ typedef struct bm_eval_key bm_eval_key;
 /* One bootstrapping job (Definition 1): ciphertext, table, shape, key set. */
 typedef struct bm_job {
     uint32_t key;       /* index into the key array of the call */
-    uint32_t m;         /* polynomials in the test vector, 1..1024 */
+    uint32_t m;         /* polynomials in the test vector, 1..1024, with 2Nm <= 2^23 */
     uint32_t t;         /* plaintext modulus, even, 2 <= t <= 2Nm */
     uint32_t reserved;  /* must be 0 */
     uint64_t in_off;    /* element offset of the input LWE_{n,2Nm} (n+1 words) */
@@ -326,15 +326,15 @@ bm_status bm_bootstrap_arbitrary(const bm_eval_key *key, uint32_t m, uint32_t t,
  * `radix` coefficients of a polynomial each in the transforms, with
  * `blocks_per_sm` blocks resident per SM:
  *   0: radix 16, 512 threads, 1 block/SM     (every ring degree)
- *   1: radix 8, 1024 threads, 1 block/SM     (N = 1024..4096)
+ *   1: radix 8, 1024 threads, 1 block/SM     (N = 1024..8192)
  *   2: radix 16, 256 threads, 2 blocks/SM    (N = 1024)
  *   3: radix 8, 512 threads, 2 blocks/SM     (N = 1024)
- *   4: radix 8, 512 threads, 1 block/SM      (N = 1024, 2048)
+ *   4: radix 8, 512 threads, 1 block/SM      (N = 1024..4096)
  * Shapes 1..4 are compiled for keys whose Q = c 2^32 + 1; other keys run
  * shape 0.  bm_kernel_shape_info describes shape s at ring degree N
  * (BM_EINVAL when it does not fit).  bm_set_kernel_shape selects the shape
  * that later launches at ring degree N use (BM_SHAPE_DEFAULT: the built-in
- * choice, shape 1 for N = 1024..4096 and 0 below); reusable batches keep the shapes current at bm_batch_create.
+ * choice, shape 1 for N = 1024..8192 and 0 below); reusable batches keep the shapes current at bm_batch_create.
  * The setting is process-wide. */
 #define BM_NUM_SHAPES 5
 #define BM_SHAPE_DEFAULT 0xffffffffu

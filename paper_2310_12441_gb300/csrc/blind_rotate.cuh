@@ -178,10 +178,16 @@ namespace brk {
 __host__ __device__ constexpr size_t smem_regions(int logn, int threads, int rb) {
     return 2ull * (threads / ((1 << logn) >> rb)) * (1ull << logn) * 8;
 }
+__host__ __device__ constexpr size_t smem_dbytes(int logn, int threads, int rb) {
+    return smem_regions(logn, threads, rb) + 4ull * (1ull << logn) * 8 <= 200 * 1024 ? 4ull * (1ull << logn) * 8 : 0;
+}
+__host__ __device__ constexpr size_t smem_twbytes(int logn, int threads, int rb) {
+    return smem_regions(logn, threads, rb) + smem_dbytes(logn, threads, rb) + 16ull * (1ull << logn) <= 226 * 1024
+               ? 16ull * (1ull << logn)
+               : 0;
+}
 __host__ __device__ constexpr size_t smem_bytes(int logn, int threads, int rb) {
-    return smem_regions(logn, threads, rb) +
-           (smem_regions(logn, threads, rb) + 4ull * (1ull << logn) * 8 <= 200 * 1024 ? 4ull * (1ull << logn) * 8 : 0) +
-           16ull * (1ull << logn);
+    return smem_regions(logn, threads, rb) + smem_dbytes(logn, threads, rb) + smem_twbytes(logn, threads, rb);
 }
 
 // Block shape for a ring of 2^LOGN coefficients run by THREADS threads,
@@ -202,10 +208,20 @@ struct Cfg {
     // key words a thread holds at once in the multiply-accumulate (fewer
     // where a 1024-thread block leaves 64 registers per thread)
     static constexpr int KC = kThreads >= 1024 && CPB > 4 ? 4 : CPB;
+    // Row sums per position: exact 128-bit registers, reduced once per row;
+    // with 8 or more positions per thread (N = 8192) they stay in the job's
+    // sum buffer instead (L2), reduced mod Q and updated by their owner
+    // after every batch (128-bit sums of 8 positions in registers spilled
+    // kilobytes per thread).
+    static constexpr bool RED = PPT >= 8;
+    static constexpr int PPTR = RED ? 1 : PPT;                    // positions of the register sums
     static constexpr size_t REGIONS = 2ull * P * N * 8;            // two regions per polynomial
     static constexpr bool DSM = REGIONS + 4ull * G * N * 8 <= 200 * 1024;   // row differences in smem
     static constexpr size_t DBYTES = DSM ? 4ull * G * N * 8 : 0;
-    static constexpr size_t TWBYTES = 16ull * N;                    // forward twiddle pairs
+    // forward twiddle pairs in shared memory when they fit (N <= 4096),
+    // else read through L1 from the key's table (N = 8192)
+    static constexpr size_t TWBYTES = smem_twbytes(LOGN, THREADS, RB);
+    static constexpr bool TWSM = TWBYTES != 0;
     static constexpr size_t SMEM = REGIONS + DBYTES + TWBYTES;
     static_assert(G != 1 || SMEM == smem_bytes(LOGN, THREADS, RB), "smem_bytes mirrors Cfg");
     static_assert(P >= 1 && P * T == THREADS, "whole polynomials per batch");
@@ -281,7 +297,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     // forward twiddle pairs to shared memory (read by every transform), in
     // the transposed order of ntr::twiddle_slot
     u64 *tws = sm + (C::REGIONS + C::DBYTES) / 8;
-    for (u32 pos = tid; pos < (u32)N; pos += C::kThreads) {
+    for (u32 pos = tid; C::TWSM && pos < (u32)N; pos += C::kThreads) {
         const u32 src = ntr::twiddle_slot<LOGN, RB>(pos);
         tws[2 * pos] = __ldg(twp + 2 * src);
         tws[2 * pos + 1] = __ldg(twp + 2 * src + 1);
@@ -329,11 +345,24 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
         const u32 ak = (u32)(ct[k] % qp);
         const u64 *bsk_k = K->bsk + (size_t)k * 2 * rgsw;
         for (u32 r0 = crank * G; r0 < m; r0 += G * csize) {
-            u64 lo[G][2][C::PPT], hi[G][2][C::PPT];
+            u64 lo[G][2][C::PPTR], hi[G][2][C::PPTR];
 #pragma unroll
             for (int g = 0; g < G; g++)
 #pragma unroll
-                for (int j = 0; j < C::PPT; j++) lo[g][0][j] = hi[g][0][j] = lo[g][1][j] = hi[g][1][j] = 0;
+                for (int j = 0; j < C::PPTR; j++) lo[g][0][j] = hi[g][0][j] = lo[g][1][j] = hi[g][1][j] = 0;
+            if constexpr (C::RED) {
+                // this thread's row sums start at zero in the sum buffer
+#pragma unroll
+                for (int g = 0; g < G; g++)
+#pragma unroll
+                    for (int j = 0; j < C::PPT; j++) {
+                        const u32 q = tid + C::kThreads * j;
+                        if (r0 + g < m && q < (u32)N) {
+                            sums[((size_t)(r0 + g) * 2) * N + q] = 0;
+                            sums[((size_t)(r0 + g) * 2 + 1) * N + q] = 0;
+                        }
+                    }
+            }
             // source row and monomial exponent of P(c) for rows r0 + g,
             // c = -a_k (sign 0) and c = a_k (sign 1), Eq. (ex1:BPc)
             u32 rsrc[G][2], rexp[G][2];
@@ -420,8 +449,9 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                     mbar_wait(mac_bar, mac_parity, status);
                     mac_parity ^= 1u;
                 };
-                u64 *out = ntr::fwd_to_smem<LOGN, RB, LAZY, SMALL0, QLOW1, true>(x, sw, l, active, tws, Q,
-                                                                                 mq.one_sh, qb, wait_mac);
+                u64 *out = ntr::fwd_to_smem<LOGN, RB, LAZY, SMALL0, QLOW1, C::TWSM>(x, sw, l, active,
+                                                                                    C::TWSM ? tws : twp, Q,
+                                                                                    mq.one_sh, qb, wait_mac);
                 // regions of the other polynomials of the batch sit at stride N;
                 // polynomial cc G + g holds combo c0 + cc of row r0 + g
                 const u64 *slots = out - (size_t)p * N;
@@ -467,9 +497,19 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                             for (int g = 0; g < G; g++)
 #pragma unroll
                                 for (int col = 0; col < 2; col++) {
-                                    add128(lo[g][col][j], hi[g][col][j], kl[g][col]);
-                                    add128_shl(lo[g][col][j], hi[g][col][j], km[g][col] - kh[g][col] - kl[g][col], lbits);
-                                    add128_shl(lo[g][col][j], hi[g][col][j], kh[g][col], 2 * lbits);
+                                    if constexpr (C::RED) {
+                                        u64 *sp = sums + ((size_t)(r0 + g) * 2 + col) * N + q;
+                                        u64 l0 = *sp, h0 = 0;
+                                        add128(l0, h0, kl[g][col]);
+                                        add128_shl(l0, h0, km[g][col] - kh[g][col] - kl[g][col], lbits);
+                                        add128_shl(l0, h0, kh[g][col], 2 * lbits);
+                                        *sp = reduce128q<QLOW1>(l0, h0, mq);
+                                    } else {
+                                        add128(lo[g][col][j], hi[g][col][j], kl[g][col]);
+                                        add128_shl(lo[g][col][j], hi[g][col][j], km[g][col] - kh[g][col] - kl[g][col],
+                                                   lbits);
+                                        add128_shl(lo[g][col][j], hi[g][col][j], kh[g][col], 2 * lbits);
+                                    }
                                     kh[g][col] = kl[g][col] = km[g][col] = 0;
                                 }
                         };
@@ -561,8 +601,10 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                     for (int j = 0; j < C::PPT; j++) {
                         const u32 q = tid + C::kThreads * j;
                         if (q < (u32)N) {
-                            sums[((size_t)r * 2) * N + q] = reduce128q<QLOW1>(lo[g][0][j], hi[g][0][j], mq);
-                            sums[((size_t)r * 2 + 1) * N + q] = reduce128q<QLOW1>(lo[g][1][j], hi[g][1][j], mq);
+                            if constexpr (!C::RED) {     // (RED: already there)
+                                sums[((size_t)r * 2) * N + q] = reduce128q<QLOW1>(lo[g][0][j], hi[g][0][j], mq);
+                                sums[((size_t)r * 2 + 1) * N + q] = reduce128q<QLOW1>(lo[g][1][j], hi[g][1][j], mq);
+                            }
                         }
                     }
                 }

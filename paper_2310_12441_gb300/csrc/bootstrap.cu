@@ -334,7 +334,7 @@ bm_status validate_jobs(const bm_eval_key *const *keys, uint32_t n_keys, const b
         const bm_job &j = jobs[i];
         if (j.key >= n_keys || j.reserved) return BM_EINVAL;
         const bm_eval_key *k = keys[j.key];
-        if (j.m < 1 || j.m > BM_MAX_M) return BM_EINVAL;
+        if (j.m < 1 || j.m > BM_MAX_M || 2ull * k->p.N * j.m > BM_MAX_QP) return BM_EINVAL;
         if (j.t < 2 || (j.t & 1) || (u64)j.t > 2ull * k->p.N * j.m) return BM_EINVAL;
     }
     return BM_OK;
@@ -450,18 +450,18 @@ bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t
     return BM_OK;
 }
 
-// Kernel shape per ring degree (log2 N = 8..12) used by launches that do
+// Kernel shape per ring degree (log2 N = 8..13) used by launches that do
 // not carry their own: the autotuner's choice once it has run, else the
-// measured best of each degree (radix 8 with 1024 threads for N = 1024,
-// 2048 and 4096; radix 16 with 512 threads below).
-constexpr u32 kDefaultShape[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1};
-std::atomic<u32> g_shape[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1};
+// measured best of each degree (radix 8 with 1024 threads for N = 1024 ..
+// 8192; radix 16 with 512 threads below).
+constexpr u32 kDefaultShape[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1};
+std::atomic<u32> g_shape[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1};
 
 struct Shapes {
-    u32 s[13];
+    u32 s[14];
     static Shapes current() {
         Shapes x;
-        for (int i = 0; i < 13; i++) x.s[i] = g_shape[i].load();
+        for (int i = 0; i < 14; i++) x.s[i] = g_shape[i].load();
         return x;
     }
 };
@@ -488,6 +488,9 @@ bm_status launch_br_any(u32 N, u32 variant, u32 shape, const DevJob *jobs, uint3
                                       status, st, dry);
         case 4096:
             return bm_launch_br_n4096(variant, shape, jobs, cnt, mmax, max_cluster, steps, ct_in, lut, ws_acc,
+                                      status, st, dry);
+        case 8192:
+            return bm_launch_br_n8192(variant, shape, jobs, cnt, mmax, max_cluster, steps, ct_in, lut, ws_acc,
                                       status, st, dry);
         default: return BM_EINVAL;
     }
@@ -851,7 +854,7 @@ ArbLayout arb_layout(const bm_eval_key *key, uint32_t m, uint32_t t, uint32_t co
 }  // namespace
 
 extern "C" size_t bm_arbitrary_workspace_bytes(const bm_eval_key *key, uint32_t m, uint32_t t, uint32_t count) {
-    if (!key || !count || m < 1 || m > BM_MAX_M || t < 2 || (t & 1)) return 0;
+    if (!key || !count || m < 1 || m > BM_MAX_M || 2ull * key->p.N * m > BM_MAX_QP || t < 2 || (t & 1)) return 0;
     return arb_layout(key, m, t, count).total;
 }
 
@@ -861,7 +864,8 @@ extern "C" bm_status bm_bootstrap_arbitrary(const bm_eval_key *key, uint32_t m, 
     if (!key || !d_f || !d_ct_in || !d_ct_out || !d_ws || ((uintptr_t)d_ws & 255)) return BM_EINVAL;
     if (!count) return BM_OK;
     const uint64_t qp = 2ull * key->p.N * m;
-    if (m < 1 || m > BM_MAX_M || t < 2 || (t & 1) || 2ull * t > qp || q < 2ull * t || q >= key->p.Q)
+    if (m < 1 || m > BM_MAX_M || qp > BM_MAX_QP || t < 2 || (t & 1) || 2ull * t > qp || q < 2ull * t ||
+        q >= key->p.Q)
         return BM_EINVAL;
     const ArbLayout L = arb_layout(key, m, t, count);
     if (ws_bytes < L.total) return BM_EWORKSPACE;
@@ -1060,7 +1064,7 @@ extern "C" void bm_batch_free(bm_batch *b) {
 
 extern "C" bm_status bm_kernel_shape_info(uint32_t shape, uint32_t N, uint32_t *radix, uint32_t *threads,
                                           uint32_t *blocks_per_sm) {
-    if (N < 256 || N > 4096 || (N & (N - 1)) || shape >= BM_NUM_SHAPES) return BM_EINVAL;
+    if (N < 256 || N > BM_MAX_N || (N & (N - 1)) || shape >= BM_NUM_SHAPES) return BM_EINVAL;
     if (shape != 0 && (N < 1024 || !br_shape_fits((int)log2u(N), (int)shape))) return BM_EINVAL;
     const BrShape b = br_shape((int)shape);
     if (radix) *radix = 1u << b.rb;
@@ -1070,7 +1074,7 @@ extern "C" bm_status bm_kernel_shape_info(uint32_t shape, uint32_t N, uint32_t *
 }
 
 extern "C" bm_status bm_set_kernel_shape(uint32_t N, uint32_t shape) {
-    if (N < 256 || N > 4096 || (N & (N - 1))) return BM_EINVAL;
+    if (N < 256 || N > BM_MAX_N || (N & (N - 1))) return BM_EINVAL;
     const u32 l = log2u(N);
     if (shape == BM_SHAPE_DEFAULT) shape = kDefaultShape[l];
     if (bm_kernel_shape_info(shape, N, nullptr, nullptr, nullptr) != BM_OK) return BM_EINVAL;
@@ -1079,7 +1083,7 @@ extern "C" bm_status bm_set_kernel_shape(uint32_t N, uint32_t shape) {
 }
 
 extern "C" bm_status bm_get_kernel_shape(uint32_t N, uint32_t *shape) {
-    if (N < 256 || N > 4096 || (N & (N - 1)) || !shape) return BM_EINVAL;
+    if (N < 256 || N > BM_MAX_N || (N & (N - 1)) || !shape) return BM_EINVAL;
     *shape = g_shape[log2u(N)].load();
     return BM_OK;
 }

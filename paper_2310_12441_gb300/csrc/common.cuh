@@ -9,6 +9,8 @@
 
 #define BM_MAX_L_B 8
 #define BM_MAX_M 1024   // q' = 2Nm <= 2^23 (u32 arithmetic on exponents)
+#define BM_MAX_N 8192   // largest ring degree (one polynomial per thread block)
+#define BM_MAX_QP (1u << 23)
 
 // Device-resident description of one evaluation key set.  One copy lives in
 // device memory (owned by the bm_eval_key) so jobs can point at it.
@@ -156,6 +158,9 @@ bm_status bm_launch_br_n2048(u32 variant, u32 shape, const DevJob *jobs, uint32_
                              u32 steps, const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status,
                              cudaStream_t st, bool dry);
 bm_status bm_launch_br_n4096(u32 variant, u32 shape, const DevJob *jobs, uint32_t cnt, u32 mmax, u32 max_cluster,
+                             u32 steps, const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status,
+                             cudaStream_t st, bool dry);
+bm_status bm_launch_br_n8192(u32 variant, u32 shape, const DevJob *jobs, uint32_t cnt, u32 mmax, u32 max_cluster,
                              u32 steps, const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status,
                              cudaStream_t st, bool dry);
 

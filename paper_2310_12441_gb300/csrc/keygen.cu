@@ -72,7 +72,7 @@ static u32 bitrev(u32 x, u32 bits) {
 
 bm_status bm_check_key_params(const bm_key_params *p) {
     if (!p) return BM_EINVAL;
-    if (p->N < 256 || p->N > 4096 || (p->N & (p->N - 1))) return BM_EINVAL;
+    if (p->N < 256 || p->N > BM_MAX_N || (p->N & (p->N - 1))) return BM_EINVAL;
     if (p->n == 0 || p->n > 4096) return BM_EINVAL;
     if (p->l_B < 2 || p->l_B > BM_MAX_L_B || p->log2_B == 0 || p->log2_B > 32) return BM_EINVAL;
     if (p->log2_Bks == 0 || p->log2_Bks > 8 || p->l_ks == 0 || p->l_ks > 16 ||
@@ -374,6 +374,7 @@ static bm_status keygen_impl(const bm_key_params *params, const int8_t *s, const
     BM_CUDA_TRY(cudaMemcpy(d_z.p, z, N, cudaMemcpyHostToDevice));
 
     const u32 threads = N / 2 < 512 ? N / 2 : 512;
+    BM_CUDA_TRY(cudaFuncSetAttribute(k_ntt_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(N * 8)));
     k_ntt_z<<<1, threads, N * 8>>>((const int8_t *)d_z.p, d_zhat, K);
     BM_CUDA_TRY(cudaGetLastError());
 

@@ -332,7 +332,7 @@ __device__ __forceinline__ u64 *fwd_to_smem(u64 (&x)[1 << RB], Swap &sw, u32 l, 
                                             Before2 &&before2) {
     constexpr int R = 1 << RB;
     constexpr int NPH = (LOGN + RB - 1) / RB;
-    static_assert(LOGN >= 8 && LOGN <= 12, "ring degree 256..4096");
+    static_assert(LOGN >= 8 && LOGN <= 13, "ring degree 256..8192");
     static_assert(RB == 3 || RB == 4, "radix 8 or 16");
     const u64 twoQ = 2 * Q;
     if (active) fwd_phase<LOGN, RB, LOGN - RB, 0, RB, LAZY, SMALL0, QLOW1, TWS>(x, l, twp, Q, twoQ, qb);

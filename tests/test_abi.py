@@ -59,8 +59,10 @@ def test_kernel_shape_table():
     api.load()
     assert set(api.kernel_shapes(1024)) == {0, 1, 2, 3, 4}
     assert set(api.kernel_shapes(2048)) == {0, 1, 4}
-    assert set(api.kernel_shapes(4096)) == {0, 1}
+    assert set(api.kernel_shapes(4096)) == {0, 1, 4}
+    assert set(api.kernel_shapes(8192)) == {0, 1}
     assert set(api.kernel_shapes(256)) == {0}
+    assert api.kernel_shapes(16384) == {}
     assert api.kernel_shapes(1024)[1] == (8, 1024, 1)
     with pytest.raises(api.BMError):
         api.set_kernel_shape(4096, 2)
