@@ -179,7 +179,9 @@ __host__ __device__ constexpr size_t smem_regions(int logn, int threads, int rb)
     return 2ull * (threads / ((1 << logn) >> rb)) * (1ull << logn) * 8;
 }
 __host__ __device__ constexpr size_t smem_dbytes(int logn, int threads, int rb) {
-    return smem_regions(logn, threads, rb) + 4ull * (1ull << logn) * 8 <= 200 * 1024 ? 4ull * (1ull << logn) * 8 : 0;
+    return smem_regions(logn, threads, rb) + 4ull * (1ull << logn) * 8 <= 200 * 1024 ? 4ull * (1ull << logn) * 8
+         : smem_regions(logn, threads, rb) + (1ull << logn) * 8 <= 200 * 1024  ? (1ull << logn) * 8
+                                                                               : 0;
 }
 __host__ __device__ constexpr size_t smem_twbytes(int logn, int threads, int rb) {
     return smem_regions(logn, threads, rb) + smem_dbytes(logn, threads, rb) + 16ull * (1ull << logn) <= 226 * 1024
@@ -217,7 +219,10 @@ struct Cfg {
     static constexpr int PPTR = RED ? 1 : PPT;                    // positions of the register sums
     static constexpr size_t REGIONS = 2ull * P * N * 8;            // two regions per polynomial
     static constexpr bool DSM = REGIONS + 4ull * G * N * 8 <= 200 * 1024;   // row differences in smem
-    static constexpr size_t DBYTES = DSM ? 4ull * G * N * 8 : 0;
+    // otherwise (N >= 4096) the difference of one (sign, component) pair,
+    // built before the batches of its digits
+    static constexpr bool DPAIR = !DSM && REGIONS + N * 8ull <= 200 * 1024;
+    static constexpr size_t DBYTES = DSM ? 4ull * G * N * 8 : DPAIR ? N * 8ull : 0;
     // forward twiddle pairs in shared memory when they fit (N <= 4096),
     // else read through L1 from the key's table (N = 8192)
     static constexpr size_t TWBYTES = smem_twbytes(LOGN, THREADS, RB);
@@ -309,7 +314,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     const u32 l = tid % C::T;          // thread within the polynomial
     const u32 pc = p / G, pg = p % G;  // its combo within the batch and row within the group
     ntr::Swap sw{sm + (size_t)p * N, sm + (size_t)(C::P + p) * N, 0};
-    u64 *dbuf = sm + (size_t)2 * C::P * N;     // [G][4][N] row differences (DSM only)
+    u64 *dbuf = sm + (size_t)2 * C::P * N;     // [G][4][N] row differences (DSM), or one pair's [N] (DPAIR)
     const u64 qb = Q << log2B;                 // Q * B, for the exact small first stage (LAZY, not QLOW1)
     const u64 lmask = (1ull << lbits) - 1;     // Karatsuba limb mask
     const u32 ncomb = 4 * lB;
@@ -339,6 +344,9 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
             : "l"(xv), "l"(bv0), "l"(bv1), "r"(lbits), "r"(lmask32));
     };
 
+    // one pair's difference in shared memory serves batches that each take
+    // digits of a single pair (CPB divides l_B; G = 1)
+    const bool dpair = C::DPAIR && G == 1 && lB % CPB == 0;
     u64 *cur = acc0, *nxt = acc1;
     const u32 steps = steps_limit < n ? steps_limit : n;
     for (u32 k = 0; k < steps; k++) {
@@ -374,57 +382,72 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                     const u32 cv = sg == 0 ? (ak ? qp - ak : 0u) : ak;
                     mmpm_row(cv, r < m ? r : 0, m, 2 * N, J.gS, gpre, rsrc[g][sg], rexp[g][sg]);
                 }
-            if constexpr (C::DSM) {
-                // D_(row, sign, comp) = P(c) ACC - ACC: coefficient idx of
-                // x^e src is src[idx - e] for idx >= e, else -src[idx - e + N]
-                // (e < N; for e >= N the two cases swap sign)
+            // D_(row, sign, comp) = P(c) ACC - ACC into drow: coefficient idx of
+            // x^e src is src[idx - e] for idx >= e, else -src[idx - e + N]
+            // (e < N; for e >= N the two cases swap sign)
+            auto build_d = [&](u32 g, u32 pair, u64 *drow) {
+                const u32 r = r0 + g;
+                const u32 sgn = pair >> 1, comp = pair & 1;
+                const u64 *srow = cur + (rsrc[g][sgn] * 2 + comp) * (u32)N;
+                const u64 *orow = cur + (r * 2 + comp) * (u32)N;
+                const u32 e = rexp[g][sgn];
+                const bool flip = e >= (u32)N;
+                const u32 es = flip ? e - N : e;
+                // this thread's loads of the row issued together, four
+                // coefficients at a time
+                constexpr int ITER = (N + C::kThreads - 1) / C::kThreads;
+                constexpr int CH = ITER < 4 ? ITER : 4;
 #pragma unroll
-                for (int g = 0; g < G; g++) {
-                    const u32 r = r0 + g;
-                    if (G > 1 && r >= m) continue;
+                for (int i0 = 0; i0 < ITER; i0 += CH) {
+                    u64 v[CH], o[CH];
 #pragma unroll
-                    for (int pair = 0; pair < 4; pair++) {
-                        const u32 sgn = pair >> 1, comp = pair & 1;
-                        const u64 *srow = cur + (rsrc[g][sgn] * 2 + comp) * (u32)N;
-                        const u64 *orow = cur + (r * 2 + comp) * (u32)N;
-                        u64 *drow = dbuf + (g * 4 + pair) * N;
-                        const u32 e = rexp[g][sgn];
-                        const bool flip = e >= (u32)N;
-                        const u32 es = flip ? e - N : e;
-                        // all of this thread's loads of the row issued together
-                        constexpr int ITER = (N + C::kThreads - 1) / C::kThreads;
-                        u64 v[ITER], o[ITER];
-#pragma unroll
-                        for (int it = 0; it < ITER; it++) {
-                            const u32 idx = tid + it * C::kThreads;
-                            if (idx < (u32)N) {
-                                const bool wrap = idx < es;
-                                v[it] = acc_load(srow + (wrap ? idx + N - es : idx - es), split);
-                                o[it] = acc_load(orow + idx, split);
-                            }
-                        }
-#pragma unroll
-                        for (int it = 0; it < ITER; it++) {
-                            const u32 idx = tid + it * C::kThreads;
-                            if (idx < (u32)N) {
-                                const bool wrap = idx < es;
-                                const u64 sv = (wrap != flip) ? sub_mod(0, v[it], Q) : v[it];
-                                drow[idx] = sub_mod(sv, o[it], Q);
-                            }
+                    for (int it = 0; it < CH; it++) {
+                        const u32 idx = tid + (i0 + it) * C::kThreads;
+                        if (idx < (u32)N) {
+                            const bool wrap = idx < es;
+                            v[it] = acc_load(srow + (wrap ? idx + N - es : idx - es), split);
+                            o[it] = acc_load(orow + idx, split);
                         }
                     }
+#pragma unroll
+                    for (int it = 0; it < CH; it++) {
+                        const u32 idx = tid + (i0 + it) * C::kThreads;
+                        if (idx < (u32)N) {
+                            const bool wrap = idx < es;
+                            const u64 sv = (wrap != flip) ? sub_mod(0, v[it], Q) : v[it];
+                            drow[idx] = sub_mod(sv, o[it], Q);
+                        }
+                    }
+                }
+            };
+            if constexpr (C::DSM) {
+#pragma unroll
+                for (int g = 0; g < G; g++) {
+                    if (G > 1 && r0 + g >= m) continue;
+#pragma unroll
+                    for (int pair = 0; pair < 4; pair++) build_d(g, pair, dbuf + (g * 4 + pair) * N);
                 }
                 __syncthreads();
             }
             for (u32 c0 = 0; c0 < ncomb; c0 += CPB) {
+                if constexpr (C::DPAIR) {
+                    // the first batch of a (sign, component) pair builds its
+                    // difference; every thread read the previous pair's before
+                    // the previous batch's barrier preceding its
+                    // multiply-accumulate
+                    if (dpair && c0 % lB == 0) {
+                        build_d(0, c0 / lB, dbuf);
+                        __syncthreads();
+                    }
+                }
                 // --- this thread's digit polynomial, transformed into shared memory
                 const u32 c = c0 + pc, r = r0 + pg;
                 const bool active = pc < (u32)CPB && c < ncomb && r < m;
                 u64 x[R];
                 if (active) {
                     const u32 pair = c / lB, sh = (c % lB) * log2B;
-                    if constexpr (C::DSM) {
-                        const u64 *dp = dbuf + ((size_t)pg * 4 + pair) * N;
+                    if (C::DSM || dpair) {
+                        const u64 *dp = dbuf + (C::DSM ? ((size_t)pg * 4 + pair) * N : 0);
 #pragma unroll
                         for (int i = 0; i < R; i++) x[i] = (u32)(dp[l + C::T * i] >> sh) & Bmask;
                     } else {
