@@ -489,6 +489,29 @@ def run_gpu(args, w):
             del batches
             torch.cuda.empty_cache()
             result.update(run_extras(args, api, dev, stream, flush, peak))
+            # decryption failures over at least --fail-count bootstraps of this
+            # run: every output above, then further (untimed) headline batches
+            tot, bad = checked, failures
+            for wr in result["workloads"]:
+                tot += wr["bootstraps_checked"]
+                bad += wr["decrypt_failures"]
+            n_uneven = sum(result["uneven"]["counts"].values())
+            for md in result["uneven"]["modes"].values():
+                tot += n_uneven
+                bad += md["decrypt_failures"]
+            extra = 0
+            while tot < args.fail_count:
+                b = make_inputs(api, sk, w, count, seed + 1000 * (args.warmup + args.steps + extra), dev)
+                step(b)
+                torch.cuda.synchronize(dev)
+                f, c = count_failures(api, sk, w, [b])
+                tot += c
+                bad += f
+                extra += 1
+                del b
+            result["failures"] = {"bootstraps": tot, "decrypt_failures": bad,
+                                  "of": "every output of this run (headline incl. warm-up, other workloads, "
+                                        f"uneven mix) plus {extra} further headline batches"}
         if not args.no_cpu:
             r, cores, sample, _ = oracle_rate(w, steps_sample=args.cpu_steps)
             result["cpu_baseline"] = {"value": r, "unit": "bootstraps/s", "cores": cores,

@@ -78,6 +78,9 @@ __device__ __forceinline__ void mbar_wait(u64 *bar, u32 parity, u32 *status) {
     set_status(status, BM_ETIMEDOUT);
 }
 
+// Load of a bootstrapping-key word (read-only for the kernel's lifetime).
+__device__ __forceinline__ u64 key_load(const u64 *p) { return __ldg(p); }
+
 // Negacyclic table check: entries in [0, t) and f(k + t/2) = -f(k) mod t.
 static __device__ bool lut_is_negacyclic(const u32 *__restrict__ lut, u32 t) {
     __shared__ int bad;
@@ -421,11 +424,43 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 }
             };
             if constexpr (C::DSM) {
+                // all four differences of the row (G = 1): per coefficient the
+                // four rotated source words and the row's own two words are
+                // requested together, one L2 round trip for the row
+                static_assert(G == 1, "one row per group");
+                constexpr int ITER = (N + C::kThreads - 1) / C::kThreads;
+                const u64 *srow[4], *orow[2];
+                u32 es[4];
+                bool flip[4];
 #pragma unroll
-                for (int g = 0; g < G; g++) {
-                    if (G > 1 && r0 + g >= m) continue;
+                for (int pair = 0; pair < 4; pair++) {
+                    const u32 sgn = pair >> 1, comp = pair & 1;
+                    srow[pair] = cur + (rsrc[0][sgn] * 2 + comp) * (u32)N;
+                    const u32 e = rexp[0][sgn];
+                    flip[pair] = e >= (u32)N;
+                    es[pair] = flip[pair] ? e - N : e;
+                }
+                orow[0] = cur + (r0 * 2) * (u32)N;
+                orow[1] = cur + (r0 * 2 + 1) * (u32)N;
 #pragma unroll
-                    for (int pair = 0; pair < 4; pair++) build_d(g, pair, dbuf + (g * 4 + pair) * N);
+                for (int it = 0; it < ITER; it++) {
+                    const u32 idx = tid + it * C::kThreads;
+                    if (idx < (u32)N) {
+                        u64 v[4], o[2];
+#pragma unroll
+                        for (int pair = 0; pair < 4; pair++) {
+                            const bool wrap = idx < es[pair];
+                            v[pair] = acc_load(srow[pair] + (wrap ? idx + N - es[pair] : idx - es[pair]), split);
+                        }
+                        o[0] = acc_load(orow[0] + idx, split);
+                        o[1] = acc_load(orow[1] + idx, split);
+#pragma unroll
+                        for (int pair = 0; pair < 4; pair++) {
+                            const bool wrap = idx < es[pair];
+                            const u64 sv = (wrap != flip[pair]) ? sub_mod(0, v[pair], Q) : v[pair];
+                            dbuf[pair * N + idx] = sub_mod(sv, o[pair & 1], Q);
+                        }
+                    }
                 }
                 __syncthreads();
             }
@@ -502,8 +537,8 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                     if (full) {
 #pragma unroll
                         for (int cc = 0; cc < PRE; cc++) {
-                            bnext[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + tid);
-                            bnext[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + tid);
+                            bnext[cc][0] = key_load(bsk_c0 + (size_t)cc * 2 * N + tid);
+                            bnext[cc][1] = key_load(bsk_c0 + (size_t)cc * 2 * N + N + tid);
                         }
                     }
                 }
@@ -547,14 +582,14 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                                 }
 #pragma unroll
                                 for (int cc = PRE; cc < CPB; cc++) {
-                                    bv[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q);
-                                    bv[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q);
+                                    bv[cc][0] = key_load(bsk_c0 + (size_t)cc * 2 * N + q);
+                                    bv[cc][1] = key_load(bsk_c0 + (size_t)cc * 2 * N + N + q);
                                 }
                                 if (j + 1 < C::PPT) {
 #pragma unroll
                                     for (int cc = 0; cc < PRE; cc++) {
-                                        bnext[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q + C::kThreads);
-                                        bnext[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q + C::kThreads);
+                                        bnext[cc][0] = key_load(bsk_c0 + (size_t)cc * 2 * N + q + C::kThreads);
+                                        bnext[cc][1] = key_load(bsk_c0 + (size_t)cc * 2 * N + N + q + C::kThreads);
                                     }
                                 }
                             } else if constexpr (C::KC < CPB) {
@@ -564,8 +599,8 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                                     u64 kv[C::KC][2];
 #pragma unroll
                                     for (int cc = 0; cc < C::KC; cc++) {
-                                        kv[cc][0] = __ldg(bsk_c0 + (size_t)(k0 + cc) * 2 * N + q);
-                                        kv[cc][1] = __ldg(bsk_c0 + (size_t)(k0 + cc) * 2 * N + N + q);
+                                        kv[cc][0] = key_load(bsk_c0 + (size_t)(k0 + cc) * 2 * N + q);
+                                        kv[cc][1] = key_load(bsk_c0 + (size_t)(k0 + cc) * 2 * N + N + q);
                                     }
 #pragma unroll
                                     for (int cc = 0; cc < C::KC; cc++)
@@ -580,8 +615,8 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                             } else {
 #pragma unroll
                                 for (int cc = 0; cc < CPB; cc++) {
-                                    bv[cc][0] = __ldg(bsk_c0 + (size_t)cc * 2 * N + q);
-                                    bv[cc][1] = __ldg(bsk_c0 + (size_t)cc * 2 * N + N + q);
+                                    bv[cc][0] = key_load(bsk_c0 + (size_t)cc * 2 * N + q);
+                                    bv[cc][1] = key_load(bsk_c0 + (size_t)cc * 2 * N + N + q);
                                 }
                             }
                             if constexpr (PIPE || C::KC == CPB) {
@@ -598,7 +633,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                         } else {
                             for (u32 cc = 0; cc < nc; cc++) {
                                 const u64 *brow = bsk_c0 + (size_t)cc * 2 * N + q;
-                                const u64 b0 = __ldg(brow), b1 = __ldg(brow + N);
+                                const u64 b0 = key_load(brow), b1 = key_load(brow + N);
 #pragma unroll
                                 for (int g = 0; g < G; g++) {
                                     if (G == 1 || r0 + g < m) {
