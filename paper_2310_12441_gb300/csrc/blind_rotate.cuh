@@ -78,8 +78,14 @@ __device__ __forceinline__ void mbar_wait(u64 *bar, u32 parity, u32 *status) {
     set_status(status, BM_ETIMEDOUT);
 }
 
-// Load of a bootstrapping-key word (read-only for the kernel's lifetime).
-__device__ __forceinline__ u64 key_load(const u64 *p) { return __ldg(p); }
+// The key words of one combo at one position, both columns, in one 16-byte
+// load (read-only for the kernel's lifetime): w0 holds the low limbs of
+// columns 0 and 1 (as two 32-bit halves), w1 their high limbs.
+__device__ __forceinline__ void key_load2(const u64 *p, u64 &w0, u64 &w1) {
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+    w0 = v.x;
+    w1 = v.y;
+}
 
 // Negacyclic table check: entries in [0, t) and f(k + t/2) = -f(k) mod t.
 static __device__ bool lut_is_negacyclic(const u32 *__restrict__ lut, u32 t) {
@@ -323,20 +329,25 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     const u32 ncomb = 4 * lB;
     const size_t rgsw = (size_t)2 * lB * 2 * N;
 
-    // Limb products of a transform value xv with the key words bv0, bv1 of
-    // the two columns (each stored pre-split, low limb | high limb << 32):
-    // x1 b1, x0 b0 and (x0 + x1)(b0 + b1) accumulate with mad.wide.u32 (one
-    // multiplier instruction each, the addition included).  xv's limbs are
-    // split once (funnel shift: lbits <= 31 and xv < 2^(lbits + 32)) for both.
+    // Limb products of a transform value xv with the key words of the two
+    // columns: x1 b1, x0 b0 and (x0 + x1)(b0 + b1) accumulate with
+    // mad.wide.u32 (one multiplier instruction each, the addition included).
+    // xv's limbs are split once (funnel shift: lbits <= 31 and xv <
+    // 2^(lbits + 32)) for both columns.  The key stores per position the low
+    // limbs of both columns in w0 and their high limbs in w1 (32-bit halves),
+    // so one 64-bit addition w0 + w1 forms both columns' limb sums b0 + b1
+    // (each below 2^32: no carry crosses the halves).
     const u32 lmask32 = (u32)lmask;
-    auto kara2 = [&](u64 xv, u64 bv0, u64 bv1, u64 (&kh)[2], u64 (&kl)[2], u64 (&km)[2]) {
-        asm("{\n\t.reg .u32 v0, v1, x0, x1, xs, a0, a1, as, c0, c1, cs;\n\t"
+    auto kara2 = [&](u64 xv, u64 w0, u64 w1, u64 (&kh)[2], u64 (&kl)[2], u64 (&km)[2]) {
+        asm("{\n\t.reg .u32 v0, v1, x0, x1, xs, a0, a1, as, c0, c1, cs;\n\t.reg .u64 s;\n\t"
             "mov.b64 {v0, v1}, %6;\n\t"
             "shf.r.clamp.b32 x1, v0, v1, %9;\n\t"
             "and.b32 x0, v0, %10;\n\t"
             "add.u32 xs, x0, x1;\n\t"
-            "mov.b64 {a0, a1}, %7;\n\tadd.u32 as, a0, a1;\n\t"
-            "mov.b64 {c0, c1}, %8;\n\tadd.u32 cs, c0, c1;\n\t"
+            "mov.b64 {a0, c0}, %7;\n\t"
+            "mov.b64 {a1, c1}, %8;\n\t"
+            "add.u64 s, %7, %8;\n\t"
+            "mov.b64 {as, cs}, s;\n\t"
             "mad.wide.u32 %0, x1, a1, %0;\n\t"
             "mad.wide.u32 %1, x0, a0, %1;\n\t"
             "mad.wide.u32 %2, xs, as, %2;\n\t"
@@ -344,7 +355,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
             "mad.wide.u32 %4, x0, c0, %4;\n\t"
             "mad.wide.u32 %5, xs, cs, %5;\n\t}"
             : "+l"(kh[0]), "+l"(kl[0]), "+l"(km[0]), "+l"(kh[1]), "+l"(kl[1]), "+l"(km[1])
-            : "l"(xv), "l"(bv0), "l"(bv1), "r"(lbits), "r"(lmask32));
+            : "l"(xv), "l"(w0), "l"(w1), "r"(lbits), "r"(lmask32));
     };
 
     // one pair's difference in shared memory serves batches that each take
@@ -537,8 +548,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                     if (full) {
 #pragma unroll
                         for (int cc = 0; cc < PRE; cc++) {
-                            bnext[cc][0] = key_load(bsk_c0 + (size_t)cc * 2 * N + tid);
-                            bnext[cc][1] = key_load(bsk_c0 + (size_t)cc * 2 * N + N + tid);
+                            key_load2(bsk_c0 + (size_t)cc * 2 * N + 2 * tid, bnext[cc][0], bnext[cc][1]);
                         }
                     }
                 }
@@ -582,14 +592,13 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                                 }
 #pragma unroll
                                 for (int cc = PRE; cc < CPB; cc++) {
-                                    bv[cc][0] = key_load(bsk_c0 + (size_t)cc * 2 * N + q);
-                                    bv[cc][1] = key_load(bsk_c0 + (size_t)cc * 2 * N + N + q);
+                                    key_load2(bsk_c0 + (size_t)cc * 2 * N + 2 * q, bv[cc][0], bv[cc][1]);
                                 }
                                 if (j + 1 < C::PPT) {
 #pragma unroll
                                     for (int cc = 0; cc < PRE; cc++) {
-                                        bnext[cc][0] = key_load(bsk_c0 + (size_t)cc * 2 * N + q + C::kThreads);
-                                        bnext[cc][1] = key_load(bsk_c0 + (size_t)cc * 2 * N + N + q + C::kThreads);
+                                        key_load2(bsk_c0 + (size_t)cc * 2 * N + 2 * (q + C::kThreads), bnext[cc][0],
+                                                  bnext[cc][1]);
                                     }
                                 }
                             } else if constexpr (C::KC < CPB) {
@@ -599,8 +608,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                                     u64 kv[C::KC][2];
 #pragma unroll
                                     for (int cc = 0; cc < C::KC; cc++) {
-                                        kv[cc][0] = key_load(bsk_c0 + (size_t)(k0 + cc) * 2 * N + q);
-                                        kv[cc][1] = key_load(bsk_c0 + (size_t)(k0 + cc) * 2 * N + N + q);
+                                        key_load2(bsk_c0 + (size_t)(k0 + cc) * 2 * N + 2 * q, kv[cc][0], kv[cc][1]);
                                     }
 #pragma unroll
                                     for (int cc = 0; cc < C::KC; cc++)
@@ -615,8 +623,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                             } else {
 #pragma unroll
                                 for (int cc = 0; cc < CPB; cc++) {
-                                    bv[cc][0] = key_load(bsk_c0 + (size_t)cc * 2 * N + q);
-                                    bv[cc][1] = key_load(bsk_c0 + (size_t)cc * 2 * N + N + q);
+                                    key_load2(bsk_c0 + (size_t)cc * 2 * N + 2 * q, bv[cc][0], bv[cc][1]);
                                 }
                             }
                             if constexpr (PIPE || C::KC == CPB) {
@@ -632,8 +639,8 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                             }
                         } else {
                             for (u32 cc = 0; cc < nc; cc++) {
-                                const u64 *brow = bsk_c0 + (size_t)cc * 2 * N + q;
-                                const u64 b0 = key_load(brow), b1 = key_load(brow + N);
+                                u64 b0, b1;
+                                key_load2(bsk_c0 + (size_t)cc * 2 * N + 2 * q, b0, b1);
 #pragma unroll
                                 for (int g = 0; g < G; g++) {
                                     if (G == 1 || r0 + g < m) {

@@ -15,7 +15,7 @@
 // Device-resident description of one evaluation key set.  One copy lives in
 // device memory (owned by the bm_eval_key) so jobs can point at it.
 struct KeyDev {
-    const u64 *bsk;    // [n][2][2 l_B][2][N], NTT domain, scaled by N^-1
+    const u64 *bsk;    // [n][2][2 l_B][N][2], NTT domain, scaled by N^-1 (limbs, see lbits)
     const u64 *ksk;    // [N][l_ks][B_ks - 1][n + 1]
     const u64 *tw;     // forward twiddles psi^bitrev(k), k in [0, N)
     const u64 *twsh;   // their Shoup companions
@@ -27,7 +27,8 @@ struct KeyDev {
     u64 ninv, ninv_sh; // N^-1 mod Q and companion
     u64 ks_pq;         // floor(P 2^64 / Q), P = B_ks^l_ks
     u32 n, N, logN, log2_B, l_B, log2_Bks, l_ks;
-    u32 lbits;         // BSK words are stored as (b mod 2^lbits) | (b >> lbits) 2^32
+    u32 lbits;         // BSK words b (column 0) and b' (column 1) of a position are stored as
+                       // (b mod 2^lbits) | (b' mod 2^lbits) 2^32, (b >> lbits) | (b' >> lbits) 2^32
 };
 
 // One job as the kernels see it.

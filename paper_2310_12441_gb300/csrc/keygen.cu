@@ -140,11 +140,12 @@ __device__ void bsk_row_finish(u64 *sm, size_t row_id, const int8_t *__restrict_
         add128(lo, hi, g1);
         const u64 c1 = reduce128(lo, hi, K.mq);
         const u64 c0 = add_mod(ah, g0, Q);
-        // stored split into the multiply-accumulate's limbs (KeyDev::lbits)
+        // stored split into the multiply-accumulate's limbs (KeyDev::lbits):
+        // per position the low limbs of both columns, then their high limbs
         const u64 lmask = (1ull << K.lbits) - 1;
         const u64 w0 = mul_shoup(c0, K.ninv, K.ninv_sh, Q), w1 = mul_shoup(c1, K.ninv, K.ninv_sh, Q);
-        o[i] = (w0 & lmask) | ((w0 >> K.lbits) << 32);
-        o[N + i] = (w1 & lmask) | ((w1 >> K.lbits) << 32);
+        o[2 * i] = (w0 & lmask) | ((w1 & lmask) << 32);
+        o[2 * i + 1] = (w0 >> K.lbits) | ((w1 >> K.lbits) << 32);
     }
 }
 
