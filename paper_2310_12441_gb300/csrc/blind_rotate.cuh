@@ -262,7 +262,7 @@ struct Cfg {
 // row sums go to the job's sum buffer; after the last row the 2m sums are
 // inverse-transformed (P per batch) and added to the rows of the next ACC
 // buffer.
-template <int LOGN, int THREADS, int RB, bool LAZY, bool SMALL0, bool QLOW1>
+template <int LOGN, int THREADS, int RB, bool LAZY, bool SMALL0, bool QLOW1, int BLK = 1>
 __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u64 *__restrict__ ct_in,
                                        const u32 *__restrict__ luts, u64 *ws, u32 *status, u64 *sm) {
     using C = Cfg<LOGN, THREADS, RB>;
@@ -535,9 +535,9 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 // The next position's key words for the first PRE combos (all of a
                 // batch of at most 4, half of a larger one) are loaded while the
                 // current position is multiplied.
-                // (not with 1024 threads: at 64 registers the extra words spilled and measured
-                // 4% slower at N = 2048 and 4096)
-                constexpr bool PIPE = C::PPT > 1 && (int)C::kThreads * C::PPT == N && C::kThreads < 1024;
+                // (not at 64 registers per thread, 1024 threads per SM: the extra words
+                // spilled and measured 4% slower at N = 2048 and 4096)
+                constexpr bool PIPE = C::PPT > 1 && (int)C::kThreads * C::PPT == N && C::kThreads * BLK < 1024;
                 constexpr int PRE = CPB <= 4 ? CPB : CPB / 2;
                 u64 bnext[PIPE ? PRE : 1][2];
                 // (Requesting the first key words before the barrier below, to

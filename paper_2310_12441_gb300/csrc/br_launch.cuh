@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(br_shape(SH).threads, br_shape(SH).blocks)
                    const u32 *__restrict__ luts, u64 *ws, u32 *status) {
     extern __shared__ __align__(16) u64 sm[];
     // a cluster of blocks shares one job (rows split); plain launches: 1 block
-    brk::br_job<LOGN, br_shape(SH).threads, br_shape(SH).rb, LAZY, SMALL0, QLOW1>(
+    brk::br_job<LOGN, br_shape(SH).threads, br_shape(SH).rb, LAZY, SMALL0, QLOW1, br_shape(SH).blocks>(
         jobs[blockIdx.x / cluster_size()], steps_limit, ct_in, luts, ws, status, sm);
 }
 

@@ -38,8 +38,8 @@ __global__ void __launch_bounds__(br_shape(SH).threads, 1)
         const u32 idx = s_next[slot];
         if (idx >= count) break;
         if (threadIdx.x == 0) s_next[slot ^ 1] = atomicAdd(counter, 1u);
-        brk::br_job<LOGN, br_shape(SH).threads, br_shape(SH).rb, lazy, lazy || q1, q1>(jobs[idx], steps, ct_in, luts,
-                                                                                 ws, status, sm);
+        brk::br_job<LOGN, br_shape(SH).threads, br_shape(SH).rb, lazy, lazy || q1, q1, br_shape(SH).blocks>(
+            jobs[idx], steps, ct_in, luts, ws, status, sm);
         __syncthreads();
         slot ^= 1;
     }
