@@ -184,26 +184,34 @@ static __device__ void acc_init(u64 *__restrict__ acc, const u32 *__restrict__ l
 namespace brk {
 // Shared memory of one block (see Cfg): two exchange regions per polynomial
 // of a batch, the row differences when they fit, the forward twiddle pairs.
+// With `blocks` blocks per SM each block plans within its share of the SM
+// (226 KB for one block, 112 KB each for two).
+__host__ __device__ constexpr size_t smem_budget(int blocks) { return blocks > 1 ? 112 * 1024 : 226 * 1024; }
+__host__ __device__ constexpr size_t smem_dbudget(int blocks) { return blocks > 1 ? 96 * 1024 : 200 * 1024; }
 __host__ __device__ constexpr size_t smem_regions(int logn, int threads, int rb) {
     return 2ull * (threads / ((1 << logn) >> rb)) * (1ull << logn) * 8;
 }
-__host__ __device__ constexpr size_t smem_dbytes(int logn, int threads, int rb) {
-    return smem_regions(logn, threads, rb) + 4ull * (1ull << logn) * 8 <= 200 * 1024 ? 4ull * (1ull << logn) * 8
-         : smem_regions(logn, threads, rb) + (1ull << logn) * 8 <= 200 * 1024  ? (1ull << logn) * 8
-                                                                               : 0;
+__host__ __device__ constexpr size_t smem_dbytes(int logn, int threads, int rb, int blocks = 1) {
+    return smem_regions(logn, threads, rb) + 4ull * (1ull << logn) * 8 <= smem_dbudget(blocks)
+               ? 4ull * (1ull << logn) * 8
+           : smem_regions(logn, threads, rb) + (1ull << logn) * 8 <= smem_dbudget(blocks) ? (1ull << logn) * 8
+                                                                                          : 0;
 }
-__host__ __device__ constexpr size_t smem_twbytes(int logn, int threads, int rb) {
-    return smem_regions(logn, threads, rb) + smem_dbytes(logn, threads, rb) + 16ull * (1ull << logn) <= 226 * 1024
+__host__ __device__ constexpr size_t smem_twbytes(int logn, int threads, int rb, int blocks = 1) {
+    return smem_regions(logn, threads, rb) + smem_dbytes(logn, threads, rb, blocks) + 16ull * (1ull << logn) <=
+                   smem_budget(blocks)
                ? 16ull * (1ull << logn)
                : 0;
 }
-__host__ __device__ constexpr size_t smem_bytes(int logn, int threads, int rb) {
-    return smem_regions(logn, threads, rb) + smem_dbytes(logn, threads, rb) + smem_twbytes(logn, threads, rb);
+__host__ __device__ constexpr size_t smem_bytes(int logn, int threads, int rb, int blocks = 1) {
+    return smem_regions(logn, threads, rb) + smem_dbytes(logn, threads, rb, blocks) +
+           smem_twbytes(logn, threads, rb, blocks);
 }
 
 // Block shape for a ring of 2^LOGN coefficients run by THREADS threads,
-// each holding 2^RB coefficients of a polynomial in the transforms.
-template <int LOGN, int THREADS, int RB = 4>
+// each holding 2^RB coefficients of a polynomial in the transforms, BLK
+// blocks per SM.
+template <int LOGN, int THREADS, int RB = 4, int BLK = 1>
 struct Cfg {
     static constexpr int kThreads = THREADS;
     static constexpr int N = 1 << LOGN;
@@ -227,17 +235,17 @@ struct Cfg {
     static constexpr bool RED = PPT >= 8;
     static constexpr int PPTR = RED ? 1 : PPT;                    // positions of the register sums
     static constexpr size_t REGIONS = 2ull * P * N * 8;            // two regions per polynomial
-    static constexpr bool DSM = REGIONS + 4ull * G * N * 8 <= 200 * 1024;   // row differences in smem
-    // otherwise (N >= 4096) the difference of one (sign, component) pair,
-    // built before the batches of its digits
-    static constexpr bool DPAIR = !DSM && REGIONS + N * 8ull <= 200 * 1024;
+    static constexpr bool DSM = REGIONS + 4ull * G * N * 8 <= smem_dbudget(BLK);   // row differences in smem
+    // otherwise (N >= 4096, or 2048 with two blocks per SM) the difference of
+    // one (sign, component) pair, built before the batches of its digits
+    static constexpr bool DPAIR = !DSM && REGIONS + N * 8ull <= smem_dbudget(BLK);
     static constexpr size_t DBYTES = DSM ? 4ull * G * N * 8 : DPAIR ? N * 8ull : 0;
-    // forward twiddle pairs in shared memory when they fit (N <= 4096),
-    // else read through L1 from the key's table (N = 8192)
-    static constexpr size_t TWBYTES = smem_twbytes(LOGN, THREADS, RB);
+    // forward twiddle pairs in shared memory when they fit, else read
+    // through L1 from the key's table
+    static constexpr size_t TWBYTES = smem_twbytes(LOGN, THREADS, RB, BLK);
     static constexpr bool TWSM = TWBYTES != 0;
     static constexpr size_t SMEM = REGIONS + DBYTES + TWBYTES;
-    static_assert(G != 1 || SMEM == smem_bytes(LOGN, THREADS, RB), "smem_bytes mirrors Cfg");
+    static_assert(G != 1 || SMEM == smem_bytes(LOGN, THREADS, RB, BLK), "smem_bytes mirrors Cfg");
     static_assert(P >= 1 && P * T == THREADS, "whole polynomials per batch");
     static_assert(T <= 32 || P <= 15, "a named barrier per polynomial (ids 1..15)");
     static_assert(SMEM <= 227 * 1024 - 1024, "shared memory per block");
@@ -265,7 +273,7 @@ struct Cfg {
 template <int LOGN, int THREADS, int RB, bool LAZY, bool SMALL0, bool QLOW1, int BLK = 1>
 __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u64 *__restrict__ ct_in,
                                        const u32 *__restrict__ luts, u64 *ws, u32 *status, u64 *sm) {
-    using C = Cfg<LOGN, THREADS, RB>;
+    using C = Cfg<LOGN, THREADS, RB, BLK>;
     constexpr int R = C::R;
     constexpr int N = C::N, G = C::G, CPB = C::CPB;
     const KeyDev *K = J.key;

@@ -27,7 +27,7 @@ __host__ __device__ constexpr bool br_shape_fits(int logn, int sh) {
     const BrShape b = br_shape(sh);
     const int T = (1 << logn) >> b.rb;
     if (b.threads % T != 0 || b.threads < T) return false;
-    const size_t smem = brk::smem_bytes(logn, b.threads, b.rb);
+    const size_t smem = brk::smem_bytes(logn, b.threads, b.rb, b.blocks);
     return smem <= 226 * 1024 && (smem + 1024) * b.blocks <= 228 * 1024;
 }
 
@@ -112,7 +112,7 @@ template <int LOGN, int SH, bool LAZY, bool SMALL0, bool QLOW1>
 bm_status launch_br_v(const DevJob *jobs, uint32_t cnt, u32 mmax, u32 max_cluster, u32 steps,
                       const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status, cudaStream_t st,
                       bool dry) {
-    using C = brk::Cfg<LOGN, br_shape(SH).threads, br_shape(SH).rb>;
+    using C = brk::Cfg<LOGN, br_shape(SH).threads, br_shape(SH).rb, br_shape(SH).blocks>;
     static std::atomic<uint64_t> attr_done{0};
     auto kern = k_blind_rotate<LOGN, SH, LAZY, SMALL0, QLOW1>;
     bm_status s = ensure_smem(kern, C::SMEM, attr_done);

@@ -49,7 +49,7 @@ template <int LOGN, u32 V, int SH>
 bm_status launch_class(const DevJob *d_jobs, uint32_t count, uint32_t steps, const uint64_t *ct_in,
                        const uint32_t *lut, u64 *ws_acc, u32 *status, u32 *counter, int sms, bool dry,
                        cudaStream_t st) {
-    using C = brk::Cfg<LOGN, br_shape(SH).threads, br_shape(SH).rb>;
+    using C = brk::Cfg<LOGN, br_shape(SH).threads, br_shape(SH).rb, br_shape(SH).blocks>;
     auto kern = k_blind_rotate_persistent<LOGN, V, SH>;
     static std::atomic<uint64_t> attr_done{0};
     bm_status s = ensure_smem(kern, C::SMEM, attr_done);

@@ -58,14 +58,14 @@ def test_kernel_shape_table():
     from paper_2310_12441_gb300 import api
     api.load()
     assert set(api.kernel_shapes(1024)) == {0, 1, 2, 3, 4}
-    assert set(api.kernel_shapes(2048)) == {0, 1, 4}
-    assert set(api.kernel_shapes(4096)) == {0, 1, 4}
+    assert set(api.kernel_shapes(2048)) == {0, 1, 2, 3, 4}
+    assert set(api.kernel_shapes(4096)) == {0, 1, 2, 3, 4}
     assert set(api.kernel_shapes(8192)) == {0, 1}
     assert set(api.kernel_shapes(256)) == {0}
     assert api.kernel_shapes(16384) == {}
     assert api.kernel_shapes(1024)[1] == (8, 1024, 1)
     with pytest.raises(api.BMError):
-        api.set_kernel_shape(4096, 2)
+        api.set_kernel_shape(8192, 2)
     with pytest.raises(api.BMError):
         api.set_kernel_shape(1000, 0)
     api.set_kernel_shape(2048, 4)
