@@ -721,7 +721,7 @@ def run_suite(args):
     # (6) plaintext-size sweep of the Sec. 5 experiments: the identity function
     # (not negacyclic, so two rounds) on log t = 5.., BootMMPM at N = 2^11 with
     # m = 2^(log t - 5), q = 2Nm; the single-polynomial (TFHE) layout where its
-    # ring degree N = 2^(log t + 6) is one the kernels run (<= 8192)
+    # ring degree N = 2^(log t + 6) is one the library runs (<= 65536)
     if "sweep" in args.suite:
         lo, hi = (int(v) for v in args.sweep_logt.split("-"))
         paper_t1 = {5: 0.7375, 6: 1.3625, 7: 2.6376, 8: 5.2578, 9: 10.203, 10: 20.261, 11: 41.795}
@@ -779,14 +779,14 @@ def run_suite(args):
                  "log_t": logt, "log_q": logt + 7, "log_N": logN, "m": 1,
                  "key_bytes": {"bsk": bsk, "ksk": ksk},
                  "paper_table1_s_per_identity_i7": paper_t1_tfhe.get(logt) if kp_s.n == 512 else None}
-            if logN <= 13:
+            if logN <= 16:
                 kst = wl.make_keyset(kp_t, 1006)
                 d.update(identity_run(kst, 1, logt, 152 * max(1, 8 >> (logN - 11)), 700 + logt))
                 d["key_bytes"]["resident"] = kst.ek.nbytes
                 del kst
                 torch.cuda.empty_cache()
             else:
-                d["not_run"] = "ring degree above 8192"
+                d["not_run"] = "ring degree above 65536"
             emit(d)
     # (5) decryption failures over >= 1e5 bootstraps of the headline workload
     if "failures" in args.suite:

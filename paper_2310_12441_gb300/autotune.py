@@ -122,6 +122,8 @@ def tune(keysets, jobs, d_in, d_lut, d_out, ws, stream, reps: int = 3, use_cache
             sel = sel[np.linspace(0, len(sel) - 1, sample).astype(int)]
         sub = jobs[sel]
         times = {}
+        if not api.kernel_shapes(N):            # ring degrees above 8192: no shape choice
+            continue
         for sh in api.kernel_shapes(N):
             api.set_kernel_shape(N, sh)
             times[sh] = _time_batch(keys, sub, d_in, d_lut, d_out, ws, api.BATCH_GRAPH, stream, reps)

@@ -1,0 +1,355 @@
+// Ring degrees above 8192: the single-polynomial layout of the plaintext-size
+// sweep at log t >= 8 (Sec. 5, Tables 1-2, N = 2^(log t + 6)), m = 1.
+//
+// A polynomial of 8N bytes no longer fits one thread block's shared memory,
+// so its transforms run in two passes over global memory and the CMux steps
+// of a launch run as a sequence of kernels (digits, column pass, row pass,
+// multiply-accumulate, inverse row and column passes, accumulator update).
+// The transform is the one of ntt.cuh: Cooley-Tukey with psi^bitrev twiddles
+// in place (bit-reversed output), Gentleman-Sande inverse without N^-1.
+// With N = N1 N2, forward stages 0 .. log N1 - 1 pair elements of the columns
+// {c + N2 t : t < N1} (stage s, group t >> (log N1 - s): the same twiddle for
+// every column); stages log N1 + s', s' < log N2, pair elements of the rows
+// [r N2, (r + 1) N2) (group (r << s') + (o >> (log N2 - s')), twiddle index
+// ((N1 + r) << s') + (o >> (log N2 - s'))).  The inverse runs the row pass
+// first, then the column pass, each stage backwards.  Values stay in [0, Q)
+// (one correction per butterfly): this path serves a comparison, not the
+// headline workloads.
+#include "blind_rotate.cuh"
+
+namespace bign {
+
+constexpr u32 TC = 16;     // columns per block of the column pass
+constexpr u32 TR = 8;      // rows per block of the row pass
+constexpr u32 NT = 256;    // threads per block
+
+// Polynomial p of launch row y: a flat array of polynomials, or the
+// digit / sum buffers of job y (after the job's three [2][N] accumulator
+// buffers: ACC ping-pong, row sums; then 4 l_B digit polynomials).
+struct LocFlat {
+    u64 *base;
+    const KeyDev *key;
+    u32 per;
+    __device__ u64 *poly(u32 y, u32 p) const { return base + ((size_t)y * per + p) * key->N; }
+    __device__ const KeyDev &k(u32) const { return *key; }
+    __device__ u32 count(u32) const { return per; }
+};
+struct LocJobs {
+    const DevJob *jobs;
+    u64 *ws;
+    u32 sel;    // 0: digit polynomials, 1: the two row sums
+    __device__ u64 *poly(u32 y, u32 p) const {
+        const DevJob &J = jobs[y];
+        const size_t vec = (size_t)2 * J.N;
+        return ws + J.acc_off + (sel == 0 ? 3 * vec : 2 * vec) + (size_t)p * J.N;
+    }
+    __device__ const KeyDev &k(u32 y) const { return *jobs[y].key; }
+    __device__ u32 count(u32 y) const { return sel == 0 ? 4 * jobs[y].key->l_B : 2; }
+};
+
+__device__ __forceinline__ void split_log(u32 logN, u32 &l1, u32 &l2) {
+    l1 = logN / 2;
+    l2 = logN - l1;
+}
+
+// Column pass: block (x = p * (N2 / TC) + chunk, y) transforms columns
+// [chunk TC, (chunk + 1) TC) of polynomial p of row y.  smem: N1 TC words.
+template <bool INV, class Loc>
+__global__ void __launch_bounds__(NT) k_cols(Loc loc, u32 per) {
+    extern __shared__ u64 sm[];
+    const KeyDev &K = loc.k(blockIdx.y);
+    u32 l1, l2;
+    split_log(K.logN, l1, l2);
+    const u32 N1 = 1u << l1, N2 = 1u << l2, chunks = N2 / TC;
+    const u32 p = blockIdx.x / chunks, c0 = (blockIdx.x % chunks) * TC;
+    if (p >= per || p >= loc.count(blockIdx.y)) return;
+    u64 *a = loc.poly(blockIdx.y, p);
+    const u64 Q = K.mq.Q;
+    for (u32 e = threadIdx.x; e < N1 * TC; e += NT) sm[e] = a[c0 + e % TC + (size_t)N2 * (e / TC)];
+    __syncthreads();
+    for (u32 st = 0; st < l1; st++) {
+        const u32 s = INV ? l1 - 1 - st : st;
+        const u32 half = N1 >> (s + 1);
+        for (u32 b = threadIdx.x; b < (N1 / 2) * TC; b += NT) {
+            const u32 bp = b / TC, cc = b % TC;
+            const u32 g = bp / half, j = bp % half;
+            const u32 t = g * 2 * half + j;
+            u64 *x = sm + t * TC + cc, *y = sm + (t + half) * TC + cc;
+            const u32 ti = (1u << s) + g;
+            if (INV) {
+                const u64 U = *x, V = *y;
+                *x = add_mod(U, V, Q);
+                *y = mul_shoup(U + Q - V, __ldg(K.itw + ti), __ldg(K.itwsh + ti), Q);
+            } else {
+                const u64 U = *x, V = mul_shoup(*y, __ldg(K.tw + ti), __ldg(K.twsh + ti), Q);
+                *x = add_mod(U, V, Q);
+                *y = sub_mod(U, V, Q);
+            }
+        }
+        __syncthreads();
+    }
+    for (u32 e = threadIdx.x; e < N1 * TC; e += NT) a[c0 + e % TC + (size_t)N2 * (e / TC)] = sm[e];
+}
+
+// Row pass: block (x = p * (N1 / TR) + chunk, y) transforms rows
+// [chunk TR, (chunk + 1) TR) of polynomial p of row y.  smem: TR N2 words.
+template <bool INV, class Loc>
+__global__ void __launch_bounds__(NT) k_rows(Loc loc, u32 per) {
+    extern __shared__ u64 sm[];
+    const KeyDev &K = loc.k(blockIdx.y);
+    u32 l1, l2;
+    split_log(K.logN, l1, l2);
+    const u32 N1 = 1u << l1, N2 = 1u << l2, chunks = N1 / TR;
+    const u32 p = blockIdx.x / chunks, r0 = (blockIdx.x % chunks) * TR;
+    if (p >= per || p >= loc.count(blockIdx.y)) return;
+    u64 *a = loc.poly(blockIdx.y, p) + (size_t)r0 * N2;
+    const u64 Q = K.mq.Q;
+    for (u32 e = threadIdx.x; e < TR * N2; e += NT) sm[e] = a[e];
+    __syncthreads();
+    for (u32 st = 0; st < l2; st++) {
+        const u32 s = INV ? l2 - 1 - st : st;      // stage within the row: global stage l1 + s
+        const u32 half = N2 >> (s + 1);
+        for (u32 b = threadIdx.x; b < TR * (N2 / 2); b += NT) {
+            const u32 rr = b / (N2 / 2), bp = b % (N2 / 2);
+            const u32 g = bp / half, j = bp % half;
+            const u32 o = g * 2 * half + j;
+            u64 *x = sm + rr * N2 + o, *y = x + half;
+            const u32 ti = ((N1 + r0 + rr) << s) + g;
+            if (INV) {
+                const u64 U = *x, V = *y;
+                *x = add_mod(U, V, Q);
+                *y = mul_shoup(U + Q - V, __ldg(K.itw + ti), __ldg(K.itwsh + ti), Q);
+            } else {
+                const u64 U = *x, V = mul_shoup(*y, __ldg(K.tw + ti), __ldg(K.twsh + ti), Q);
+                *x = add_mod(U, V, Q);
+                *y = sub_mod(U, V, Q);
+            }
+        }
+        __syncthreads();
+    }
+    for (u32 e = threadIdx.x; e < TR * N2; e += NT) a[e] = sm[e];
+}
+
+template <class Loc>
+bm_status transform(Loc loc, u32 rows, u32 per, u32 N, bool inverse, cudaStream_t st) {
+    u32 logN = 0;
+    while ((1u << logN) < N) logN++;
+    const u32 l1 = logN / 2, l2 = logN - l1, N1 = 1u << l1, N2 = 1u << l2;
+    if (N1 < TR || N2 < TC) return BM_EINVAL;
+    const size_t smc = (size_t)N1 * TC * 8, smr = (size_t)TR * N2 * 8;
+    auto kc = inverse ? k_cols<true, Loc> : k_cols<false, Loc>;
+    auto kr = inverse ? k_rows<true, Loc> : k_rows<false, Loc>;
+    BM_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+    BM_CUDA_TRY(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    const dim3 gc(per * (N2 / TC), rows), gr(per * (N1 / TR), rows);
+    if (!inverse) {
+        kc<<<gc, NT, smc, st>>>(loc, per);
+        kr<<<gr, NT, smr, st>>>(loc, per);
+    } else {
+        kr<<<gr, NT, smr, st>>>(loc, per);
+        kc<<<gc, NT, smc, st>>>(loc, per);
+    }
+    BM_CUDA_TRY(cudaGetLastError());
+    return BM_OK;
+}
+
+// ACC <- P(b) (0, v_test floor(Q/t)) (blind_rotate.cuh: acc_init), or zero
+// and BM_ENONNEGACYCLIC for a table that is not negacyclic.
+__global__ void k_init(const DevJob *__restrict__ jobs, const u64 *__restrict__ ct_in,
+                       const u32 *__restrict__ luts, u64 *ws, u32 *status) {
+    const DevJob &J = jobs[blockIdx.x];
+    const KeyDev &K = *J.key;
+    u64 *acc0 = ws + J.acc_off;
+    const u32 *lut = luts + J.lut_off;
+    if (!lut_is_negacyclic(lut, J.t)) {
+        if (threadIdx.x == 0) set_status(status, BM_ENONNEGACYCLIC);
+        for (u32 i = threadIdx.x; i < 4 * J.N; i += blockDim.x) acc0[i] = 0;
+        return;
+    }
+    const u32 *gpre = J.gS ? status + J.gpre : nullptr;
+    const u32 qp = 2u * J.N * J.m;
+    acc_init(acc0, lut, ct_in[J.in_off + K.n] % qp, 1, J.t, J.N, K.mq.Q, J.gS, J.gSinv, gpre);
+}
+
+// Digit polynomials of CMux step k (jobs with k < n): combo c = (sign,
+// component, digit) of D = P(-+a_k) ACC - ACC, Eq. (ex1:BPc) with m = 1.
+__global__ void k_digits(const DevJob *__restrict__ jobs, const u64 *__restrict__ ct_in, u64 *ws, u32 k,
+                         const u32 *status) {
+    const DevJob &J = jobs[blockIdx.y];
+    const KeyDev &K = *J.key;
+    if (k >= K.n) return;
+    const u32 N = J.N, lB = K.l_B, log2B = K.log2_B;
+    const u64 Q = K.mq.Q;
+    const u32 qp = 2u * N;
+    const size_t vec = (size_t)2 * N;
+    const u64 *cur = ws + J.acc_off + ((k & 1) ? vec : 0);
+    u64 *X = ws + J.acc_off + 3 * vec;
+    const u32 ak = (u32)(ct_in[J.in_off + k] % qp);
+    const u32 *gpre = J.gS ? status + J.gpre : nullptr;
+    u32 src, e[2];
+    mmpm_row(ak ? qp - ak : 0u, 0, 1, 2 * N, J.gS, gpre, src, e[0]);
+    mmpm_row(ak, 0, 1, 2 * N, J.gS, gpre, src, e[1]);
+    const u64 Bmask = (1ull << log2B) - 1;
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (u32 pair = 0; pair < 4; pair++) {
+            const u32 sgn = pair >> 1, comp = pair & 1;
+            const u64 *row = cur + (size_t)comp * N;
+            const u64 D = sub_mod(rotated_coeff(row, i, e[sgn], N, Q), row[i], Q);
+            for (u32 d = 0; d < lB; d++) X[(size_t)(pair * lB + d) * N + i] = (D >> (d * log2B)) & Bmask;
+        }
+    }
+}
+
+// Multiply-accumulate of step k: row sums (NTT domain) of the 4 l_B digit
+// transforms against the key rows, exact in 128 bits, reduced mod Q.
+__global__ void k_mac(const DevJob *__restrict__ jobs, u64 *ws, u32 k) {
+    const DevJob &J = jobs[blockIdx.y];
+    const KeyDev &K = *J.key;
+    if (k >= K.n) return;
+    const u32 N = J.N, nc = 4 * K.l_B, lb = K.lbits;
+    const size_t vec = (size_t)2 * N;
+    const u64 *X = ws + J.acc_off + 3 * vec;
+    u64 *sums = ws + J.acc_off + 2 * vec;
+    const u64 *bk = K.bsk + (size_t)k * 2 * (2 * K.l_B * 2 * N);
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+        for (u32 c = 0; c < nc; c++) {
+            const u64 x = X[(size_t)c * N + i];
+            const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2 *>(bk + (size_t)c * 2 * N + 2 * i));
+            const u64 b0 = (w.x & 0xffffffffull) + ((w.y & 0xffffffffull) << lb);
+            const u64 b1 = (w.x >> 32) + ((w.y >> 32) << lb);
+            mac128(lo0, hi0, x, b0);
+            mac128(lo1, hi1, x, b1);
+        }
+        sums[i] = reduce128(lo0, hi0, K.mq);
+        sums[N + i] = reduce128(lo1, hi1, K.mq);
+    }
+}
+
+// ACC of step k + 1 = ACC of step k + inverse-transformed row sums.
+__global__ void k_update(const DevJob *__restrict__ jobs, u64 *ws, u32 k) {
+    const DevJob &J = jobs[blockIdx.y];
+    const KeyDev &K = *J.key;
+    if (k >= K.n) return;
+    const size_t vec = (size_t)2 * J.N;
+    const u64 *cur = ws + J.acc_off + ((k & 1) ? vec : 0);
+    u64 *nxt = ws + J.acc_off + ((k & 1) ? 0 : vec);
+    const u64 *sums = ws + J.acc_off + 2 * vec;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < vec; i += (size_t)gridDim.x * blockDim.x)
+        nxt[i] = add_mod(cur[i], sums[i], K.mq.Q);
+}
+
+// RGSW row finish of key generation (the formula of keygen.cu, elementwise):
+// a (mask) and e (error) rows already transformed.
+__global__ void k_bsk_finish(const u64 *__restrict__ a, const u64 *__restrict__ e, const int8_t *__restrict__ s,
+                             const u64 *__restrict__ zhat, u64 *__restrict__ bsk, const KeyDev *Kp, size_t row0) {
+    const KeyDev &K = *Kp;
+    const u32 N = K.N, lB = K.l_B;
+    const u64 Q = K.mq.Q;
+    const size_t r = blockIdx.y, row_id = row0 + r;
+    const u32 row = (u32)(row_id % (2 * lB));
+    const u32 sgn = (u32)((row_id / (2 * lB)) % 2);
+    const int sk = s[row_id / (4 * lB)];
+    const bool mu = sgn == 0 ? sk > 0 : sk < 0;
+    u64 g = 0;
+    if (mu) {
+        u64 gg = 1 % Q;
+        for (u32 d = 0; d < row % lB; d++) {
+            u64 lo = 0, hi = 0;
+            mac128(lo, hi, gg, 1ull << K.log2_B);
+            gg = reduce128(lo, hi, K.mq);
+        }
+        g = gg;
+    }
+    const u64 g0 = row < lB ? g : 0, g1 = row < lB ? 0 : g;
+    const u64 lmask = (1ull << K.lbits) - 1;
+    u64 *o = bsk + row_id * 2 * N;
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const u64 ah = a[r * N + i], eh = e[r * N + i];
+        u64 lo = 0, hi = 0;
+        mac128(lo, hi, ah, zhat[i]);
+        add128(lo, hi, eh);
+        add128(lo, hi, g1);
+        const u64 c1 = reduce128(lo, hi, K.mq);
+        const u64 c0 = add_mod(ah, g0, Q);
+        const u64 w0 = mul_shoup(c0, K.ninv, K.ninv_sh, Q), w1 = mul_shoup(c1, K.ninv, K.ninv_sh, Q);
+        o[2 * i] = (w0 & lmask) | ((w1 & lmask) << 32);
+        o[2 * i + 1] = (w0 >> K.lbits) | ((w1 >> K.lbits) << 32);
+    }
+}
+
+__global__ void k_pointwise(u64 *a, const u64 *__restrict__ b, size_t words, const KeyDev *Kp) {
+    const KeyDev &K = *Kp;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x) {
+        u64 lo = 0, hi = 0;
+        mac128(lo, hi, a[i], b[i]);
+        a[i] = mul_shoup(reduce128(lo, hi, K.mq), K.ninv, K.ninv_sh, K.mq.Q);
+    }
+}
+
+__global__ void k_reduce_copy(u64 *dst, const u64 *__restrict__ src, size_t words, u64 Q) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i] % Q;
+}
+
+}  // namespace bign
+
+size_t bm_big_extra_words(u32 N, u32 l_B) { return N > BM_MAX_N_BLOCK ? (size_t)4 * l_B * N : 0; }
+
+// Forward or inverse transform of `count` contiguous polynomials of key K.
+bm_status bm_big_ntt(u64 *polys, uint32_t count, const KeyDev *d_key, u32 N, bool inverse, cudaStream_t st) {
+    if (!count) return BM_OK;
+    return bign::transform(bign::LocFlat{polys, d_key, count}, 1, count, N, inverse, st);
+}
+
+// BSK rows [row0, row0 + rows) from their transformed masks and errors.
+bm_status bm_big_bsk_finish(const u64 *a, const u64 *e, const int8_t *d_s, const u64 *d_zhat, u64 *d_bsk,
+                            const KeyDev *d_key, u32 N, size_t row0, uint32_t rows, cudaStream_t st) {
+    const dim3 grid((N + 255) / 256 < 64 ? (N + 255) / 256 : 64, rows);
+    bign::k_bsk_finish<<<grid, 256, 0, st>>>(a, e, d_s, d_zhat, d_bsk, d_key, row0);
+    BM_CUDA_TRY(cudaGetLastError());
+    return BM_OK;
+}
+
+// Negacyclic products a b (count pairs of N words, any values below 2^64)
+// through the two-pass transform; scratch: count N words.
+bm_status bm_big_poly_mul(const u64 *a, const u64 *b, uint32_t count, u64 *out, u64 *scratch, const KeyDev *d_key,
+                          u64 Q, u32 N, cudaStream_t st) {
+    const size_t words = (size_t)count * N;
+    const unsigned blocks = (unsigned)((words + 255) / 256 < 4096 ? (words + 255) / 256 : 4096);
+    bign::k_reduce_copy<<<blocks, 256, 0, st>>>(out, a, words, Q);
+    bign::k_reduce_copy<<<blocks, 256, 0, st>>>(scratch, b, words, Q);
+    BM_CUDA_TRY(cudaGetLastError());
+    bm_status s;
+    if ((s = bm_big_ntt(out, count, d_key, N, false, st)) != BM_OK) return s;
+    if ((s = bm_big_ntt(scratch, count, d_key, N, false, st)) != BM_OK) return s;
+    bign::k_pointwise<<<blocks, 256, 0, st>>>(out, scratch, words, d_key);
+    BM_CUDA_TRY(cudaGetLastError());
+    return bm_big_ntt(out, count, d_key, N, true, st);
+}
+
+// Blind rotation of jobs [0, cnt) of `jobs` (device table; ring degree N
+// above 8192, m = 1): CMux steps 0 .. steps - 1 of every job (fewer for jobs
+// whose key has fewer), the final ACC where the one-block kernels leave it.
+bm_status bm_launch_br_big(u32 N, const DevJob *jobs, uint32_t cnt, u32 steps, const uint64_t *ct_in,
+                           const uint32_t *lut, u64 *ws_acc, u32 *status, cudaStream_t st) {
+    if (!cnt) return BM_OK;
+    bign::k_init<<<cnt, 1024, 0, st>>>(jobs, ct_in, lut, ws_acc, status);
+    BM_CUDA_TRY(cudaGetLastError());
+    const unsigned px = (N + 255) / 256;
+    // the grids cover the most digit polynomials a key can have (4 BM_MAX_L_B);
+    // blocks beyond a job's 4 l_B return at once
+    for (u32 k = 0; k < steps; k++) {
+        bign::k_digits<<<dim3(px, cnt), 256, 0, st>>>(jobs, ct_in, ws_acc, k, status);
+        BM_CUDA_TRY(cudaGetLastError());
+        bm_status s = bign::transform(bign::LocJobs{jobs, ws_acc, 0}, cnt, 4 * BM_MAX_L_B, N, false, st);
+        if (s != BM_OK) return s;
+        bign::k_mac<<<dim3(px, cnt), 256, 0, st>>>(jobs, ws_acc, k);
+        BM_CUDA_TRY(cudaGetLastError());
+        if ((s = bign::transform(bign::LocJobs{jobs, ws_acc, 1}, cnt, 2, N, true, st)) != BM_OK) return s;
+        bign::k_update<<<dim3(2 * px, cnt), 256, 0, st>>>(jobs, ws_acc, k);
+        BM_CUDA_TRY(cudaGetLastError());
+    }
+    return BM_OK;
+}

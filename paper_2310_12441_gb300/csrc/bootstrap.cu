@@ -335,6 +335,7 @@ bm_status validate_jobs(const bm_eval_key *const *keys, uint32_t n_keys, const b
         if (j.key >= n_keys || j.reserved) return BM_EINVAL;
         const bm_eval_key *k = keys[j.key];
         if (j.m < 1 || j.m > BM_MAX_M || 2ull * k->p.N * j.m > BM_MAX_QP) return BM_EINVAL;
+        if (k->p.N > BM_MAX_N_BLOCK && j.m != 1) return BM_EINVAL;   // big.cu: the single-polynomial layout
         if (j.t < 2 || (j.t & 1) || (u64)j.t > 2ull * k->p.N * j.m) return BM_EINVAL;
     }
     return BM_OK;
@@ -395,7 +396,7 @@ bm_status make_plan(const bm_eval_key *const *keys, const bm_job *jobs, uint32_t
             d.gpre = (gen_base + 4 * gpos) / 4;
             gpos += m + 1;
         }
-        acc_words += 3ull * 2 * jobs[i].m * k->p.N;
+        acc_words += 3ull * 2 * jobs[i].m * k->p.N + bm_big_extra_words(k->p.N, k->p.l_B);
     }
     pl.classes.clear();
     if (order_by_cost) {
@@ -515,8 +516,18 @@ bm_status run_groups(const Plan &pl, uint32_t first, uint32_t last, u32 steps, c
             mmax = pl.dj[j].m > mmax ? pl.dj[j].m : mmax;
             j++;
         }
-        bm_status s = launch_br_any(N, variant, shapes.s[log2u(N)], d_jobs + i, j - i, mmax, max_cluster, steps,
-                                d_ct_in, d_lut, ws_acc, status, st, dry);
+        bm_status s;
+        if (N > BM_MAX_N_BLOCK) {
+            // the launch covers the most steps any of its keys has
+            u32 nmax = 0;
+            for (uint32_t q = i; q < j; q++) nmax = pl.dj[q].n > nmax ? pl.dj[q].n : nmax;
+            s = dry ? BM_OK
+                    : bm_launch_br_big(N, d_jobs + i, j - i, steps < nmax ? steps : nmax, d_ct_in, d_lut, ws_acc,
+                                       status, st);
+        } else {
+            s = launch_br_any(N, variant, shapes.s[log2u(N)], d_jobs + i, j - i, mmax, max_cluster, steps, d_ct_in,
+                              d_lut, ws_acc, status, st, dry);
+        }
         if (s != BM_OK) return s;
         i = j;
     }
@@ -538,6 +549,9 @@ struct Fork {
 struct KsShape {
     u32 threads, cpt;
     size_t smem;   // digits of all N coefficients (one block per job) + partial sums
+    u32 maxN, maxlks, maxn;
+    // shared memory when S blocks split a job's coefficients
+    size_t smem_for(u32 S) const { return align_up((size_t)(maxN / S) * maxlks, 16) + 8 * (size_t)(maxn + 1); }
 };
 
 KsShape ks_shape(const bm_eval_key *const *keys, uint32_t n_keys) {
@@ -550,7 +564,10 @@ KsShape ks_shape(const bm_eval_key *const *keys, uint32_t n_keys) {
     KsShape k;
     k.cpt = maxn + 1 <= 1024 ? 4 : 8;
     k.threads = k.cpt == 4 ? 256 : ((maxn + 1 + 7) / 8 + 31) / 32 * 32;
-    k.smem = align_up((size_t)maxN * maxlks, 16) + 8 * (size_t)(maxn + 1);
+    k.maxN = maxN;
+    k.maxlks = maxlks;
+    k.maxn = maxn;
+    k.smem = k.smem_for(1);
     return k;
 }
 
@@ -569,14 +586,18 @@ bm_status launch_ks_kernel(Kern kern, uint32_t count, u32 S, const KsShape &ks, 
     static std::atomic<uint64_t> attr_done{0};
     bm_status s = ensure_smem(kern, 96 * 1024, attr_done);
     if (s != BM_OK) return s;
-    if (ks.smem > 96 * 1024) return BM_EINVAL;
+    // large ring degrees (digits of N coefficients above 96 KB) split every
+    // job's coefficients over more blocks of a cluster
+    while (S < 8 && ks.smem_for(S) > 96 * 1024) S *= 2;
+    const size_t smem = ks.smem_for(S);
+    if (smem > 96 * 1024) return BM_EINVAL;
     if (S == 1) {
-        kern<<<count, ks.threads, ks.smem, st>>>(args...);
+        kern<<<count, ks.threads, smem, st>>>(args...);
     } else {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(count * S);
         cfg.blockDim = dim3(ks.threads);
-        cfg.dynamicSmemBytes = ks.smem;
+        cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -807,6 +828,16 @@ extern "C" bm_status bm_poly_mul(const bm_eval_key *key, const uint64_t *d_a, co
     if (!count) return BM_OK;
     DeviceGuard g(key->device);
     const u32 N = key->p.N;
+    if (N > BM_MAX_N_BLOCK) {
+        // two-pass transforms over global memory; scratch for the second operand
+        u64 *scratch = nullptr;
+        BM_CUDA_TRY(cudaMalloc(&scratch, (size_t)count * N * 8));
+        bm_status s = bm_big_poly_mul(d_a, d_b, count, d_out, scratch, key->d_view, key->p.Q, N, (cudaStream_t)stream);
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        cudaFree(scratch);
+        if (s != BM_OK) return s;
+        return e == cudaSuccess ? BM_OK : BM_ECUDA;
+    }
     const size_t smem = 2 * (size_t)N * 8;
     BM_CUDA_TRY(cudaFuncSetAttribute(k_poly_mul, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_poly_mul<<<count, N / 2 < 512 ? N / 2 : 512, smem, (cudaStream_t)stream>>>(key->d_view, d_a, d_b, d_out);
@@ -1064,7 +1095,7 @@ extern "C" void bm_batch_free(bm_batch *b) {
 
 extern "C" bm_status bm_kernel_shape_info(uint32_t shape, uint32_t N, uint32_t *radix, uint32_t *threads,
                                           uint32_t *blocks_per_sm) {
-    if (N < 256 || N > BM_MAX_N || (N & (N - 1)) || shape >= BM_NUM_SHAPES) return BM_EINVAL;
+    if (N < 256 || N > BM_MAX_N_BLOCK || (N & (N - 1)) || shape >= BM_NUM_SHAPES) return BM_EINVAL;
     if (shape != 0 && (N < 1024 || !br_shape_fits((int)log2u(N), (int)shape))) return BM_EINVAL;
     const BrShape b = br_shape((int)shape);
     if (radix) *radix = 1u << b.rb;
@@ -1074,7 +1105,7 @@ extern "C" bm_status bm_kernel_shape_info(uint32_t shape, uint32_t N, uint32_t *
 }
 
 extern "C" bm_status bm_set_kernel_shape(uint32_t N, uint32_t shape) {
-    if (N < 256 || N > BM_MAX_N || (N & (N - 1))) return BM_EINVAL;
+    if (N < 256 || N > BM_MAX_N_BLOCK || (N & (N - 1))) return BM_EINVAL;
     const u32 l = log2u(N);
     if (shape == BM_SHAPE_DEFAULT) shape = kDefaultShape[l];
     if (bm_kernel_shape_info(shape, N, nullptr, nullptr, nullptr) != BM_OK) return BM_EINVAL;
@@ -1083,7 +1114,7 @@ extern "C" bm_status bm_set_kernel_shape(uint32_t N, uint32_t shape) {
 }
 
 extern "C" bm_status bm_get_kernel_shape(uint32_t N, uint32_t *shape) {
-    if (N < 256 || N > BM_MAX_N || (N & (N - 1)) || !shape) return BM_EINVAL;
+    if (N < 256 || N > BM_MAX_N_BLOCK || (N & (N - 1)) || !shape) return BM_EINVAL;
     *shape = g_shape[log2u(N)].load();
     return BM_OK;
 }

@@ -9,7 +9,8 @@
 
 #define BM_MAX_L_B 8
 #define BM_MAX_M 1024   // q' = 2Nm <= 2^23 (u32 arithmetic on exponents)
-#define BM_MAX_N 8192   // largest ring degree (one polynomial per thread block)
+#define BM_MAX_N_BLOCK 8192   // largest ring degree of the one-block kernels
+#define BM_MAX_N 65536        // largest ring degree (above BM_MAX_N_BLOCK: big.cu, m = 1)
 #define BM_MAX_QP (1u << 23)
 
 // Device-resident description of one evaluation key set.  One copy lives in
@@ -164,6 +165,18 @@ bm_status bm_launch_br_n4096(u32 variant, u32 shape, const DevJob *jobs, uint32_
 bm_status bm_launch_br_n8192(u32 variant, u32 shape, const DevJob *jobs, uint32_t cnt, u32 mmax, u32 max_cluster,
                              u32 steps, const uint64_t *ct_in, const uint32_t *lut, u64 *ws_acc, u32 *status,
                              cudaStream_t st, bool dry);
+
+// Ring degrees above BM_MAX_N_BLOCK (big.cu): two-pass transforms in global
+// memory, CMux steps as kernel sequences.  Jobs of such degrees have m = 1 and
+// 4 l_B N more workspace words (their digit polynomials).
+size_t bm_big_extra_words(u32 N, u32 l_B);
+bm_status bm_big_ntt(u64 *polys, uint32_t count, const KeyDev *d_key, u32 N, bool inverse, cudaStream_t st);
+bm_status bm_big_bsk_finish(const u64 *a, const u64 *e, const int8_t *d_s, const u64 *d_zhat, u64 *d_bsk,
+                            const KeyDev *d_key, u32 N, size_t row0, uint32_t rows, cudaStream_t st);
+bm_status bm_big_poly_mul(const u64 *a, const u64 *b, uint32_t count, u64 *out, u64 *scratch, const KeyDev *d_key,
+                          u64 Q, u32 N, cudaStream_t st);
+bm_status bm_launch_br_big(u32 N, const DevJob *jobs, uint32_t cnt, u32 steps, const uint64_t *ct_in,
+                           const uint32_t *lut, u64 *ws_acc, u32 *status, cudaStream_t st);
 
 // Host helpers (keygen.cu)
 bm_status bm_check_key_params(const bm_key_params *p);

@@ -183,6 +183,28 @@ __global__ void k_bsk_rows_seeded(uint64_t seed, rng::Cdt cdt, const int8_t *__r
     bsk_row_finish(sm, row_id, s, zhat, bsk, K);
 }
 
+// Ring degrees above BM_MAX_N_BLOCK (one block cannot transform a row): the
+// rows' masks and errors in Z_Q, [rows][N], for the two-pass transforms of
+// big.cu; seeded (the same streams and indices as k_bsk_rows_seeded) or from
+// caller randomness (errors as int8).
+__global__ void k_big_rows_seeded(uint64_t seed, rng::Cdt cdt, u64 *__restrict__ a, u64 *__restrict__ e, u32 N,
+                                  u64 Q, size_t row0) {
+    const size_t r = blockIdx.y;
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const uint64_t idx = (uint64_t)(row0 + r) * N + i;
+        a[r * N + i] = rng::uniform_mod(rng::element(seed, rng::kBskMask, N, idx), Q);
+        e[r * N + i] = signed_to_zq(rng::gaussian(rng::element(seed, rng::kBskErr, N, idx), cdt), Q);
+    }
+}
+__global__ void k_big_rows_given(const int8_t *__restrict__ err, u64 *__restrict__ e, size_t words, u64 Q) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x)
+        e[i] = signed_to_zq(err[i], Q);
+}
+__global__ void k_big_z(const int8_t *__restrict__ z, u64 *__restrict__ zq, u32 N, u64 Q) {
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        zq[i] = signed_to_zq(z[i], Q);
+}
+
 struct KsGadget { u64 g[16]; };
 
 // Key-switching row `row` = (i, j, v) by one warp: (a', <a', s> + e + v z_i g_j)
@@ -375,14 +397,45 @@ static bm_status keygen_impl(const bm_key_params *params, const int8_t *s, const
     BM_CUDA_TRY(cudaMemcpy(d_z.p, z, N, cudaMemcpyHostToDevice));
 
     const u32 threads = N / 2 < 512 ? N / 2 : 512;
+    const size_t rows_per_k = 2 * 2 * (size_t)lB;
+    const u32 kchunk = 64;
+    if (N > BM_MAX_N_BLOCK) {
+        // z^ and the RGSW rows through the two-pass transforms (big.cu)
+        const unsigned zb = (N + 255) / 256;
+        k_big_z<<<zb, 256>>>((const int8_t *)d_z.p, d_zhat, N, p.Q);
+        BM_CUDA_TRY(cudaGetLastError());
+        bm_status st = bm_big_ntt(d_zhat, 1, ek->d_view, N, false, 0);
+        if (st != BM_OK) return st;
+        DevBuf d_a, d_e, d_err8;
+        BM_CUDA_TRY(cudaMalloc(&d_a.p, kchunk * rows_per_k * N * 8));
+        BM_CUDA_TRY(cudaMalloc(&d_e.p, kchunk * rows_per_k * N * 8));
+        if (src.rnd) BM_CUDA_TRY(cudaMalloc(&d_err8.p, kchunk * rows_per_k * N));
+        for (u32 k0 = 0; k0 < n; k0 += kchunk) {
+            const u32 k1 = k0 + kchunk < n ? k0 + kchunk : n;
+            const size_t rows = (size_t)(k1 - k0) * rows_per_k, row0 = (size_t)k0 * rows_per_k;
+            if (src.rnd) {
+                BM_CUDA_TRY(cudaMemcpy(d_a.p, src.rnd->bsk_mask + row0 * N, rows * N * 8, cudaMemcpyHostToDevice));
+                BM_CUDA_TRY(cudaMemcpy(d_err8.p, src.rnd->bsk_err + row0 * N, rows * N, cudaMemcpyHostToDevice));
+                k_big_rows_given<<<4096, 256>>>((const int8_t *)d_err8.p, (u64 *)d_e.p, rows * N, p.Q);
+            } else {
+                k_big_rows_seeded<<<dim3(zb < 64 ? zb : 64, (unsigned)rows), 256>>>(src.seed, src.cdt, (u64 *)d_a.p,
+                                                                                     (u64 *)d_e.p, N, p.Q, row0);
+            }
+            BM_CUDA_TRY(cudaGetLastError());
+            if ((st = bm_big_ntt((u64 *)d_a.p, (u32)rows, ek->d_view, N, false, 0)) != BM_OK) return st;
+            if ((st = bm_big_ntt((u64 *)d_e.p, (u32)rows, ek->d_view, N, false, 0)) != BM_OK) return st;
+            if ((st = bm_big_bsk_finish((const u64 *)d_a.p, (const u64 *)d_e.p, (const int8_t *)d_s.p, d_zhat,
+                                        ek->d_bsk, ek->d_view, N, row0, (u32)rows, 0)) != BM_OK)
+                return st;
+            BM_CUDA_TRY(cudaDeviceSynchronize());
+        }
+    } else {
     BM_CUDA_TRY(cudaFuncSetAttribute(k_ntt_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(N * 8)));
     k_ntt_z<<<1, threads, N * 8>>>((const int8_t *)d_z.p, d_zhat, K);
     BM_CUDA_TRY(cudaGetLastError());
 
     // Bootstrapping keys: one RGSW row per block, in chunks of key indices
     // (which bounds the staging memory of caller-supplied randomness).
-    const size_t rows_per_k = 2 * 2 * (size_t)lB;
-    const u32 kchunk = 64;
     if (src.rnd) {
         DevBuf d_mask, d_err;
         BM_CUDA_TRY(cudaMalloc(&d_mask.p, kchunk * rows_per_k * N * 8));
@@ -414,6 +467,7 @@ static bm_status keygen_impl(const bm_key_params *params, const int8_t *s, const
             BM_CUDA_TRY(cudaGetLastError());
         }
         BM_CUDA_TRY(cudaDeviceSynchronize());
+    }
     }
     // Key-switching keys: one LWE row per warp.
     KsGadget G;
