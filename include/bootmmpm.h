@@ -57,7 +57,9 @@ typedef int32_t bm_status;
  * shape (m, t) with the same N. */
 typedef struct bm_key_params {
     uint32_t n;         /* LWE dimension */
-    uint32_t N;         /* ring degree, power of two, 256..8192 */
+    uint32_t N;         /* ring degree, power of two, 256..65536; above 8192 only jobs
+                           with m = 1 (the single-polynomial layout) run, through
+                           two-pass transforms in global memory */
     uint32_t log2_B;    /* blind-rotation gadget base B = 2^log2_B */
     uint32_t l_B;       /* gadget digits, B^l_B >= Q, 2 <= l_B <= 8 */
     uint32_t log2_Bks;  /* key-switching base B_ks = 2^log2_Bks, <= 8 */
@@ -88,7 +90,8 @@ typedef struct bm_eval_key bm_eval_key;
 /* One bootstrapping job (Definition 1): ciphertext, table, shape, key set. */
 typedef struct bm_job {
     uint32_t key;       /* index into the key array of the call */
-    uint32_t m;         /* polynomials in the test vector, 1..1024, with 2Nm <= 2^23 */
+    uint32_t m;         /* polynomials in the test vector, 1..1024, with 2Nm <= 2^23
+                           (1 for N above 8192) */
     uint32_t t;         /* plaintext modulus, even, 2 <= t <= 2Nm */
     uint32_t reserved;  /* must be 0 */
     uint64_t in_off;    /* element offset of the input LWE_{n,2Nm} (n+1 words) */
@@ -257,7 +260,9 @@ bm_status bm_key_switch(const bm_eval_key *key, const uint64_t *d_lwe_in,
                         uint32_t count, uint64_t *d_out, void *stream);
 
 /* Negacyclic products in R_{N,Q} (Section 2 item (6)) through the library's
- * NTT: d_out[i] = d_a[i] * d_b[i] for `count` pairs of N coefficients. */
+ * NTT: d_out[i] = d_a[i] * d_b[i] for `count` pairs of N coefficients.  For
+ * N above 8192 the call allocates count N words of device scratch and
+ * returns after the stream has finished. */
 bm_status bm_poly_mul(const bm_eval_key *key, const uint64_t *d_a,
                       const uint64_t *d_b, uint32_t count, uint64_t *d_out,
                       void *stream);
