@@ -47,3 +47,17 @@ def test_seeded_calls_reject_bad_arguments(api):
     for sigma in (0.0, -1.0, 4.5):
         with pytest.raises(api.BMError):
             api.bm_encrypt_seeded(sk, 1024, 32, np.zeros(2, np.uint32), 5, sigma=sigma)
+
+
+def test_ring_degree_range_on_the_host(api, orc):
+    """Key parameters are accepted up to ring degree 65536 (above 8192 the
+    single-polynomial layout runs through two-pass transforms) and refused
+    beyond; the secret key of a 65536-coefficient set still equals the
+    oracle's draws."""
+    kp = P.KeyParams(**{**P.KEYS_SWEEP_N2048.__dict__, "n": 16, "N": 65536})
+    sk = api.bm_secret_key_seeded(kp, 5)
+    s, z = api.bm_secret_key_get(sk)
+    want = orc.seeded_key_randomness(kp, 5, bsk_keys=0, with_ksk=False)
+    assert np.array_equal(s, want["s"]) and np.array_equal(z, want["z"])
+    with pytest.raises(api.BMError):
+        api.bm_secret_key_seeded(P.KeyParams(**{**kp.__dict__, "N": 131072}), 5)
