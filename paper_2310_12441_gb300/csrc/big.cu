@@ -130,6 +130,21 @@ __global__ void __launch_bounds__(NT) k_rows(Loc loc, u32 per) {
     for (u32 e = threadIdx.x; e < TR * N2; e += NT) a[e] = sm[e];
 }
 
+// The row pass alone (the step's inverse starts with it).
+template <class Loc>
+bm_status transform_rows(Loc loc, u32 rows, u32 per, u32 N, bool inverse, cudaStream_t st) {
+    u32 logN = 0;
+    while ((1u << logN) < N) logN++;
+    const u32 l1 = logN / 2, l2 = logN - l1, N1 = 1u << l1, N2 = 1u << l2;
+    if (N1 < TR) return BM_EINVAL;
+    const size_t smr = (size_t)TR * N2 * 8;
+    auto kr = inverse ? k_rows<true, Loc> : k_rows<false, Loc>;
+    BM_CUDA_TRY(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    kr<<<dim3(per * (N1 / TR), rows), NT, smr, st>>>(loc, per);
+    BM_CUDA_TRY(cudaGetLastError());
+    return BM_OK;
+}
+
 template <class Loc>
 bm_status transform(Loc loc, u32 rows, u32 per, u32 N, bool inverse, cudaStream_t st) {
     u32 logN = 0;
@@ -171,73 +186,152 @@ __global__ void k_init(const DevJob *__restrict__ jobs, const u64 *__restrict__ 
     acc_init(acc0, lut, ct_in[J.in_off + K.n] % qp, 1, J.t, J.N, K.mq.Q, J.gS, J.gSinv, gpre);
 }
 
-// Digit polynomials of CMux step k (jobs with k < n): combo c = (sign,
-// component, digit) of D = P(-+a_k) ACC - ACC, Eq. (ex1:BPc) with m = 1.
-__global__ void k_digits(const DevJob *__restrict__ jobs, const u64 *__restrict__ ct_in, u64 *ws, u32 k,
-                         const u32 *status) {
+// ---- Step kernels: digits fused into the forward column pass, the
+// multiply-accumulate into the forward row pass, the accumulator update into
+// the inverse column pass (three passes over the digit polynomials per step
+// where separate kernels made six).
+
+// Digits + forward column pass of step k: block (x = pair (N2 / TC) + chunk,
+// y = job) builds the difference of (sign, component) pair `pair` on its TC
+// columns, then for every digit transforms the digit columns (stages
+// 0 .. log N1 - 1) into the job's digit polynomial pair l_B + d.  smem:
+// 2 N1 TC words (the difference, the digit tile).
+__global__ void __launch_bounds__(NT) k_digits_cols(const DevJob *__restrict__ jobs, const u64 *__restrict__ ct_in,
+                                                    u64 *ws, u32 k, const u32 *status) {
+    extern __shared__ u64 sm[];
     const DevJob &J = jobs[blockIdx.y];
     const KeyDev &K = *J.key;
     if (k >= K.n) return;
-    const u32 N = J.N, lB = K.l_B, log2B = K.log2_B;
-    const u64 Q = K.mq.Q;
-    const u32 qp = 2u * N;
+    u32 l1, l2;
+    split_log(K.logN, l1, l2);
+    const u32 N = J.N, N1 = 1u << l1, N2 = 1u << l2, chunks = N2 / TC;
+    const u32 pair = blockIdx.x / chunks, c0 = (blockIdx.x % chunks) * TC;
+    const u32 lB = K.l_B, log2B = K.log2_B;
+    const u64 Q = K.mq.Q, Bmask = (1ull << log2B) - 1;
     const size_t vec = (size_t)2 * N;
     const u64 *cur = ws + J.acc_off + ((k & 1) ? vec : 0);
     u64 *X = ws + J.acc_off + 3 * vec;
+    const u32 qp = 2u * N;
     const u32 ak = (u32)(ct_in[J.in_off + k] % qp);
     const u32 *gpre = J.gS ? status + J.gpre : nullptr;
-    u32 src, e[2];
-    mmpm_row(ak ? qp - ak : 0u, 0, 1, 2 * N, J.gS, gpre, src, e[0]);
-    mmpm_row(ak, 0, 1, 2 * N, J.gS, gpre, src, e[1]);
-    const u64 Bmask = (1ull << log2B) - 1;
-    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-#pragma unroll
-        for (u32 pair = 0; pair < 4; pair++) {
-            const u32 sgn = pair >> 1, comp = pair & 1;
-            const u64 *row = cur + (size_t)comp * N;
-            const u64 D = sub_mod(rotated_coeff(row, i, e[sgn], N, Q), row[i], Q);
-            for (u32 d = 0; d < lB; d++) X[(size_t)(pair * lB + d) * N + i] = (D >> (d * log2B)) & Bmask;
+    const u32 sgn = pair >> 1, comp = pair & 1;
+    u32 src, e;
+    mmpm_row(sgn == 0 ? (ak ? qp - ak : 0u) : ak, 0, 1, 2 * N, J.gS, gpre, src, e);
+    const u64 *row = cur + (size_t)comp * N;
+    u64 *Dt = sm, *tile = sm + N1 * TC;
+    for (u32 x = threadIdx.x; x < N1 * TC; x += NT) {
+        const u32 i = c0 + x % TC + N2 * (x / TC);
+        Dt[x] = sub_mod(rotated_coeff(row, i, e, N, Q), row[i], Q);
+    }
+    for (u32 d = 0; d < lB; d++) {
+        __syncthreads();     // the difference is complete; the previous digit's tile is stored
+        for (u32 x = threadIdx.x; x < N1 * TC; x += NT) tile[x] = (Dt[x] >> (d * log2B)) & Bmask;
+        __syncthreads();
+        for (u32 s = 0; s < l1; s++) {
+            const u32 half = N1 >> (s + 1);
+            for (u32 b = threadIdx.x; b < (N1 / 2) * TC; b += NT) {
+                const u32 bp = b / TC, cc = b % TC;
+                const u32 g = bp / half, j = bp % half;
+                const u32 t = g * 2 * half + j;
+                u64 *x = tile + t * TC + cc, *y = tile + (t + half) * TC + cc;
+                const u32 ti = (1u << s) + g;
+                const u64 U = *x, V = mul_shoup(*y, __ldg(K.tw + ti), __ldg(K.twsh + ti), Q);
+                *x = add_mod(U, V, Q);
+                *y = sub_mod(U, V, Q);
+            }
+            __syncthreads();
         }
+        u64 *a = X + (size_t)(pair * lB + d) * N;
+        for (u32 x = threadIdx.x; x < N1 * TC; x += NT) a[c0 + x % TC + (size_t)N2 * (x / TC)] = tile[x];
     }
 }
 
-// Multiply-accumulate of step k: row sums (NTT domain) of the 4 l_B digit
-// transforms against the key rows, exact in 128 bits, reduced mod Q.
-__global__ void k_mac(const DevJob *__restrict__ jobs, u64 *ws, u32 k) {
+// Forward row pass of all 4 l_B digit polynomials on rows [r0, r0 + trm),
+// then the multiply-accumulate of those positions against the key rows of
+// step k (exact 128-bit sums, reduced) into the job's row sums.
+// Block (x = row chunk, y = job); smem: 4 l_B trm N2 words.
+__global__ void __launch_bounds__(NT) k_rows_mac(const DevJob *__restrict__ jobs, u64 *ws, u32 k, u32 trm) {
+    extern __shared__ u64 sm[];
     const DevJob &J = jobs[blockIdx.y];
     const KeyDev &K = *J.key;
     if (k >= K.n) return;
-    const u32 N = J.N, nc = 4 * K.l_B, lb = K.lbits;
+    u32 l1, l2;
+    split_log(K.logN, l1, l2);
+    const u32 N = J.N, N1 = 1u << l1, N2 = 1u << l2;
+    const u32 r0 = blockIdx.x * trm, nc = 4 * K.l_B, lb = K.lbits, w = trm * N2;
+    const u64 Q = K.mq.Q;
     const size_t vec = (size_t)2 * N;
     const u64 *X = ws + J.acc_off + 3 * vec;
     u64 *sums = ws + J.acc_off + 2 * vec;
+    for (u32 x = threadIdx.x; x < nc * w; x += NT) sm[x] = X[(size_t)(x / w) * N + (size_t)r0 * N2 + x % w];
+    __syncthreads();
+    for (u32 s = 0; s < l2; s++) {
+        const u32 half = N2 >> (s + 1);
+        for (u32 b = threadIdx.x; b < nc * trm * (N2 / 2); b += NT) {
+            const u32 pr = b / (N2 / 2), bp = b % (N2 / 2);      // pr = c trm + rr
+            const u32 g = bp / half, j = bp % half;
+            const u32 o = g * 2 * half + j;
+            u64 *x = sm + (size_t)pr * N2 + o, *y = x + half;
+            const u32 ti = ((N1 + r0 + pr % trm) << s) + g;
+            const u64 U = *x, V = mul_shoup(*y, __ldg(K.tw + ti), __ldg(K.twsh + ti), Q);
+            *x = add_mod(U, V, Q);
+            *y = sub_mod(U, V, Q);
+        }
+        __syncthreads();
+    }
     const u64 *bk = K.bsk + (size_t)k * 2 * (2 * K.l_B * 2 * N);
-    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (u32 pos = threadIdx.x; pos < w; pos += NT) {
+        const size_t i = (size_t)r0 * N2 + pos;
         u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
         for (u32 c = 0; c < nc; c++) {
-            const u64 x = X[(size_t)c * N + i];
-            const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2 *>(bk + (size_t)c * 2 * N + 2 * i));
-            const u64 b0 = (w.x & 0xffffffffull) + ((w.y & 0xffffffffull) << lb);
-            const u64 b1 = (w.x >> 32) + ((w.y >> 32) << lb);
-            mac128(lo0, hi0, x, b0);
-            mac128(lo1, hi1, x, b1);
+            const u64 x = sm[(size_t)c * w + pos];
+            const ulonglong2 wv = __ldg(reinterpret_cast<const ulonglong2 *>(bk + (size_t)c * 2 * N + 2 * i));
+            mac128(lo0, hi0, x, (wv.x & 0xffffffffull) + ((wv.y & 0xffffffffull) << lb));
+            mac128(lo1, hi1, x, (wv.x >> 32) + ((wv.y >> 32) << lb));
         }
         sums[i] = reduce128(lo0, hi0, K.mq);
         sums[N + i] = reduce128(lo1, hi1, K.mq);
     }
 }
 
-// ACC of step k + 1 = ACC of step k + inverse-transformed row sums.
-__global__ void k_update(const DevJob *__restrict__ jobs, u64 *ws, u32 k) {
+// Inverse column pass of the two row sums (stages log N1 - 1 .. 0) fused
+// with the accumulator update of step k.  Block (x = comp (N2 / TC) +
+// chunk, y = job); smem N1 TC words.
+__global__ void __launch_bounds__(NT) k_cols_inv_update(const DevJob *__restrict__ jobs, u64 *ws, u32 k) {
+    extern __shared__ u64 sm[];
     const DevJob &J = jobs[blockIdx.y];
     const KeyDev &K = *J.key;
     if (k >= K.n) return;
-    const size_t vec = (size_t)2 * J.N;
-    const u64 *cur = ws + J.acc_off + ((k & 1) ? vec : 0);
-    u64 *nxt = ws + J.acc_off + ((k & 1) ? 0 : vec);
-    const u64 *sums = ws + J.acc_off + 2 * vec;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < vec; i += (size_t)gridDim.x * blockDim.x)
-        nxt[i] = add_mod(cur[i], sums[i], K.mq.Q);
+    u32 l1, l2;
+    split_log(K.logN, l1, l2);
+    const u32 N = J.N, N1 = 1u << l1, N2 = 1u << l2, chunks = N2 / TC;
+    const u32 comp = blockIdx.x / chunks, c0 = (blockIdx.x % chunks) * TC;
+    const u64 Q = K.mq.Q;
+    const size_t vec = (size_t)2 * N;
+    const u64 *cur = ws + J.acc_off + ((k & 1) ? vec : 0) + (size_t)comp * N;
+    u64 *nxt = ws + J.acc_off + ((k & 1) ? 0 : vec) + (size_t)comp * N;
+    const u64 *a = ws + J.acc_off + 2 * vec + (size_t)comp * N;
+    for (u32 x = threadIdx.x; x < N1 * TC; x += NT) sm[x] = a[c0 + x % TC + (size_t)N2 * (x / TC)];
+    __syncthreads();
+    for (u32 st = 0; st < l1; st++) {
+        const u32 s = l1 - 1 - st;
+        const u32 half = N1 >> (s + 1);
+        for (u32 b = threadIdx.x; b < (N1 / 2) * TC; b += NT) {
+            const u32 bp = b / TC, cc = b % TC;
+            const u32 g = bp / half, j = bp % half;
+            const u32 t = g * 2 * half + j;
+            u64 *x = sm + t * TC + cc, *y = sm + (t + half) * TC + cc;
+            const u32 ti = (1u << s) + g;
+            const u64 U = *x, V = *y;
+            *x = add_mod(U, V, Q);
+            *y = mul_shoup(U + Q - V, __ldg(K.itw + ti), __ldg(K.itwsh + ti), Q);
+        }
+        __syncthreads();
+    }
+    for (u32 x = threadIdx.x; x < N1 * TC; x += NT) {
+        const size_t i = c0 + x % TC + (size_t)N2 * (x / TC);
+        nxt[i] = add_mod(cur[i], sm[x], Q);
+    }
 }
 
 // RGSW row finish of key generation (the formula of keygen.cu, elementwise):
@@ -337,18 +431,29 @@ bm_status bm_launch_br_big(u32 N, const DevJob *jobs, uint32_t cnt, u32 steps, c
     if (!cnt) return BM_OK;
     bign::k_init<<<cnt, 1024, 0, st>>>(jobs, ct_in, lut, ws_acc, status);
     BM_CUDA_TRY(cudaGetLastError());
-    const unsigned px = (N + 255) / 256;
-    // the grids cover the most digit polynomials a key can have (4 BM_MAX_L_B);
-    // blocks beyond a job's 4 l_B return at once
+    u32 logN = 0;
+    while ((1u << logN) < N) logN++;
+    const u32 l1 = logN / 2, l2 = logN - l1, N1 = 1u << l1, N2 = 1u << l2;
+    // rows per block of the row pass + multiply-accumulate: the digit rows of
+    // every combo a key can have (4 BM_MAX_L_B) within 64 KB
+    const u32 ncmax = 4 * BM_MAX_L_B;
+    u32 trm = 8192 / (ncmax * N2);
+    trm = trm < 1 ? 1 : trm > N1 ? N1 : trm;
+    const size_t sm_dc = (size_t)2 * N1 * bign::TC * 8, sm_rm = (size_t)ncmax * trm * N2 * 8,
+                 sm_ci = (size_t)N1 * bign::TC * 8;
+    BM_CUDA_TRY(cudaFuncSetAttribute(bign::k_digits_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_dc));
+    BM_CUDA_TRY(cudaFuncSetAttribute(bign::k_rows_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rm));
+    BM_CUDA_TRY(cudaFuncSetAttribute(bign::k_cols_inv_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm_ci));
+    const dim3 g_dc(4 * (N2 / bign::TC), cnt), g_rm(N1 / trm, cnt), g_ci(2 * (N2 / bign::TC), cnt);
     for (u32 k = 0; k < steps; k++) {
-        bign::k_digits<<<dim3(px, cnt), 256, 0, st>>>(jobs, ct_in, ws_acc, k, status);
+        bign::k_digits_cols<<<g_dc, bign::NT, sm_dc, st>>>(jobs, ct_in, ws_acc, k, status);
+        bign::k_rows_mac<<<g_rm, bign::NT, sm_rm, st>>>(jobs, ws_acc, k, trm);
         BM_CUDA_TRY(cudaGetLastError());
-        bm_status s = bign::transform(bign::LocJobs{jobs, ws_acc, 0}, cnt, 4 * BM_MAX_L_B, N, false, st);
+        // inverse: row pass of the two sums, then the column pass with the update
+        bm_status s = bign::transform_rows(bign::LocJobs{jobs, ws_acc, 1}, cnt, 2, N, true, st);
         if (s != BM_OK) return s;
-        bign::k_mac<<<dim3(px, cnt), 256, 0, st>>>(jobs, ws_acc, k);
-        BM_CUDA_TRY(cudaGetLastError());
-        if ((s = bign::transform(bign::LocJobs{jobs, ws_acc, 1}, cnt, 2, N, true, st)) != BM_OK) return s;
-        bign::k_update<<<dim3(2 * px, cnt), 256, 0, st>>>(jobs, ws_acc, k);
+        bign::k_cols_inv_update<<<g_ci, bign::NT, sm_ci, st>>>(jobs, ws_acc, k);
         BM_CUDA_TRY(cudaGetLastError());
     }
     return BM_OK;
