@@ -277,7 +277,8 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     constexpr int R = C::R;
     constexpr int N = C::N, G = C::G, CPB = C::CPB;
     const KeyDev *K = J.key;
-    const u32 lbits = J.lbits;
+    // (keys of the Q = c 2^32 + 1 kernels have 30-bit limbs: choose_variant)
+    const u32 lbits = QLOW1 ? 30u : J.lbits;
     const bool fold_each = J.fold_each != 0;
     const u32 m = J.m, t = J.t, lB = K->l_B, log2B = K->log2_B, n = K->n;
     const ModQ mq = K->mq;
@@ -347,6 +348,26 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     // (each below 2^32: no carry crosses the halves).
     const u32 lmask32 = (u32)lmask;
     auto kara2 = [&](u64 xv, u64 w0, u64 w1, u64 (&kh)[2], u64 (&kl)[2], u64 (&km)[2]) {
+        if constexpr (QLOW1) {
+            asm("{\n\t.reg .u32 v0, v1, x0, x1, xs, a0, a1, as, c0, c1, cs;\n\t.reg .u64 s;\n\t"
+                "mov.b64 {v0, v1}, %6;\n\t"
+                "shf.r.clamp.b32 x1, v0, v1, 30;\n\t"
+                "and.b32 x0, v0, 1073741823;\n\t"
+                "add.u32 xs, x0, x1;\n\t"
+                "mov.b64 {a0, c0}, %7;\n\t"
+                "mov.b64 {a1, c1}, %8;\n\t"
+                "add.u64 s, %7, %8;\n\t"
+                "mov.b64 {as, cs}, s;\n\t"
+                "mad.wide.u32 %0, x1, a1, %0;\n\t"
+                "mad.wide.u32 %1, x0, a0, %1;\n\t"
+                "mad.wide.u32 %2, xs, as, %2;\n\t"
+                "mad.wide.u32 %3, x1, c1, %3;\n\t"
+                "mad.wide.u32 %4, x0, c0, %4;\n\t"
+                "mad.wide.u32 %5, xs, cs, %5;\n\t}"
+                : "+l"(kh[0]), "+l"(kl[0]), "+l"(km[0]), "+l"(kh[1]), "+l"(kl[1]), "+l"(km[1])
+                : "l"(xv), "l"(w0), "l"(w1));
+            return;
+        }
         asm("{\n\t.reg .u32 v0, v1, x0, x1, xs, a0, a1, as, c0, c1, cs;\n\t.reg .u64 s;\n\t"
             "mov.b64 {v0, v1}, %6;\n\t"
             "shf.r.clamp.b32 x1, v0, v1, %9;\n\t"

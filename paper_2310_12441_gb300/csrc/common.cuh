@@ -67,9 +67,14 @@ inline u32 choose_variant(const bm_key_params &p) {
     const u128 lim = (u128)1 << 64, Q = p.Q, B = (u128)1 << p.log2_B;
     u32 v = 0;
     // (Q < 2^60 keeps every value the Q = c 2^32 + 1 butterflies correct below 2^63)
-    const bool qlow1 = (p.Q & 0xffffffffull) == 1 && p.Q < (1ull << 60);
+    bool qlow1 = (p.Q & 0xffffffffull) == 1 && p.Q < (1ull << 60);
+    // the Q = c 2^32 + 1 kernels also fix the multiply-accumulate's limbs at
+    // 30 bits (limb_plan: the transform outputs' bound below 2^60, above 2^58)
+    const bool lazy1 = (1 + 4 * (u128)logN) * Q < ((u128)1 << 62) && 128 * Q < lim;
+    const u128 xmax1 = lazy1 ? (1 + 4 * (u128)logN) * Q : Q;
+    if (qlow1 && !(xmax1 - 1 >= ((u128)1 << 58) && xmax1 - 1 < ((u128)1 << 60))) qlow1 = false;
     if (qlow1) {
-        if ((1 + 4 * (u128)logN) * Q < ((u128)1 << 62) && 128 * Q < lim) v |= BR_V_LAZY;
+        if (lazy1) v |= BR_V_LAZY;
         v |= BR_V_QLOW1;
     } else if ((1 + 4 * (u128)logN) * Q < lim && p.log2_B <= 31 && B + Q * B + 4 * Q * (logN - 1) < lim &&
                128 * Q < lim) {
