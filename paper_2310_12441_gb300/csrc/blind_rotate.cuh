@@ -325,6 +325,10 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
         tws[2 * pos] = __ldg(twp + 2 * src);
         tws[2 * pos + 1] = __ldg(twp + 2 * src + 1);
     }
+    // combo c = (pair, digit) as pair | (digit log2 B) << 8, so the batches
+    // find their digit without dividing by the runtime l_B
+    __shared__ u32 ctab[4 * BM_MAX_L_B];
+    if (tid < 4 * lB) ctab[tid] = (tid / lB) | (((tid % lB) * log2B) << 8);
     if (split) cluster_sync(); else __syncthreads();
     mbar_arrive(mac_bar);
 
@@ -510,8 +514,9 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                     // difference; every thread read the previous pair's before
                     // the previous batch's barrier preceding its
                     // multiply-accumulate
-                    if (dpair && c0 % lB == 0) {
-                        build_d(0, c0 / lB, dbuf);
+                    const u32 b0 = ctab[c0];
+                    if (dpair && (b0 >> 8) == 0) {
+                        build_d(0, b0 & 255u, dbuf);
                         __syncthreads();
                     }
                 }
@@ -519,8 +524,9 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
                 const u32 c = c0 + pc, r = r0 + pg;
                 const bool active = pc < (u32)CPB && c < ncomb && r < m;
                 u64 x[R];
+                const u32 ce = ctab[c < ncomb ? c : 0u];
+                const u32 pair = ce & 255u, sh = ce >> 8;
                 if (active) {
-                    const u32 pair = c / lB, sh = (c % lB) * log2B;
                     if (C::DSM || dpair) {
                         const u64 *dp = dbuf + (C::DSM ? ((size_t)pg * 4 + pair) * N : 0);
 #pragma unroll
