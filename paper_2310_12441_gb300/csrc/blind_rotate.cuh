@@ -108,9 +108,10 @@ static __device__ bool lut_is_negacyclic(const u32 *__restrict__ lut, u32 t) {
 //  - otherwise a generator A = (x^{u_i} delta_{i-1 mod m, j}) of Theorem 1 with
 //    S = sum u = gS and pre[k] = u_0 + ... + u_{k-1} (all mod 2N):
 //    E_c(i) = a S + sum_{t in [b]} u_{(i - t) mod m}.
-__device__ __forceinline__ void mmpm_row(u32 c, u32 i, u32 m, u32 twoN, u32 gS, const u32 *pre, u32 &src,
-                                         u32 &e) {
-    const u32 a = c / m, b = c % m;
+// (mmpm_row_ab takes a = c / m and b = c mod m, which the rows of one CMux
+// step share; 2N is a power of two.)
+__device__ __forceinline__ void mmpm_row_ab(u32 a, u32 b, u32 i, u32 m, u32 twoN, u32 gS, const u32 *pre,
+                                            u32 &src, u32 &e) {
     src = i >= b ? i - b : i + m - b;
     if (!gS) {
         e = i >= b ? a : a + 1;
@@ -119,7 +120,11 @@ __device__ __forceinline__ void mmpm_row(u32 c, u32 i, u32 m, u32 twoN, u32 gS, 
     }
     u32 w = 0;
     if (b != 0) w = b <= i + 1 ? pre[i + 1] + twoN - pre[i + 1 - b] : pre[i + 1] + pre[m] + twoN - pre[m + i + 1 - b];
-    e = (u32)(((u64)a * gS + w) % twoN);
+    e = (u32)(((u64)a * gS + w) & (twoN - 1));
+}
+__device__ __forceinline__ void mmpm_row(u32 c, u32 i, u32 m, u32 twoN, u32 gS, const u32 *pre, u32 &src,
+                                         u32 &e) {
+    mmpm_row_ab(c / m, c % m, i, m, twoN, gS, pre, src, e);
 }
 
 // ACC <- P(b) (0, v_test floor(Q/t)) with the negacyclic extension
@@ -397,7 +402,17 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
     u64 *cur = acc0, *nxt = acc1;
     const u32 steps = steps_limit < n ? steps_limit : n;
     for (u32 k = 0; k < steps; k++) {
-        const u32 ak = (u32)(ct[k] % qp);
+        // a_k mod q' (q' = 2Nm is a power of two for power-of-two m); the
+        // rows of the step share c = -a_k, a_k and their quotients by m
+        const u64 ctk = ct[k];
+        const u32 ak = (qp & (qp - 1)) == 0 ? (u32)ctk & (qp - 1) : (u32)(ctk % qp);
+        u32 ca[2], cb[2];
+#pragma unroll
+        for (int sg = 0; sg < 2; sg++) {
+            const u32 cv = sg == 0 ? (ak ? qp - ak : 0u) : ak;
+            ca[sg] = cv / m;
+            cb[sg] = cv - ca[sg] * m;
+        }
         const u64 *bsk_k = K->bsk + (size_t)k * 2 * rgsw;
         for (u32 r0 = crank * G; r0 < m; r0 += G * csize) {
             u64 lo[G][2][C::PPTR], hi[G][2][C::PPTR];
@@ -426,8 +441,7 @@ __device__ __forceinline__ void br_job(const DevJob &J, u32 steps_limit, const u
 #pragma unroll
                 for (int sg = 0; sg < 2; sg++) {
                     const u32 r = r0 + g;
-                    const u32 cv = sg == 0 ? (ak ? qp - ak : 0u) : ak;
-                    mmpm_row(cv, r < m ? r : 0, m, 2 * N, J.gS, gpre, rsrc[g][sg], rexp[g][sg]);
+                    mmpm_row_ab(ca[sg], cb[sg], r < m ? r : 0, m, 2 * N, J.gS, gpre, rsrc[g][sg], rexp[g][sg]);
                 }
             // D_(row, sign, comp) = P(c) ACC - ACC into drow: coefficient idx of
             // x^e src is src[idx - e] for idx >= e, else -src[idx - e + N]
