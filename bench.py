@@ -50,7 +50,7 @@ METRIC = "bootstraps/s on 1 GB300 (batched vs plain, bit-exact); p50/p99 served 
 # hash to the captured version.
 KERNEL_SOURCES = ["blind_rotate.cuh", "ntt_reg.cuh", "modarith.cuh", "common.cuh", "br_launch.cuh"]
 CAPTURED_TRAFFIC = {
-    P.BATCH_N1024.name: {"hash": "77db4d2db596fff8", "bytes_per_job": (255.134464e6 + 6.314752e6) / 152},
+    P.BATCH_N1024.name: {"hash": "2e5795488aa486bf", "bytes_per_job": (254.637056e6 + 6.749184e6) / 152},
 }
 
 
