@@ -69,10 +69,10 @@ __global__ void __launch_bounds__(NT) k_cols(Loc loc, u32 per) {
     __syncthreads();
     for (u32 st = 0; st < l1; st++) {
         const u32 s = INV ? l1 - 1 - st : st;
-        const u32 half = N1 >> (s + 1);
+        const u32 lh = l1 - 1 - s, half = 1u << lh;
         for (u32 b = threadIdx.x; b < (N1 / 2) * TC; b += NT) {
             const u32 bp = b / TC, cc = b % TC;
-            const u32 g = bp / half, j = bp % half;
+            const u32 g = bp >> lh, j = bp & (half - 1);
             const u32 t = g * 2 * half + j;
             u64 *x = sm + t * TC + cc, *y = sm + (t + half) * TC + cc;
             const u32 ti = (1u << s) + g;
@@ -108,10 +108,10 @@ __global__ void __launch_bounds__(NT) k_rows(Loc loc, u32 per) {
     __syncthreads();
     for (u32 st = 0; st < l2; st++) {
         const u32 s = INV ? l2 - 1 - st : st;      // stage within the row: global stage l1 + s
-        const u32 half = N2 >> (s + 1);
+        const u32 lh = l2 - 1 - s, half = 1u << lh;
         for (u32 b = threadIdx.x; b < TR * (N2 / 2); b += NT) {
-            const u32 rr = b / (N2 / 2), bp = b % (N2 / 2);
-            const u32 g = bp / half, j = bp % half;
+            const u32 rr = b >> (l2 - 1), bp = b & (N2 / 2 - 1);
+            const u32 g = bp >> lh, j = bp & (half - 1);
             const u32 o = g * 2 * half + j;
             u64 *x = sm + rr * N2 + o, *y = x + half;
             const u32 ti = ((N1 + r0 + rr) << s) + g;
@@ -228,10 +228,10 @@ __global__ void __launch_bounds__(NT) k_digits_cols(const DevJob *__restrict__ j
         for (u32 x = threadIdx.x; x < N1 * TC; x += NT) tile[x] = (Dt[x] >> (d * log2B)) & Bmask;
         __syncthreads();
         for (u32 s = 0; s < l1; s++) {
-            const u32 half = N1 >> (s + 1);
+            const u32 lh = l1 - 1 - s, half = 1u << lh;
             for (u32 b = threadIdx.x; b < (N1 / 2) * TC; b += NT) {
                 const u32 bp = b / TC, cc = b % TC;
-                const u32 g = bp / half, j = bp % half;
+                const u32 g = bp >> lh, j = bp & (half - 1);
                 const u32 t = g * 2 * half + j;
                 u64 *x = tile + t * TC + cc, *y = tile + (t + half) * TC + cc;
                 const u32 ti = (1u << s) + g;
@@ -259,20 +259,21 @@ __global__ void __launch_bounds__(NT) k_rows_mac(const DevJob *__restrict__ jobs
     split_log(K.logN, l1, l2);
     const u32 N = J.N, N1 = 1u << l1, N2 = 1u << l2;
     const u32 r0 = blockIdx.x * trm, nc = 4 * K.l_B, lb = K.lbits, w = trm * N2;
+    const u32 lw = __ffs(w) - 1;         // trm and N2 are powers of two
     const u64 Q = K.mq.Q;
     const size_t vec = (size_t)2 * N;
     const u64 *X = ws + J.acc_off + 3 * vec;
     u64 *sums = ws + J.acc_off + 2 * vec;
-    for (u32 x = threadIdx.x; x < nc * w; x += NT) sm[x] = X[(size_t)(x / w) * N + (size_t)r0 * N2 + x % w];
+    for (u32 x = threadIdx.x; x < nc * w; x += NT) sm[x] = X[(size_t)(x >> lw) * N + (size_t)r0 * N2 + (x & (w - 1))];
     __syncthreads();
     for (u32 s = 0; s < l2; s++) {
-        const u32 half = N2 >> (s + 1);
+        const u32 lh = l2 - 1 - s, half = 1u << lh;
         for (u32 b = threadIdx.x; b < nc * trm * (N2 / 2); b += NT) {
-            const u32 pr = b / (N2 / 2), bp = b % (N2 / 2);      // pr = c trm + rr
-            const u32 g = bp / half, j = bp % half;
+            const u32 pr = b >> (l2 - 1), bp = b & (N2 / 2 - 1);   // pr = c trm + rr
+            const u32 g = bp >> lh, j = bp & (half - 1);
             const u32 o = g * 2 * half + j;
             u64 *x = sm + (size_t)pr * N2 + o, *y = x + half;
-            const u32 ti = ((N1 + r0 + pr % trm) << s) + g;
+            const u32 ti = ((N1 + r0 + (pr & (trm - 1))) << s) + g;
             const u64 U = *x, V = mul_shoup(*y, __ldg(K.tw + ti), __ldg(K.twsh + ti), Q);
             *x = add_mod(U, V, Q);
             *y = sub_mod(U, V, Q);
@@ -315,10 +316,10 @@ __global__ void __launch_bounds__(NT) k_cols_inv_update(const DevJob *__restrict
     __syncthreads();
     for (u32 st = 0; st < l1; st++) {
         const u32 s = l1 - 1 - st;
-        const u32 half = N1 >> (s + 1);
+        const u32 lh = l1 - 1 - s, half = 1u << lh;
         for (u32 b = threadIdx.x; b < (N1 / 2) * TC; b += NT) {
             const u32 bp = b / TC, cc = b % TC;
-            const u32 g = bp / half, j = bp % half;
+            const u32 g = bp >> lh, j = bp & (half - 1);
             const u32 t = g * 2 * half + j;
             u64 *x = sm + t * TC + cc, *y = sm + (t + half) * TC + cc;
             const u32 ti = (1u << s) + g;
@@ -437,8 +438,8 @@ bm_status bm_launch_br_big(u32 N, const DevJob *jobs, uint32_t cnt, u32 steps, c
     // rows per block of the row pass + multiply-accumulate: the digit rows of
     // every combo a key can have (4 BM_MAX_L_B) within 64 KB
     const u32 ncmax = 4 * BM_MAX_L_B;
-    u32 trm = 8192 / (ncmax * N2);
-    trm = trm < 1 ? 1 : trm > N1 ? N1 : trm;
+    u32 trm = 1;
+    while (2 * trm * ncmax * N2 <= 8192 && 2 * trm <= N1) trm *= 2;     // a power of two
     const size_t sm_dc = (size_t)2 * N1 * bign::TC * 8, sm_rm = (size_t)ncmax * trm * N2 * 8,
                  sm_ci = (size_t)N1 * bign::TC * 8;
     BM_CUDA_TRY(cudaFuncSetAttribute(bign::k_digits_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_dc));
