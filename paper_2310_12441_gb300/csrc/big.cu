@@ -12,16 +12,19 @@
 // every column); stages log N1 + s', s' < log N2, pair elements of the rows
 // [r N2, (r + 1) N2) (group (r << s') + (o >> (log N2 - s')), twiddle index
 // ((N1 + r) << s') + (o >> (log N2 - s'))).  The inverse runs the row pass
-// first, then the column pass, each stage backwards.  Values stay in [0, Q)
-// (one correction per butterfly): this path serves a comparison, not the
-// headline workloads.
+// first, then the column pass, each stage backwards.  Each pass keeps
+// 2^4 values per thread in registers for four stages at a time (one
+// shared-memory exchange and barrier per four stages).  For Q = c 2^32 + 1
+// the butterflies are lazy (forward values below 8Q, inverse below 4Q, brought
+// into [0, Q) where a transform ends); other moduli correct every butterfly.
 #include "blind_rotate.cuh"
 
 namespace bign {
 
 constexpr u32 TC = 16;     // columns per block of the column pass
-constexpr u32 TR = 8;      // rows per block of the row pass
+constexpr u32 TR = 32;     // rows per block of the row pass
 constexpr u32 NT = 256;    // threads per block
+constexpr u32 RMAX = 4;    // stages per register chunk (16 values per work item)
 
 // Polynomial p of launch row y: a flat array of polynomials, or the
 // digit / sum buffers of job y (after the job's three [2][N] accumulator
@@ -52,47 +55,191 @@ __device__ __forceinline__ void split_log(u32 logN, u32 &l1, u32 &l2) {
     l2 = logN - l1;
 }
 
+// ---- Arithmetic of the passes.  For Q = c 2^32 + 1 < 2^60 (QL) the
+// butterflies are the lazy ones of modarith.cuh: forward values in [0, 8Q),
+// inverse values in [0, 4Q), brought into [0, Q) where a transform ends;
+// for other moduli every butterfly corrects into [0, Q).
+__device__ __forceinline__ bool qlow1_of(u64 Q) { return (Q & 0xffffffffull) == 1 && Q < (1ull << 60); }
+
+template <bool QL>
+struct Arith {
+    u64 Q, fourQ;
+    u32 c;
+    __device__ explicit Arith(u64 q) : Q(q), fourQ(4 * q), c((u32)(q >> 32)) {}
+    __device__ __forceinline__ void fwd(u64 &X, u64 &Y, u64 W, u64 Wsh) const {
+        if constexpr (QL) {
+            bfly_ct_qlow1(X, Y, W, Wsh, c, fourQ);
+        } else {
+            const u64 U = X, V = mul_shoup(Y, W, Wsh, Q);
+            X = add_mod(U, V, Q);
+            Y = sub_mod(U, V, Q);
+        }
+    }
+    __device__ __forceinline__ void inv(u64 &X, u64 &Y, u64 W, u64 Wsh) const {
+        if constexpr (QL) {
+            bfly_gs_qlow1(X, Y, W, Wsh, c, fourQ);
+        } else {
+            const u64 U = X, V = Y;
+            X = add_mod(U, V, Q);
+            Y = mul_shoup(U + Q - V, W, Wsh, Q);
+        }
+    }
+    // the last forward stage's value (below 8Q) into [0, Q)
+    __device__ __forceinline__ u64 fwd_final(u64 x) const {
+        if constexpr (QL) return csub63(csub63(csub63(x, fourQ), 2 * Q), Q);
+        else return x;
+    }
+    // the last inverse stage's value (below 4Q) into [0, Q)
+    __device__ __forceinline__ u64 inv_final(u64 x) const {
+        if constexpr (QL) return csub63(csub63(x, 2 * Q), Q);
+        else return x;
+    }
+};
+
+// Row tiles in shared memory: element e of row q at q qs + e + (e >> 4), one
+// pad word per 16 (qs = N2 + N2 / 16), so that the later stages' strided
+// accesses fall on distinct banks.  Column tiles: element e of column q at
+// q + TC e.
+__device__ __forceinline__ u32 row_stride(u32 N2) { return N2 + N2 / 16; }
+__device__ __forceinline__ u32 row_at(u32 q, u32 qs, u32 e) { return q * qs + e + (e >> 4); }
+
+// Stage s0 + r of a register chunk (see pass_chunk), r a constant so that
+// every index into x is one.
+template <int R, int r, bool INV, bool QL>
+__device__ __forceinline__ void chunk_stage(u64 (&x)[1 << R], const u64 *__restrict__ tp, u32 tb, u32 s0, u32 G,
+                                            const Arith<QL> &A) {
+    constexpr u32 h = 1u << (R - 1 - r);
+#pragma unroll
+    for (u32 gi = 0; gi < (1u << r); gi++) {
+        const ulonglong2 W = __ldg(reinterpret_cast<const ulonglong2 *>(tp) + ((tb << (s0 + r)) + (G << r) + gi));
+#pragma unroll
+        for (u32 j = 0; j < h; j++) {
+            if constexpr (INV) A.inv(x[gi * 2 * h + j], x[gi * 2 * h + j + h], W.x, W.y);
+            else A.fwd(x[gi * 2 * h + j], x[gi * 2 * h + j + h], W.x, W.y);
+        }
+    }
+}
+
+// The chunk's stages in order: r = 0 .. R - 1 forward, R - 1 .. 0 inverse.
+template <int R, int k, bool INV, bool QL>
+__device__ __forceinline__ void chunk_stages(u64 (&x)[1 << R], const u64 *__restrict__ tp, u32 tb, u32 s0, u32 G,
+                                             const Arith<QL> &A) {
+    if constexpr (k < R) {
+        chunk_stage<R, INV ? R - 1 - k : k, INV, QL>(x, tp, tb, s0, G, A);
+        chunk_stages<R, k + 1, INV, QL>(x, tp, tb, s0, G, A);
+    }
+}
+
+// Stages s0 .. s0 + R - 1 (forward) or s0 + R - 1 .. s0 (inverse) of the
+// length-2^l transforms of nseq sequences held in shared memory, 2^R values
+// per work item in registers.  Item (q, G, J), G < 2^s0, J < 2^(l - s0 - R),
+// holds the elements G 2^(l - s0) + J + i 2^(l - s0 - R), i < 2^R, of
+// sequence q; at stage s0 + r it pairs i with i + 2^(R - 1 - r) under twiddle
+// ((tb0 + (q & qmask)) << (s0 + r)) + (G << r) + (i >> (R - r)), which is
+// the twiddle of the stage's group in the whole transform (columns: tb0 = 1,
+// qmask = 0; rows: tb0 = N1 + first row, qmask = rows per polynomial - 1).
+// ROW: J varies fastest across threads, then G, then the row; columns: the
+// column varies fastest.
+template <int R, bool INV, bool ROW, bool QL>
+__device__ __forceinline__ void pass_chunk(u64 *sm, u32 l, u32 s0, u32 nseq, u32 qs, u32 tb0, u32 qmask,
+                                           const u64 *__restrict__ tp, const Arith<QL> &A) {
+    constexpr u32 V = 1u << R;
+    const u32 lJ = l - s0 - R, items = nseq << (l - R);
+    for (u32 w = threadIdx.x; w < items; w += NT) {
+        u32 q, G, J;
+        if constexpr (ROW) {
+            J = w & ((1u << lJ) - 1);
+            G = (w >> lJ) & ((1u << s0) - 1);
+            q = w >> (l - R);
+        } else {
+            q = w & (TC - 1);
+            J = (w >> 4) & ((1u << lJ) - 1);
+            G = (w >> 4) >> lJ;
+        }
+        const u32 e0 = (G << (l - s0)) + J;
+        u64 *base = ROW ? sm + (size_t)q * qs : sm + q;
+        u64 x[V];
+#pragma unroll
+        for (u32 i = 0; i < V; i++) {
+            const u32 e = e0 + (i << lJ);
+            x[i] = ROW ? base[e + (e >> 4)] : base[TC * e];
+        }
+        chunk_stages<R, 0, INV, QL>(x, tp, tb0 + (q & qmask), s0, G, A);
+#pragma unroll
+        for (u32 i = 0; i < V; i++) {
+            const u32 e = e0 + (i << lJ);
+            if constexpr (ROW) base[e + (e >> 4)] = x[i];
+            else base[TC * e] = x[i];
+        }
+    }
+}
+
+// Every stage of one pass (length 2^l): register chunks of RMAX stages from
+// stage 0 (the last one shorter), the inverse the same chunks in reverse; a
+// barrier after each.  The caller has made the tile visible.
+template <bool INV, bool ROW, bool QL>
+__device__ void pass_stages(u64 *sm, u32 l, u32 nseq, u32 qs, u32 tb0, u32 qmask, const u64 *__restrict__ tp,
+                            const Arith<QL> &A) {
+    const u32 last = ((l - 1) / RMAX) * RMAX;
+    for (u32 k = 0; k <= last; k += RMAX) {
+        const u32 s0 = INV ? last - k : k;
+        const u32 R = l - s0 < RMAX ? l - s0 : RMAX;
+        if (R == 4) pass_chunk<4, INV, ROW, QL>(sm, l, s0, nseq, qs, tb0, qmask, tp, A);
+        else if (R == 3) pass_chunk<3, INV, ROW, QL>(sm, l, s0, nseq, qs, tb0, qmask, tp, A);
+        else if (R == 2) pass_chunk<2, INV, ROW, QL>(sm, l, s0, nseq, qs, tb0, qmask, tp, A);
+        else pass_chunk<1, INV, ROW, QL>(sm, l, s0, nseq, qs, tb0, qmask, tp, A);
+        __syncthreads();
+    }
+}
+
+// Column pass of TC columns from c0 of polynomial a.  smem: N1 TC words.
+// The forward pass leaves its values lazy (the row pass continues them); the
+// inverse pass ends the transform.
+template <bool INV, bool QL>
+__device__ void cols_body(u64 *sm, u64 *a, u32 c0, u32 l1, u32 N2, const KeyDev &K) {
+    const Arith<QL> A(K.mq.Q);
+    const u32 N1 = 1u << l1;
+    for (u32 e = threadIdx.x; e < N1 * TC; e += NT) sm[e] = a[c0 + e % TC + (size_t)N2 * (e / TC)];
+    __syncthreads();
+    pass_stages<INV, false, QL>(sm, l1, TC, 0, 1, 0, INV ? K.itwp : K.twp, A);
+    for (u32 e = threadIdx.x; e < N1 * TC; e += NT)
+        a[c0 + e % TC + (size_t)N2 * (e / TC)] = INV ? A.inv_final(sm[e]) : sm[e];
+}
+
+// Row pass of rows [r0, r0 + TR) of polynomial a.  smem: TR (N2 + N2 / 16)
+// words.  The forward pass ends the transform; the inverse one leaves its
+// values lazy for the column pass.
+template <bool INV, bool QL>
+__device__ void rows_body(u64 *sm, u64 *a, u32 r0, u32 l1, u32 l2, const KeyDev &K) {
+    const Arith<QL> A(K.mq.Q);
+    const u32 N2 = 1u << l2, qs = row_stride(N2);
+    for (u32 e = threadIdx.x; e < TR * N2; e += NT) sm[row_at(e >> l2, qs, e & (N2 - 1))] = a[e];
+    __syncthreads();
+    pass_stages<INV, true, QL>(sm, l2, TR, qs, (1u << l1) + r0, TR - 1, INV ? K.itwp : K.twp, A);
+    for (u32 e = threadIdx.x; e < TR * N2; e += NT) {
+        const u64 v = sm[row_at(e >> l2, qs, e & (N2 - 1))];
+        a[e] = INV ? v : A.fwd_final(v);
+    }
+}
+
 // Column pass: block (x = p * (N2 / TC) + chunk, y) transforms columns
-// [chunk TC, (chunk + 1) TC) of polynomial p of row y.  smem: N1 TC words.
+// [chunk TC, (chunk + 1) TC) of polynomial p of row y.
 template <bool INV, class Loc>
 __global__ void __launch_bounds__(NT) k_cols(Loc loc, u32 per) {
     extern __shared__ u64 sm[];
     const KeyDev &K = loc.k(blockIdx.y);
     u32 l1, l2;
     split_log(K.logN, l1, l2);
-    const u32 N1 = 1u << l1, N2 = 1u << l2, chunks = N2 / TC;
+    const u32 N2 = 1u << l2, chunks = N2 / TC;
     const u32 p = blockIdx.x / chunks, c0 = (blockIdx.x % chunks) * TC;
     if (p >= per || p >= loc.count(blockIdx.y)) return;
     u64 *a = loc.poly(blockIdx.y, p);
-    const u64 Q = K.mq.Q;
-    for (u32 e = threadIdx.x; e < N1 * TC; e += NT) sm[e] = a[c0 + e % TC + (size_t)N2 * (e / TC)];
-    __syncthreads();
-    for (u32 st = 0; st < l1; st++) {
-        const u32 s = INV ? l1 - 1 - st : st;
-        const u32 lh = l1 - 1 - s, half = 1u << lh;
-        for (u32 b = threadIdx.x; b < (N1 / 2) * TC; b += NT) {
-            const u32 bp = b / TC, cc = b % TC;
-            const u32 g = bp >> lh, j = bp & (half - 1);
-            const u32 t = g * 2 * half + j;
-            u64 *x = sm + t * TC + cc, *y = sm + (t + half) * TC + cc;
-            const u32 ti = (1u << s) + g;
-            if (INV) {
-                const u64 U = *x, V = *y;
-                *x = add_mod(U, V, Q);
-                *y = mul_shoup(U + Q - V, __ldg(K.itw + ti), __ldg(K.itwsh + ti), Q);
-            } else {
-                const u64 U = *x, V = mul_shoup(*y, __ldg(K.tw + ti), __ldg(K.twsh + ti), Q);
-                *x = add_mod(U, V, Q);
-                *y = sub_mod(U, V, Q);
-            }
-        }
-        __syncthreads();
-    }
-    for (u32 e = threadIdx.x; e < N1 * TC; e += NT) a[c0 + e % TC + (size_t)N2 * (e / TC)] = sm[e];
+    if (qlow1_of(K.mq.Q)) cols_body<INV, true>(sm, a, c0, l1, N2, K);
+    else cols_body<INV, false>(sm, a, c0, l1, N2, K);
 }
 
 // Row pass: block (x = p * (N1 / TR) + chunk, y) transforms rows
-// [chunk TR, (chunk + 1) TR) of polynomial p of row y.  smem: TR N2 words.
+// [chunk TR, (chunk + 1) TR) of polynomial p of row y.
 template <bool INV, class Loc>
 __global__ void __launch_bounds__(NT) k_rows(Loc loc, u32 per) {
     extern __shared__ u64 sm[];
@@ -103,31 +250,8 @@ __global__ void __launch_bounds__(NT) k_rows(Loc loc, u32 per) {
     const u32 p = blockIdx.x / chunks, r0 = (blockIdx.x % chunks) * TR;
     if (p >= per || p >= loc.count(blockIdx.y)) return;
     u64 *a = loc.poly(blockIdx.y, p) + (size_t)r0 * N2;
-    const u64 Q = K.mq.Q;
-    for (u32 e = threadIdx.x; e < TR * N2; e += NT) sm[e] = a[e];
-    __syncthreads();
-    for (u32 st = 0; st < l2; st++) {
-        const u32 s = INV ? l2 - 1 - st : st;      // stage within the row: global stage l1 + s
-        const u32 lh = l2 - 1 - s, half = 1u << lh;
-        for (u32 b = threadIdx.x; b < TR * (N2 / 2); b += NT) {
-            const u32 rr = b >> (l2 - 1), bp = b & (N2 / 2 - 1);
-            const u32 g = bp >> lh, j = bp & (half - 1);
-            const u32 o = g * 2 * half + j;
-            u64 *x = sm + rr * N2 + o, *y = x + half;
-            const u32 ti = ((N1 + r0 + rr) << s) + g;
-            if (INV) {
-                const u64 U = *x, V = *y;
-                *x = add_mod(U, V, Q);
-                *y = mul_shoup(U + Q - V, __ldg(K.itw + ti), __ldg(K.itwsh + ti), Q);
-            } else {
-                const u64 U = *x, V = mul_shoup(*y, __ldg(K.tw + ti), __ldg(K.twsh + ti), Q);
-                *x = add_mod(U, V, Q);
-                *y = sub_mod(U, V, Q);
-            }
-        }
-        __syncthreads();
-    }
-    for (u32 e = threadIdx.x; e < TR * N2; e += NT) a[e] = sm[e];
+    if (qlow1_of(K.mq.Q)) rows_body<INV, true>(sm, a, r0, l1, l2, K);
+    else rows_body<INV, false>(sm, a, r0, l1, l2, K);
 }
 
 // The row pass alone (the step's inverse starts with it).
@@ -136,8 +260,8 @@ bm_status transform_rows(Loc loc, u32 rows, u32 per, u32 N, bool inverse, cudaSt
     u32 logN = 0;
     while ((1u << logN) < N) logN++;
     const u32 l1 = logN / 2, l2 = logN - l1, N1 = 1u << l1, N2 = 1u << l2;
-    if (N1 < TR) return BM_EINVAL;
-    const size_t smr = (size_t)TR * N2 * 8;
+    if (N1 < TR || N2 < TC) return BM_EINVAL;
+    const size_t smr = (size_t)TR * (N2 + N2 / 16) * 8;
     auto kr = inverse ? k_rows<true, Loc> : k_rows<false, Loc>;
     BM_CUDA_TRY(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
     kr<<<dim3(per * (N1 / TR), rows), NT, smr, st>>>(loc, per);
@@ -151,7 +275,7 @@ bm_status transform(Loc loc, u32 rows, u32 per, u32 N, bool inverse, cudaStream_
     while ((1u << logN) < N) logN++;
     const u32 l1 = logN / 2, l2 = logN - l1, N1 = 1u << l1, N2 = 1u << l2;
     if (N1 < TR || N2 < TC) return BM_EINVAL;
-    const size_t smc = (size_t)N1 * TC * 8, smr = (size_t)TR * N2 * 8;
+    const size_t smc = (size_t)N1 * TC * 8, smr = (size_t)TR * (N2 + N2 / 16) * 8;
     auto kc = inverse ? k_cols<true, Loc> : k_cols<false, Loc>;
     auto kr = inverse ? k_rows<true, Loc> : k_rows<false, Loc>;
     BM_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
@@ -196,12 +320,10 @@ __global__ void k_init(const DevJob *__restrict__ jobs, const u64 *__restrict__ 
 // columns, then for every digit transforms the digit columns (stages
 // 0 .. log N1 - 1) into the job's digit polynomial pair l_B + d.  smem:
 // 2 N1 TC words (the difference, the digit tile).
-__global__ void __launch_bounds__(NT) k_digits_cols(const DevJob *__restrict__ jobs, const u64 *__restrict__ ct_in,
-                                                    u64 *ws, u32 k, const u32 *status) {
-    extern __shared__ u64 sm[];
-    const DevJob &J = jobs[blockIdx.y];
-    const KeyDev &K = *J.key;
-    if (k >= K.n) return;
+template <bool QL>
+__device__ void digits_cols_body(u64 *sm, const DevJob &J, const KeyDev &K, const u64 *__restrict__ ct_in, u64 *ws,
+                                 u32 k, const u32 *status) {
+    const Arith<QL> A(K.mq.Q);
     u32 l1, l2;
     split_log(K.logN, l1, l2);
     const u32 N = J.N, N1 = 1u << l1, N2 = 1u << l2, chunks = N2 / TC;
@@ -227,65 +349,52 @@ __global__ void __launch_bounds__(NT) k_digits_cols(const DevJob *__restrict__ j
         __syncthreads();     // the difference is complete; the previous digit's tile is stored
         for (u32 x = threadIdx.x; x < N1 * TC; x += NT) tile[x] = (Dt[x] >> (d * log2B)) & Bmask;
         __syncthreads();
-        for (u32 s = 0; s < l1; s++) {
-            const u32 lh = l1 - 1 - s, half = 1u << lh;
-            for (u32 b = threadIdx.x; b < (N1 / 2) * TC; b += NT) {
-                const u32 bp = b / TC, cc = b % TC;
-                const u32 g = bp >> lh, j = bp & (half - 1);
-                const u32 t = g * 2 * half + j;
-                u64 *x = tile + t * TC + cc, *y = tile + (t + half) * TC + cc;
-                const u32 ti = (1u << s) + g;
-                const u64 U = *x, V = mul_shoup(*y, __ldg(K.tw + ti), __ldg(K.twsh + ti), Q);
-                *x = add_mod(U, V, Q);
-                *y = sub_mod(U, V, Q);
-            }
-            __syncthreads();
-        }
+        pass_stages<false, false, QL>(tile, l1, TC, 0, 1, 0, K.twp, A);
         u64 *a = X + (size_t)(pair * lB + d) * N;
         for (u32 x = threadIdx.x; x < N1 * TC; x += NT) a[c0 + x % TC + (size_t)N2 * (x / TC)] = tile[x];
     }
 }
 
-// Forward row pass of all 4 l_B digit polynomials on rows [r0, r0 + trm),
-// then the multiply-accumulate of those positions against the key rows of
-// step k (exact 128-bit sums, reduced) into the job's row sums.
-// Block (x = row chunk, y = job); smem: 4 l_B trm N2 words.
-__global__ void __launch_bounds__(NT) k_rows_mac(const DevJob *__restrict__ jobs, u64 *ws, u32 k, u32 trm) {
+__global__ void __launch_bounds__(NT) k_digits_cols(const DevJob *__restrict__ jobs, const u64 *__restrict__ ct_in,
+                                                    u64 *ws, u32 k, const u32 *status) {
     extern __shared__ u64 sm[];
     const DevJob &J = jobs[blockIdx.y];
     const KeyDev &K = *J.key;
     if (k >= K.n) return;
+    if (qlow1_of(K.mq.Q)) digits_cols_body<true>(sm, J, K, ct_in, ws, k, status);
+    else digits_cols_body<false>(sm, J, K, ct_in, ws, k, status);
+}
+
+// Forward row pass of all 4 l_B digit polynomials on rows [r0, r0 + trm)
+// (trm a power of two), then the multiply-accumulate of those positions
+// against the key rows of step k (exact 128-bit sums, reduced) into the
+// job's row sums.  The transform outputs enter the sums unreduced: below 8Q
+// (QL, Q < 2^60) times key words below Q, 4 l_B <= 32 of them stay below
+// 2^128.  Block (x = row chunk, y = job); smem: 4 l_B trm (N2 + N2 / 16)
+// words.
+template <bool QL>
+__device__ void rows_mac_body(u64 *sm, const DevJob &J, const KeyDev &K, u64 *ws, u32 k, u32 trm) {
+    const Arith<QL> A(K.mq.Q);
     u32 l1, l2;
     split_log(K.logN, l1, l2);
-    const u32 N = J.N, N1 = 1u << l1, N2 = 1u << l2;
+    const u32 N = J.N, N1 = 1u << l1, N2 = 1u << l2, qs = row_stride(N2);
     const u32 r0 = blockIdx.x * trm, nc = 4 * K.l_B, lb = K.lbits, w = trm * N2;
-    const u32 lw = __ffs(w) - 1;         // trm and N2 are powers of two
-    const u64 Q = K.mq.Q;
+    const u32 lw = __ffs(w) - 1;
     const size_t vec = (size_t)2 * N;
     const u64 *X = ws + J.acc_off + 3 * vec;
     u64 *sums = ws + J.acc_off + 2 * vec;
-    for (u32 x = threadIdx.x; x < nc * w; x += NT) sm[x] = X[(size_t)(x >> lw) * N + (size_t)r0 * N2 + (x & (w - 1))];
+    // row q = c trm + rr of the tile is row r0 + rr of digit polynomial c
+    for (u32 x = threadIdx.x; x < nc * w; x += NT)
+        sm[row_at(x >> l2, qs, x & (N2 - 1))] = X[(size_t)(x >> lw) * N + (size_t)r0 * N2 + (x & (w - 1))];
     __syncthreads();
-    for (u32 s = 0; s < l2; s++) {
-        const u32 lh = l2 - 1 - s, half = 1u << lh;
-        for (u32 b = threadIdx.x; b < nc * trm * (N2 / 2); b += NT) {
-            const u32 pr = b >> (l2 - 1), bp = b & (N2 / 2 - 1);   // pr = c trm + rr
-            const u32 g = bp >> lh, j = bp & (half - 1);
-            const u32 o = g * 2 * half + j;
-            u64 *x = sm + (size_t)pr * N2 + o, *y = x + half;
-            const u32 ti = ((N1 + r0 + (pr & (trm - 1))) << s) + g;
-            const u64 U = *x, V = mul_shoup(*y, __ldg(K.tw + ti), __ldg(K.twsh + ti), Q);
-            *x = add_mod(U, V, Q);
-            *y = sub_mod(U, V, Q);
-        }
-        __syncthreads();
-    }
+    pass_stages<false, true, QL>(sm, l2, nc * trm, qs, N1 + r0, trm - 1, K.twp, A);
     const u64 *bk = K.bsk + (size_t)k * 2 * (2 * K.l_B * 2 * N);
     for (u32 pos = threadIdx.x; pos < w; pos += NT) {
         const size_t i = (size_t)r0 * N2 + pos;
+        const u32 rr = pos >> l2, o = pos & (N2 - 1);
         u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
         for (u32 c = 0; c < nc; c++) {
-            const u64 x = sm[(size_t)c * w + pos];
+            const u64 x = sm[row_at(c * trm + rr, qs, o)];
             const ulonglong2 wv = __ldg(reinterpret_cast<const ulonglong2 *>(bk + (size_t)c * 2 * N + 2 * i));
             mac128(lo0, hi0, x, (wv.x & 0xffffffffull) + ((wv.y & 0xffffffffull) << lb));
             mac128(lo1, hi1, x, (wv.x >> 32) + ((wv.y >> 32) << lb));
@@ -295,14 +404,21 @@ __global__ void __launch_bounds__(NT) k_rows_mac(const DevJob *__restrict__ jobs
     }
 }
 
-// Inverse column pass of the two row sums (stages log N1 - 1 .. 0) fused
-// with the accumulator update of step k.  Block (x = comp (N2 / TC) +
-// chunk, y = job); smem N1 TC words.
-__global__ void __launch_bounds__(NT) k_cols_inv_update(const DevJob *__restrict__ jobs, u64 *ws, u32 k) {
+__global__ void __launch_bounds__(NT) k_rows_mac(const DevJob *__restrict__ jobs, u64 *ws, u32 k, u32 trm) {
     extern __shared__ u64 sm[];
     const DevJob &J = jobs[blockIdx.y];
     const KeyDev &K = *J.key;
     if (k >= K.n) return;
+    if (qlow1_of(K.mq.Q)) rows_mac_body<true>(sm, J, K, ws, k, trm);
+    else rows_mac_body<false>(sm, J, K, ws, k, trm);
+}
+
+// Inverse column pass of the two row sums (stages log N1 - 1 .. 0) fused
+// with the accumulator update of step k.  Block (x = comp (N2 / TC) +
+// chunk, y = job); smem N1 TC words.
+template <bool QL>
+__device__ void cols_inv_update_body(u64 *sm, const DevJob &J, const KeyDev &K, u64 *ws, u32 k) {
+    const Arith<QL> A(K.mq.Q);
     u32 l1, l2;
     split_log(K.logN, l1, l2);
     const u32 N = J.N, N1 = 1u << l1, N2 = 1u << l2, chunks = N2 / TC;
@@ -314,25 +430,20 @@ __global__ void __launch_bounds__(NT) k_cols_inv_update(const DevJob *__restrict
     const u64 *a = ws + J.acc_off + 2 * vec + (size_t)comp * N;
     for (u32 x = threadIdx.x; x < N1 * TC; x += NT) sm[x] = a[c0 + x % TC + (size_t)N2 * (x / TC)];
     __syncthreads();
-    for (u32 st = 0; st < l1; st++) {
-        const u32 s = l1 - 1 - st;
-        const u32 lh = l1 - 1 - s, half = 1u << lh;
-        for (u32 b = threadIdx.x; b < (N1 / 2) * TC; b += NT) {
-            const u32 bp = b / TC, cc = b % TC;
-            const u32 g = bp >> lh, j = bp & (half - 1);
-            const u32 t = g * 2 * half + j;
-            u64 *x = sm + t * TC + cc, *y = sm + (t + half) * TC + cc;
-            const u32 ti = (1u << s) + g;
-            const u64 U = *x, V = *y;
-            *x = add_mod(U, V, Q);
-            *y = mul_shoup(U + Q - V, __ldg(K.itw + ti), __ldg(K.itwsh + ti), Q);
-        }
-        __syncthreads();
-    }
+    pass_stages<true, false, QL>(sm, l1, TC, 0, 1, 0, K.itwp, A);
     for (u32 x = threadIdx.x; x < N1 * TC; x += NT) {
         const size_t i = c0 + x % TC + (size_t)N2 * (x / TC);
-        nxt[i] = add_mod(cur[i], sm[x], Q);
+        nxt[i] = add_mod(cur[i], A.inv_final(sm[x]), Q);
     }
+}
+
+__global__ void __launch_bounds__(NT) k_cols_inv_update(const DevJob *__restrict__ jobs, u64 *ws, u32 k) {
+    extern __shared__ u64 sm[];
+    const DevJob &J = jobs[blockIdx.y];
+    const KeyDev &K = *J.key;
+    if (k >= K.n) return;
+    if (qlow1_of(K.mq.Q)) cols_inv_update_body<true>(sm, J, K, ws, k);
+    else cols_inv_update_body<false>(sm, J, K, ws, k);
 }
 
 // RGSW row finish of key generation (the formula of keygen.cu, elementwise):
@@ -436,11 +547,12 @@ bm_status bm_launch_br_big(u32 N, const DevJob *jobs, uint32_t cnt, u32 steps, c
     while ((1u << logN) < N) logN++;
     const u32 l1 = logN / 2, l2 = logN - l1, N1 = 1u << l1, N2 = 1u << l2;
     // rows per block of the row pass + multiply-accumulate: the digit rows of
-    // every combo a key can have (4 BM_MAX_L_B) within 64 KB
+    // every combo a key can have (4 BM_MAX_L_B), 64 KB of values (68 KB with
+    // the row padding)
     const u32 ncmax = 4 * BM_MAX_L_B;
     u32 trm = 1;
     while (2 * trm * ncmax * N2 <= 8192 && 2 * trm <= N1) trm *= 2;     // a power of two
-    const size_t sm_dc = (size_t)2 * N1 * bign::TC * 8, sm_rm = (size_t)ncmax * trm * N2 * 8,
+    const size_t sm_dc = (size_t)2 * N1 * bign::TC * 8, sm_rm = (size_t)ncmax * trm * (N2 + N2 / 16) * 8,
                  sm_ci = (size_t)N1 * bign::TC * 8;
     BM_CUDA_TRY(cudaFuncSetAttribute(bign::k_digits_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_dc));
     BM_CUDA_TRY(cudaFuncSetAttribute(bign::k_rows_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rm));
