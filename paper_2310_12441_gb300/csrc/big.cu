@@ -23,7 +23,7 @@ namespace bign {
 
 constexpr u32 TC = 16;     // columns per block of the column pass
 constexpr u32 TR = 32;     // rows per block of the row pass
-constexpr u32 NT = 256;    // threads per block
+constexpr u32 NT = 256;    // threads per block (three blocks per SM: at most 80 registers)
 constexpr u32 RMAX = 4;    // stages per register chunk (16 values per work item)
 
 // Polynomial p of launch row y: a flat array of polynomials, or the
@@ -131,18 +131,20 @@ __device__ __forceinline__ void chunk_stages(u64 (&x)[1 << R], const u64 *__rest
 }
 
 // Stages s0 .. s0 + R - 1 (forward) or s0 + R - 1 .. s0 (inverse) of the
-// length-2^l transforms of nseq sequences held in shared memory, 2^R values
-// per work item in registers.  Item (q, G, J), G < 2^s0, J < 2^(l - s0 - R),
-// holds the elements G 2^(l - s0) + J + i 2^(l - s0 - R), i < 2^R, of
-// sequence q; at stage s0 + r it pairs i with i + 2^(R - 1 - r) under twiddle
+// length-2^l transforms of nseq sequences, 2^R values per work item in
+// registers.  Item (q, G, J), G < 2^s0, J < 2^(l - s0 - R), holds the
+// elements G 2^(l - s0) + J + i 2^(l - s0 - R), i < 2^R, of sequence q; at
+// stage s0 + r it pairs i with i + 2^(R - 1 - r) under twiddle
 // ((tb0 + (q & qmask)) << (s0 + r)) + (G << r) + (i >> (R - r)), which is
 // the twiddle of the stage's group in the whole transform (columns: tb0 = 1,
 // qmask = 0; rows: tb0 = N1 + first row, qmask = rows per polynomial - 1).
 // ROW: J varies fastest across threads, then G, then the row; columns: the
-// column varies fastest.
-template <int R, bool INV, bool ROW, bool QL>
-__device__ __forceinline__ void pass_chunk(u64 *sm, u32 l, u32 s0, u32 nseq, u32 qs, u32 tb0, u32 qmask,
-                                           const u64 *__restrict__ tp, const Arith<QL> &A) {
+// column varies fastest.  ld(q, e) and st(q, e, v) fetch and put element e
+// of sequence q (the shared-memory tile, or global memory for the first and
+// last chunk of a pass).
+template <int R, bool INV, bool ROW, bool QL, class Ld, class St>
+__device__ __forceinline__ void pass_chunk(u32 l, u32 s0, u32 nseq, u32 tb0, u32 qmask, const u64 *__restrict__ tp,
+                                           const Arith<QL> &A, Ld &ld, St &st) {
     constexpr u32 V = 1u << R;
     const u32 lJ = l - s0 - R, items = nseq << (l - R);
     for (u32 w = threadIdx.x; w < items; w += NT) {
@@ -157,75 +159,72 @@ __device__ __forceinline__ void pass_chunk(u64 *sm, u32 l, u32 s0, u32 nseq, u32
             G = (w >> 4) >> lJ;
         }
         const u32 e0 = (G << (l - s0)) + J;
-        u64 *base = ROW ? sm + (size_t)q * qs : sm + q;
         u64 x[V];
 #pragma unroll
-        for (u32 i = 0; i < V; i++) {
-            const u32 e = e0 + (i << lJ);
-            x[i] = ROW ? base[e + (e >> 4)] : base[TC * e];
-        }
+        for (u32 i = 0; i < V; i++) x[i] = ld(q, e0 + (i << lJ));
         chunk_stages<R, 0, INV, QL>(x, tp, tb0 + (q & qmask), s0, G, A);
 #pragma unroll
-        for (u32 i = 0; i < V; i++) {
-            const u32 e = e0 + (i << lJ);
-            if constexpr (ROW) base[e + (e >> 4)] = x[i];
-            else base[TC * e] = x[i];
-        }
+        for (u32 i = 0; i < V; i++) st(q, e0 + (i << lJ), x[i]);
     }
 }
 
-// Every stage of one pass (length 2^l): register chunks of RMAX stages from
-// stage 0 (the last one shorter), the inverse the same chunks in reverse; a
-// barrier after each.  The caller has made the tile visible.
-template <bool INV, bool ROW, bool QL>
-__device__ void pass_stages(u64 *sm, u32 l, u32 nseq, u32 qs, u32 tb0, u32 qmask, const u64 *__restrict__ tp,
-                            const Arith<QL> &A) {
-    const u32 last = ((l - 1) / RMAX) * RMAX;
-    for (u32 k = 0; k <= last; k += RMAX) {
-        const u32 s0 = INV ? last - k : k;
-        const u32 R = l - s0 < RMAX ? l - s0 : RMAX;
-        if (R == 4) pass_chunk<4, INV, ROW, QL>(sm, l, s0, nseq, qs, tb0, qmask, tp, A);
-        else if (R == 3) pass_chunk<3, INV, ROW, QL>(sm, l, s0, nseq, qs, tb0, qmask, tp, A);
-        else if (R == 2) pass_chunk<2, INV, ROW, QL>(sm, l, s0, nseq, qs, tb0, qmask, tp, A);
-        else pass_chunk<1, INV, ROW, QL>(sm, l, s0, nseq, qs, tb0, qmask, tp, A);
+// The stages of one pass.  The ring degrees of this path (2^14 .. 2^16) give
+// passes of 7 or 8 stages: two register chunks, stages 0-3 and 4 .. l - 1
+// (the inverse takes them in the other order), one barrier between them.
+// The first chunk takes its values through ld_first, the second puts them
+// through st_last; in between they sit in the tile sm (row tiles of stride
+// qs).  The caller synchronises before sm is reused.
+template <bool INV, bool ROW, bool QL, class Ld, class St>
+__device__ __forceinline__ void pass_stages(u64 *sm, u32 l, u32 nseq, u32 qs, u32 tb0, u32 qmask,
+                                            const u64 *__restrict__ tp, const Arith<QL> &A, Ld &&ld_first,
+                                            St &&st_last) {
+    auto ld_sm = [&](u32 q, u32 e) { return ROW ? sm[row_at(q, qs, e)] : sm[q + TC * e]; };
+    auto st_sm = [&](u32 q, u32 e, u64 v) {
+        if constexpr (ROW) sm[row_at(q, qs, e)] = v;
+        else sm[q + TC * e] = v;
+    };
+    if constexpr (!INV) {
+        pass_chunk<4, INV, ROW, QL>(l, 0, nseq, tb0, qmask, tp, A, ld_first, st_sm);
         __syncthreads();
+        if (l == 8) pass_chunk<4, INV, ROW, QL>(l, 4, nseq, tb0, qmask, tp, A, ld_sm, st_last);
+        else pass_chunk<3, INV, ROW, QL>(l, 4, nseq, tb0, qmask, tp, A, ld_sm, st_last);
+    } else {
+        if (l == 8) pass_chunk<4, INV, ROW, QL>(l, 4, nseq, tb0, qmask, tp, A, ld_first, st_sm);
+        else pass_chunk<3, INV, ROW, QL>(l, 4, nseq, tb0, qmask, tp, A, ld_first, st_sm);
+        __syncthreads();
+        pass_chunk<4, INV, ROW, QL>(l, 0, nseq, tb0, qmask, tp, A, ld_sm, st_last);
     }
 }
 
-// Column pass of TC columns from c0 of polynomial a.  smem: N1 TC words.
-// The forward pass leaves its values lazy (the row pass continues them); the
-// inverse pass ends the transform.
+// Column pass of TC columns from c0 of polynomial a, in place.  smem: N1 TC
+// words.  The forward pass leaves its values lazy (the row pass continues
+// them); the inverse pass ends the transform.
 template <bool INV, bool QL>
 __device__ void cols_body(u64 *sm, u64 *a, u32 c0, u32 l1, u32 N2, const KeyDev &K) {
     const Arith<QL> A(K.mq.Q);
-    const u32 N1 = 1u << l1;
-    for (u32 e = threadIdx.x; e < N1 * TC; e += NT) sm[e] = a[c0 + e % TC + (size_t)N2 * (e / TC)];
-    __syncthreads();
-    pass_stages<INV, false, QL>(sm, l1, TC, 0, 1, 0, INV ? K.itwp : K.twp, A);
-    for (u32 e = threadIdx.x; e < N1 * TC; e += NT)
-        a[c0 + e % TC + (size_t)N2 * (e / TC)] = INV ? A.inv_final(sm[e]) : sm[e];
+    u64 *col = a + c0;
+    pass_stages<INV, false, QL>(
+        sm, l1, TC, 0, 1, 0, INV ? K.itwp : K.twp, A, [&](u32 q, u32 e) { return col[q + (size_t)N2 * e]; },
+        [&](u32 q, u32 e, u64 v) { col[q + (size_t)N2 * e] = INV ? A.inv_final(v) : v; });
 }
 
-// Row pass of rows [r0, r0 + TR) of polynomial a.  smem: TR (N2 + N2 / 16)
-// words.  The forward pass ends the transform; the inverse one leaves its
-// values lazy for the column pass.
+// Row pass of rows [r0, r0 + TR) of polynomial a (a at row r0), in place.
+// smem: TR (N2 + N2 / 16) words.  The forward pass ends the transform; the
+// inverse one leaves its values lazy for the column pass.
 template <bool INV, bool QL>
 __device__ void rows_body(u64 *sm, u64 *a, u32 r0, u32 l1, u32 l2, const KeyDev &K) {
     const Arith<QL> A(K.mq.Q);
-    const u32 N2 = 1u << l2, qs = row_stride(N2);
-    for (u32 e = threadIdx.x; e < TR * N2; e += NT) sm[row_at(e >> l2, qs, e & (N2 - 1))] = a[e];
-    __syncthreads();
-    pass_stages<INV, true, QL>(sm, l2, TR, qs, (1u << l1) + r0, TR - 1, INV ? K.itwp : K.twp, A);
-    for (u32 e = threadIdx.x; e < TR * N2; e += NT) {
-        const u64 v = sm[row_at(e >> l2, qs, e & (N2 - 1))];
-        a[e] = INV ? v : A.fwd_final(v);
-    }
+    const u32 N2 = 1u << l2;
+    pass_stages<INV, true, QL>(
+        sm, l2, TR, row_stride(N2), (1u << l1) + r0, TR - 1, INV ? K.itwp : K.twp, A,
+        [&](u32 q, u32 e) { return a[(size_t)q * N2 + e]; },
+        [&](u32 q, u32 e, u64 v) { a[(size_t)q * N2 + e] = INV ? v : A.fwd_final(v); });
 }
 
 // Column pass: block (x = p * (N2 / TC) + chunk, y) transforms columns
 // [chunk TC, (chunk + 1) TC) of polynomial p of row y.
 template <bool INV, class Loc>
-__global__ void __launch_bounds__(NT) k_cols(Loc loc, u32 per) {
+__global__ void __launch_bounds__(NT, 3) k_cols(Loc loc, u32 per) {
     extern __shared__ u64 sm[];
     const KeyDev &K = loc.k(blockIdx.y);
     u32 l1, l2;
@@ -241,7 +240,7 @@ __global__ void __launch_bounds__(NT) k_cols(Loc loc, u32 per) {
 // Row pass: block (x = p * (N1 / TR) + chunk, y) transforms rows
 // [chunk TR, (chunk + 1) TR) of polynomial p of row y.
 template <bool INV, class Loc>
-__global__ void __launch_bounds__(NT) k_rows(Loc loc, u32 per) {
+__global__ void __launch_bounds__(NT, 3) k_rows(Loc loc, u32 per) {
     extern __shared__ u64 sm[];
     const KeyDev &K = loc.k(blockIdx.y);
     u32 l1, l2;
@@ -254,16 +253,27 @@ __global__ void __launch_bounds__(NT) k_rows(Loc loc, u32 per) {
     else rows_body<INV, false>(sm, a, r0, l1, l2, K);
 }
 
+// Dynamic shared memory of a kernel, with the largest shared-memory carveout
+// (several blocks of these kernels share an SM).
+template <class F>
+bm_status smem_attrs(F *kernel, size_t bytes) {
+    BM_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    BM_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
+    return BM_OK;
+}
+
 // The row pass alone (the step's inverse starts with it).
 template <class Loc>
 bm_status transform_rows(Loc loc, u32 rows, u32 per, u32 N, bool inverse, cudaStream_t st) {
     u32 logN = 0;
     while ((1u << logN) < N) logN++;
     const u32 l1 = logN / 2, l2 = logN - l1, N1 = 1u << l1, N2 = 1u << l2;
-    if (N1 < TR || N2 < TC) return BM_EINVAL;
+    if (l1 < 7 || l2 > 8) return BM_EINVAL;     // passes of 7 or 8 stages (pass_stages)
     const size_t smr = (size_t)TR * (N2 + N2 / 16) * 8;
     auto kr = inverse ? k_rows<true, Loc> : k_rows<false, Loc>;
-    BM_CUDA_TRY(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    bm_status s0 = smem_attrs(kr, smr);
+    if (s0 != BM_OK) return s0;
     kr<<<dim3(per * (N1 / TR), rows), NT, smr, st>>>(loc, per);
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
@@ -274,12 +284,13 @@ bm_status transform(Loc loc, u32 rows, u32 per, u32 N, bool inverse, cudaStream_
     u32 logN = 0;
     while ((1u << logN) < N) logN++;
     const u32 l1 = logN / 2, l2 = logN - l1, N1 = 1u << l1, N2 = 1u << l2;
-    if (N1 < TR || N2 < TC) return BM_EINVAL;
+    if (l1 < 7 || l2 > 8) return BM_EINVAL;     // passes of 7 or 8 stages (pass_stages)
     const size_t smc = (size_t)N1 * TC * 8, smr = (size_t)TR * (N2 + N2 / 16) * 8;
     auto kc = inverse ? k_cols<true, Loc> : k_cols<false, Loc>;
     auto kr = inverse ? k_rows<true, Loc> : k_rows<false, Loc>;
-    BM_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
-    BM_CUDA_TRY(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    bm_status s0 = smem_attrs(kc, smc);
+    if (s0 == BM_OK) s0 = smem_attrs(kr, smr);
+    if (s0 != BM_OK) return s0;
     const dim3 gc(per * (N2 / TC), rows), gr(per * (N1 / TR), rows);
     if (!inverse) {
         kc<<<gc, NT, smc, st>>>(loc, per);
@@ -346,16 +357,16 @@ __device__ void digits_cols_body(u64 *sm, const DevJob &J, const KeyDev &K, cons
         Dt[x] = sub_mod(rotated_coeff(row, i, e, N, Q), row[i], Q);
     }
     for (u32 d = 0; d < lB; d++) {
-        __syncthreads();     // the difference is complete; the previous digit's tile is stored
-        for (u32 x = threadIdx.x; x < N1 * TC; x += NT) tile[x] = (Dt[x] >> (d * log2B)) & Bmask;
-        __syncthreads();
-        pass_stages<false, false, QL>(tile, l1, TC, 0, 1, 0, K.twp, A);
-        u64 *a = X + (size_t)(pair * lB + d) * N;
-        for (u32 x = threadIdx.x; x < N1 * TC; x += NT) a[c0 + x % TC + (size_t)N2 * (x / TC)] = tile[x];
+        __syncthreads();     // the difference is complete; the previous digit is out of the tile
+        const u32 sh = d * log2B;
+        u64 *a = X + (size_t)(pair * lB + d) * N + c0;
+        pass_stages<false, false, QL>(
+            tile, l1, TC, 0, 1, 0, K.twp, A, [&](u32 q, u32 e) { return (Dt[q + TC * e] >> sh) & Bmask; },
+            [&](u32 q, u32 e, u64 v) { a[q + (size_t)N2 * e] = v; });
     }
 }
 
-__global__ void __launch_bounds__(NT) k_digits_cols(const DevJob *__restrict__ jobs, const u64 *__restrict__ ct_in,
+__global__ void __launch_bounds__(NT, 3) k_digits_cols(const DevJob *__restrict__ jobs, const u64 *__restrict__ ct_in,
                                                     u64 *ws, u32 k, const u32 *status) {
     extern __shared__ u64 sm[];
     const DevJob &J = jobs[blockIdx.y];
@@ -379,32 +390,42 @@ __device__ void rows_mac_body(u64 *sm, const DevJob &J, const KeyDev &K, u64 *ws
     split_log(K.logN, l1, l2);
     const u32 N = J.N, N1 = 1u << l1, N2 = 1u << l2, qs = row_stride(N2);
     const u32 r0 = blockIdx.x * trm, nc = 4 * K.l_B, lb = K.lbits, w = trm * N2;
-    const u32 lw = __ffs(w) - 1;
     const size_t vec = (size_t)2 * N;
     const u64 *X = ws + J.acc_off + 3 * vec;
     u64 *sums = ws + J.acc_off + 2 * vec;
     // row q = c trm + rr of the tile is row r0 + rr of digit polynomial c
-    for (u32 x = threadIdx.x; x < nc * w; x += NT)
-        sm[row_at(x >> l2, qs, x & (N2 - 1))] = X[(size_t)(x >> lw) * N + (size_t)r0 * N2 + (x & (w - 1))];
+    const u32 ltrm = __ffs(trm) - 1;
+    const u64 *Xr = X + (size_t)r0 * N2;
+    pass_stages<false, true, QL>(
+        sm, l2, nc * trm, qs, N1 + r0, trm - 1, K.twp, A,
+        [&](u32 q, u32 e) { return Xr[(size_t)(q >> ltrm) * N + ((q & (trm - 1)) << l2) + e]; },
+        [&](u32 q, u32 e, u64 v) { sm[row_at(q, qs, e)] = v; });
     __syncthreads();
-    pass_stages<false, true, QL>(sm, l2, nc * trm, qs, N1 + r0, trm - 1, K.twp, A);
     const u64 *bk = K.bsk + (size_t)k * 2 * (2 * K.l_B * 2 * N);
     for (u32 pos = threadIdx.x; pos < w; pos += NT) {
         const size_t i = (size_t)r0 * N2 + pos;
         const u32 rr = pos >> l2, o = pos & (N2 - 1);
         u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
-        for (u32 c = 0; c < nc; c++) {
-            const u64 x = sm[row_at(c * trm + rr, qs, o)];
-            const ulonglong2 wv = __ldg(reinterpret_cast<const ulonglong2 *>(bk + (size_t)c * 2 * N + 2 * i));
-            mac128(lo0, hi0, x, (wv.x & 0xffffffffull) + ((wv.y & 0xffffffffull) << lb));
-            mac128(lo1, hi1, x, (wv.x >> 32) + ((wv.y >> 32) << lb));
+        for (u32 c = 0; c < nc; c += 4) {      // nc = 4 l_B: four combos' loads in flight
+            ulonglong2 wv[4];
+            u64 x[4];
+#pragma unroll
+            for (u32 u = 0; u < 4; u++) {
+                wv[u] = __ldg(reinterpret_cast<const ulonglong2 *>(bk + (size_t)(c + u) * 2 * N + 2 * i));
+                x[u] = sm[row_at((c + u) * trm + rr, qs, o)];
+            }
+#pragma unroll
+            for (u32 u = 0; u < 4; u++) {
+                mac128(lo0, hi0, x[u], (wv[u].x & 0xffffffffull) + ((wv[u].y & 0xffffffffull) << lb));
+                mac128(lo1, hi1, x[u], (wv[u].x >> 32) + ((wv[u].y >> 32) << lb));
+            }
         }
         sums[i] = reduce128(lo0, hi0, K.mq);
         sums[N + i] = reduce128(lo1, hi1, K.mq);
     }
 }
 
-__global__ void __launch_bounds__(NT) k_rows_mac(const DevJob *__restrict__ jobs, u64 *ws, u32 k, u32 trm) {
+__global__ void __launch_bounds__(NT, 3) k_rows_mac(const DevJob *__restrict__ jobs, u64 *ws, u32 k, u32 trm) {
     extern __shared__ u64 sm[];
     const DevJob &J = jobs[blockIdx.y];
     const KeyDev &K = *J.key;
@@ -428,16 +449,15 @@ __device__ void cols_inv_update_body(u64 *sm, const DevJob &J, const KeyDev &K, 
     const u64 *cur = ws + J.acc_off + ((k & 1) ? vec : 0) + (size_t)comp * N;
     u64 *nxt = ws + J.acc_off + ((k & 1) ? 0 : vec) + (size_t)comp * N;
     const u64 *a = ws + J.acc_off + 2 * vec + (size_t)comp * N;
-    for (u32 x = threadIdx.x; x < N1 * TC; x += NT) sm[x] = a[c0 + x % TC + (size_t)N2 * (x / TC)];
-    __syncthreads();
-    pass_stages<true, false, QL>(sm, l1, TC, 0, 1, 0, K.itwp, A);
-    for (u32 x = threadIdx.x; x < N1 * TC; x += NT) {
-        const size_t i = c0 + x % TC + (size_t)N2 * (x / TC);
-        nxt[i] = add_mod(cur[i], A.inv_final(sm[x]), Q);
-    }
+    pass_stages<true, false, QL>(
+        sm, l1, TC, 0, 1, 0, K.itwp, A, [&](u32 q, u32 e) { return a[c0 + q + (size_t)N2 * e]; },
+        [&](u32 q, u32 e, u64 v) {
+            const size_t i = c0 + q + (size_t)N2 * e;
+            nxt[i] = add_mod(cur[i], A.inv_final(v), Q);
+        });
 }
 
-__global__ void __launch_bounds__(NT) k_cols_inv_update(const DevJob *__restrict__ jobs, u64 *ws, u32 k) {
+__global__ void __launch_bounds__(NT, 3) k_cols_inv_update(const DevJob *__restrict__ jobs, u64 *ws, u32 k) {
     extern __shared__ u64 sm[];
     const DevJob &J = jobs[blockIdx.y];
     const KeyDev &K = *J.key;
@@ -554,10 +574,11 @@ bm_status bm_launch_br_big(u32 N, const DevJob *jobs, uint32_t cnt, u32 steps, c
     while (2 * trm * ncmax * N2 <= 8192 && 2 * trm <= N1) trm *= 2;     // a power of two
     const size_t sm_dc = (size_t)2 * N1 * bign::TC * 8, sm_rm = (size_t)ncmax * trm * (N2 + N2 / 16) * 8,
                  sm_ci = (size_t)N1 * bign::TC * 8;
-    BM_CUDA_TRY(cudaFuncSetAttribute(bign::k_digits_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_dc));
-    BM_CUDA_TRY(cudaFuncSetAttribute(bign::k_rows_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rm));
-    BM_CUDA_TRY(cudaFuncSetAttribute(bign::k_cols_inv_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sm_ci));
+    if (l1 < 7 || l2 > 8) return BM_EINVAL;     // passes of 7 or 8 stages (pass_stages)
+    bm_status s0;
+    if ((s0 = bign::smem_attrs(bign::k_digits_cols, sm_dc)) != BM_OK) return s0;
+    if ((s0 = bign::smem_attrs(bign::k_rows_mac, sm_rm)) != BM_OK) return s0;
+    if ((s0 = bign::smem_attrs(bign::k_cols_inv_update, sm_ci)) != BM_OK) return s0;
     const dim3 g_dc(4 * (N2 / bign::TC), cnt), g_rm(N1 / trm, cnt), g_ci(2 * (N2 / bign::TC), cnt);
     for (u32 k = 0; k < steps; k++) {
         bign::k_digits_cols<<<g_dc, bign::NT, sm_dc, st>>>(jobs, ct_in, ws_acc, k, status);
