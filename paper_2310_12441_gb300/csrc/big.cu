@@ -24,7 +24,10 @@ namespace bign {
 constexpr u32 TC = 16;     // columns per block of the column pass
 constexpr u32 TR = 32;     // rows per block of the row pass
 constexpr u32 NT = 256;    // threads per block (three blocks per SM: at most 80 registers)
-constexpr u32 RMAX = 4;    // stages per register chunk (16 values per work item)
+
+// Threads per block of a column pass: the work items of its four-stage
+// chunk, TC 2^(log N1 - 4) (128 at N1 = 128), at most NT.
+inline u32 col_threads(u32 l1) { return (TC << (l1 - 4)) < NT ? NT / 2 : NT; }
 
 // Polynomial p of launch row y: a flat array of polynomials, or the
 // digit / sum buffers of job y (after the job's three [2][N] accumulator
@@ -84,6 +87,17 @@ struct Arith {
             Y = mul_shoup(U + Q - V, W, Wsh, Q);
         }
     }
+    // forward butterfly of the first stage on digits X, Y < 2^32 (QL): Y W
+    // by the one-quotient product (below 3Q), both outputs below 4Q + X
+    __device__ __forceinline__ void fwd_small(u64 &X, u64 &Y, u64 W, u64 Wsh) const {
+        if constexpr (QL) {
+            const u64 T = small_mul_qlow1(Y, W, Wsh, c), x = X;
+            X = add64c(x, T);
+            Y = sub64c(add64c(x, fourQ), T);
+        } else {
+            fwd(X, Y, W, Wsh);
+        }
+    }
     // the last forward stage's value (below 8Q) into [0, Q)
     __device__ __forceinline__ u64 fwd_final(u64 x) const {
         if constexpr (QL) return csub63(csub63(csub63(x, fourQ), 2 * Q), Q);
@@ -104,8 +118,8 @@ __device__ __forceinline__ u32 row_stride(u32 N2) { return N2 + N2 / 16; }
 __device__ __forceinline__ u32 row_at(u32 q, u32 qs, u32 e) { return q * qs + e + (e >> 4); }
 
 // Stage s0 + r of a register chunk (see pass_chunk), r a constant so that
-// every index into x is one.
-template <int R, int r, bool INV, bool QL>
+// every index into x is one.  SM0: stage 0 of a forward transform of digits.
+template <int R, int r, bool INV, bool QL, bool SM0>
 __device__ __forceinline__ void chunk_stage(u64 (&x)[1 << R], const u64 *__restrict__ tp, u32 tb, u32 s0, u32 G,
                                             const Arith<QL> &A) {
     constexpr u32 h = 1u << (R - 1 - r);
@@ -115,18 +129,19 @@ __device__ __forceinline__ void chunk_stage(u64 (&x)[1 << R], const u64 *__restr
 #pragma unroll
         for (u32 j = 0; j < h; j++) {
             if constexpr (INV) A.inv(x[gi * 2 * h + j], x[gi * 2 * h + j + h], W.x, W.y);
+            else if constexpr (SM0 && r == 0) A.fwd_small(x[gi * 2 * h + j], x[gi * 2 * h + j + h], W.x, W.y);
             else A.fwd(x[gi * 2 * h + j], x[gi * 2 * h + j + h], W.x, W.y);
         }
     }
 }
 
 // The chunk's stages in order: r = 0 .. R - 1 forward, R - 1 .. 0 inverse.
-template <int R, int k, bool INV, bool QL>
+template <int R, int k, bool INV, bool QL, bool SM0>
 __device__ __forceinline__ void chunk_stages(u64 (&x)[1 << R], const u64 *__restrict__ tp, u32 tb, u32 s0, u32 G,
                                              const Arith<QL> &A) {
     if constexpr (k < R) {
-        chunk_stage<R, INV ? R - 1 - k : k, INV, QL>(x, tp, tb, s0, G, A);
-        chunk_stages<R, k + 1, INV, QL>(x, tp, tb, s0, G, A);
+        chunk_stage<R, INV ? R - 1 - k : k, INV, QL, SM0>(x, tp, tb, s0, G, A);
+        chunk_stages<R, k + 1, INV, QL, SM0>(x, tp, tb, s0, G, A);
     }
 }
 
@@ -141,13 +156,14 @@ __device__ __forceinline__ void chunk_stages(u64 (&x)[1 << R], const u64 *__rest
 // ROW: J varies fastest across threads, then G, then the row; columns: the
 // column varies fastest.  ld(q, e) and st(q, e, v) fetch and put element e
 // of sequence q (the shared-memory tile, or global memory for the first and
-// last chunk of a pass).
-template <int R, bool INV, bool ROW, bool QL, class Ld, class St>
+// last chunk of a pass).  NTH threads per block; SM0: the chunk starts at
+// stage 0 of a forward transform of digits below 2^32.
+template <int R, bool INV, bool ROW, bool QL, u32 NTH, bool SM0, class Ld, class St>
 __device__ __forceinline__ void pass_chunk(u32 l, u32 s0, u32 nseq, u32 tb0, u32 qmask, const u64 *__restrict__ tp,
                                            const Arith<QL> &A, Ld &ld, St &st) {
     constexpr u32 V = 1u << R;
     const u32 lJ = l - s0 - R, items = nseq << (l - R);
-    for (u32 w = threadIdx.x; w < items; w += NT) {
+    for (u32 w = threadIdx.x; w < items; w += NTH) {
         u32 q, G, J;
         if constexpr (ROW) {
             J = w & ((1u << lJ) - 1);
@@ -162,7 +178,7 @@ __device__ __forceinline__ void pass_chunk(u32 l, u32 s0, u32 nseq, u32 tb0, u32
         u64 x[V];
 #pragma unroll
         for (u32 i = 0; i < V; i++) x[i] = ld(q, e0 + (i << lJ));
-        chunk_stages<R, 0, INV, QL>(x, tp, tb0 + (q & qmask), s0, G, A);
+        chunk_stages<R, 0, INV, QL, SM0>(x, tp, tb0 + (q & qmask), s0, G, A);
 #pragma unroll
         for (u32 i = 0; i < V; i++) st(q, e0 + (i << lJ), x[i]);
     }
@@ -173,8 +189,9 @@ __device__ __forceinline__ void pass_chunk(u32 l, u32 s0, u32 nseq, u32 tb0, u32
 // (the inverse takes them in the other order), one barrier between them.
 // The first chunk takes its values through ld_first, the second puts them
 // through st_last; in between they sit in the tile sm (row tiles of stride
-// qs).  The caller synchronises before sm is reused.
-template <bool INV, bool ROW, bool QL, class Ld, class St>
+// qs).  The caller synchronises before sm is reused.  NTH threads per
+// block; SM0: a forward transform of digits below 2^32.
+template <bool INV, bool ROW, bool QL, u32 NTH = NT, bool SM0 = false, class Ld, class St>
 __device__ __forceinline__ void pass_stages(u64 *sm, u32 l, u32 nseq, u32 qs, u32 tb0, u32 qmask,
                                             const u64 *__restrict__ tp, const Arith<QL> &A, Ld &&ld_first,
                                             St &&st_last) {
@@ -184,26 +201,26 @@ __device__ __forceinline__ void pass_stages(u64 *sm, u32 l, u32 nseq, u32 qs, u3
         else sm[q + TC * e] = v;
     };
     if constexpr (!INV) {
-        pass_chunk<4, INV, ROW, QL>(l, 0, nseq, tb0, qmask, tp, A, ld_first, st_sm);
+        pass_chunk<4, INV, ROW, QL, NTH, SM0>(l, 0, nseq, tb0, qmask, tp, A, ld_first, st_sm);
         __syncthreads();
-        if (l == 8) pass_chunk<4, INV, ROW, QL>(l, 4, nseq, tb0, qmask, tp, A, ld_sm, st_last);
-        else pass_chunk<3, INV, ROW, QL>(l, 4, nseq, tb0, qmask, tp, A, ld_sm, st_last);
+        if (l == 8) pass_chunk<4, INV, ROW, QL, NTH, false>(l, 4, nseq, tb0, qmask, tp, A, ld_sm, st_last);
+        else pass_chunk<3, INV, ROW, QL, NTH, false>(l, 4, nseq, tb0, qmask, tp, A, ld_sm, st_last);
     } else {
-        if (l == 8) pass_chunk<4, INV, ROW, QL>(l, 4, nseq, tb0, qmask, tp, A, ld_first, st_sm);
-        else pass_chunk<3, INV, ROW, QL>(l, 4, nseq, tb0, qmask, tp, A, ld_first, st_sm);
+        if (l == 8) pass_chunk<4, INV, ROW, QL, NTH, false>(l, 4, nseq, tb0, qmask, tp, A, ld_first, st_sm);
+        else pass_chunk<3, INV, ROW, QL, NTH, false>(l, 4, nseq, tb0, qmask, tp, A, ld_first, st_sm);
         __syncthreads();
-        pass_chunk<4, INV, ROW, QL>(l, 0, nseq, tb0, qmask, tp, A, ld_sm, st_last);
+        pass_chunk<4, INV, ROW, QL, NTH, false>(l, 0, nseq, tb0, qmask, tp, A, ld_sm, st_last);
     }
 }
 
 // Column pass of TC columns from c0 of polynomial a, in place.  smem: N1 TC
 // words.  The forward pass leaves its values lazy (the row pass continues
 // them); the inverse pass ends the transform.
-template <bool INV, bool QL>
+template <bool INV, bool QL, u32 NTH>
 __device__ void cols_body(u64 *sm, u64 *a, u32 c0, u32 l1, u32 N2, const KeyDev &K) {
     const Arith<QL> A(K.mq.Q);
     u64 *col = a + c0;
-    pass_stages<INV, false, QL>(
+    pass_stages<INV, false, QL, NTH>(
         sm, l1, TC, 0, 1, 0, INV ? K.itwp : K.twp, A, [&](u32 q, u32 e) { return col[q + (size_t)N2 * e]; },
         [&](u32 q, u32 e, u64 v) { col[q + (size_t)N2 * e] = INV ? A.inv_final(v) : v; });
 }
@@ -223,8 +240,8 @@ __device__ void rows_body(u64 *sm, u64 *a, u32 r0, u32 l1, u32 l2, const KeyDev 
 
 // Column pass: block (x = p * (N2 / TC) + chunk, y) transforms columns
 // [chunk TC, (chunk + 1) TC) of polynomial p of row y.
-template <bool INV, class Loc>
-__global__ void __launch_bounds__(NT, 3) k_cols(Loc loc, u32 per) {
+template <bool INV, class Loc, u32 NTH>
+__global__ void __launch_bounds__(NTH, 3 * NT / NTH) k_cols(Loc loc, u32 per) {
     extern __shared__ u64 sm[];
     const KeyDev &K = loc.k(blockIdx.y);
     u32 l1, l2;
@@ -233,8 +250,8 @@ __global__ void __launch_bounds__(NT, 3) k_cols(Loc loc, u32 per) {
     const u32 p = blockIdx.x / chunks, c0 = (blockIdx.x % chunks) * TC;
     if (p >= per || p >= loc.count(blockIdx.y)) return;
     u64 *a = loc.poly(blockIdx.y, p);
-    if (qlow1_of(K.mq.Q)) cols_body<INV, true>(sm, a, c0, l1, N2, K);
-    else cols_body<INV, false>(sm, a, c0, l1, N2, K);
+    if (qlow1_of(K.mq.Q)) cols_body<INV, true, NTH>(sm, a, c0, l1, N2, K);
+    else cols_body<INV, false, NTH>(sm, a, c0, l1, N2, K);
 }
 
 // Row pass: block (x = p * (N1 / TR) + chunk, y) transforms rows
@@ -286,18 +303,20 @@ bm_status transform(Loc loc, u32 rows, u32 per, u32 N, bool inverse, cudaStream_
     const u32 l1 = logN / 2, l2 = logN - l1, N1 = 1u << l1, N2 = 1u << l2;
     if (l1 < 7 || l2 > 8) return BM_EINVAL;     // passes of 7 or 8 stages (pass_stages)
     const size_t smc = (size_t)N1 * TC * 8, smr = (size_t)TR * (N2 + N2 / 16) * 8;
-    auto kc = inverse ? k_cols<true, Loc> : k_cols<false, Loc>;
+    const u32 nc = col_threads(l1);
+    auto kc = nc == NT ? (inverse ? k_cols<true, Loc, NT> : k_cols<false, Loc, NT>)
+                       : (inverse ? k_cols<true, Loc, NT / 2> : k_cols<false, Loc, NT / 2>);
     auto kr = inverse ? k_rows<true, Loc> : k_rows<false, Loc>;
     bm_status s0 = smem_attrs(kc, smc);
     if (s0 == BM_OK) s0 = smem_attrs(kr, smr);
     if (s0 != BM_OK) return s0;
     const dim3 gc(per * (N2 / TC), rows), gr(per * (N1 / TR), rows);
     if (!inverse) {
-        kc<<<gc, NT, smc, st>>>(loc, per);
+        kc<<<gc, nc, smc, st>>>(loc, per);
         kr<<<gr, NT, smr, st>>>(loc, per);
     } else {
         kr<<<gr, NT, smr, st>>>(loc, per);
-        kc<<<gc, NT, smc, st>>>(loc, per);
+        kc<<<gc, nc, smc, st>>>(loc, per);
     }
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
@@ -331,7 +350,7 @@ __global__ void k_init(const DevJob *__restrict__ jobs, const u64 *__restrict__ 
 // columns, then for every digit transforms the digit columns (stages
 // 0 .. log N1 - 1) into the job's digit polynomial pair l_B + d.  smem:
 // 2 N1 TC words (the difference, the digit tile).
-template <bool QL>
+template <bool QL, u32 NTH>
 __device__ void digits_cols_body(u64 *sm, const DevJob &J, const KeyDev &K, const u64 *__restrict__ ct_in, u64 *ws,
                                  u32 k, const u32 *status) {
     const Arith<QL> A(K.mq.Q);
@@ -352,7 +371,7 @@ __device__ void digits_cols_body(u64 *sm, const DevJob &J, const KeyDev &K, cons
     mmpm_row(sgn == 0 ? (ak ? qp - ak : 0u) : ak, 0, 1, 2 * N, J.gS, gpre, src, e);
     const u64 *row = cur + (size_t)comp * N;
     u64 *Dt = sm, *tile = sm + N1 * TC;
-    for (u32 x = threadIdx.x; x < N1 * TC; x += NT) {
+    for (u32 x = threadIdx.x; x < N1 * TC; x += NTH) {
         const u32 i = c0 + x % TC + N2 * (x / TC);
         Dt[x] = sub_mod(rotated_coeff(row, i, e, N, Q), row[i], Q);
     }
@@ -360,20 +379,21 @@ __device__ void digits_cols_body(u64 *sm, const DevJob &J, const KeyDev &K, cons
         __syncthreads();     // the difference is complete; the previous digit is out of the tile
         const u32 sh = d * log2B;
         u64 *a = X + (size_t)(pair * lB + d) * N + c0;
-        pass_stages<false, false, QL>(
+        pass_stages<false, false, QL, NTH, true>(
             tile, l1, TC, 0, 1, 0, K.twp, A, [&](u32 q, u32 e) { return (Dt[q + TC * e] >> sh) & Bmask; },
             [&](u32 q, u32 e, u64 v) { a[q + (size_t)N2 * e] = v; });
     }
 }
 
-__global__ void __launch_bounds__(NT, 3) k_digits_cols(const DevJob *__restrict__ jobs, const u64 *__restrict__ ct_in,
+template <u32 NTH>
+__global__ void __launch_bounds__(NTH, 3 * NT / NTH) k_digits_cols(const DevJob *__restrict__ jobs, const u64 *__restrict__ ct_in,
                                                     u64 *ws, u32 k, const u32 *status) {
     extern __shared__ u64 sm[];
     const DevJob &J = jobs[blockIdx.y];
     const KeyDev &K = *J.key;
     if (k >= K.n) return;
-    if (qlow1_of(K.mq.Q)) digits_cols_body<true>(sm, J, K, ct_in, ws, k, status);
-    else digits_cols_body<false>(sm, J, K, ct_in, ws, k, status);
+    if (qlow1_of(K.mq.Q)) digits_cols_body<true, NTH>(sm, J, K, ct_in, ws, k, status);
+    else digits_cols_body<false, NTH>(sm, J, K, ct_in, ws, k, status);
 }
 
 // Forward row pass of all 4 l_B digit polynomials on rows [r0, r0 + trm)
@@ -437,19 +457,19 @@ __global__ void __launch_bounds__(NT, 3) k_rows_mac(const DevJob *__restrict__ j
 // Inverse column pass of the two row sums (stages log N1 - 1 .. 0) fused
 // with the accumulator update of step k.  Block (x = comp (N2 / TC) +
 // chunk, y = job); smem N1 TC words.
-template <bool QL>
+template <bool QL, u32 NTH>
 __device__ void cols_inv_update_body(u64 *sm, const DevJob &J, const KeyDev &K, u64 *ws, u32 k) {
     const Arith<QL> A(K.mq.Q);
     u32 l1, l2;
     split_log(K.logN, l1, l2);
-    const u32 N = J.N, N1 = 1u << l1, N2 = 1u << l2, chunks = N2 / TC;
+    const u32 N = J.N, N2 = 1u << l2, chunks = N2 / TC;
     const u32 comp = blockIdx.x / chunks, c0 = (blockIdx.x % chunks) * TC;
     const u64 Q = K.mq.Q;
     const size_t vec = (size_t)2 * N;
     const u64 *cur = ws + J.acc_off + ((k & 1) ? vec : 0) + (size_t)comp * N;
     u64 *nxt = ws + J.acc_off + ((k & 1) ? 0 : vec) + (size_t)comp * N;
     const u64 *a = ws + J.acc_off + 2 * vec + (size_t)comp * N;
-    pass_stages<true, false, QL>(
+    pass_stages<true, false, QL, NTH>(
         sm, l1, TC, 0, 1, 0, K.itwp, A, [&](u32 q, u32 e) { return a[c0 + q + (size_t)N2 * e]; },
         [&](u32 q, u32 e, u64 v) {
             const size_t i = c0 + q + (size_t)N2 * e;
@@ -457,13 +477,14 @@ __device__ void cols_inv_update_body(u64 *sm, const DevJob &J, const KeyDev &K, 
         });
 }
 
-__global__ void __launch_bounds__(NT, 3) k_cols_inv_update(const DevJob *__restrict__ jobs, u64 *ws, u32 k) {
+template <u32 NTH>
+__global__ void __launch_bounds__(NTH, 3 * NT / NTH) k_cols_inv_update(const DevJob *__restrict__ jobs, u64 *ws, u32 k) {
     extern __shared__ u64 sm[];
     const DevJob &J = jobs[blockIdx.y];
     const KeyDev &K = *J.key;
     if (k >= K.n) return;
-    if (qlow1_of(K.mq.Q)) cols_inv_update_body<true>(sm, J, K, ws, k);
-    else cols_inv_update_body<false>(sm, J, K, ws, k);
+    if (qlow1_of(K.mq.Q)) cols_inv_update_body<true, NTH>(sm, J, K, ws, k);
+    else cols_inv_update_body<false, NTH>(sm, J, K, ws, k);
 }
 
 // RGSW row finish of key generation (the formula of keygen.cu, elementwise):
@@ -576,18 +597,21 @@ bm_status bm_launch_br_big(u32 N, const DevJob *jobs, uint32_t cnt, u32 steps, c
                  sm_ci = (size_t)N1 * bign::TC * 8;
     if (l1 < 7 || l2 > 8) return BM_EINVAL;     // passes of 7 or 8 stages (pass_stages)
     bm_status s0;
-    if ((s0 = bign::smem_attrs(bign::k_digits_cols, sm_dc)) != BM_OK) return s0;
+    const u32 nc = bign::col_threads(l1);
+    auto kdc = nc == bign::NT ? bign::k_digits_cols<bign::NT> : bign::k_digits_cols<bign::NT / 2>;
+    auto kci = nc == bign::NT ? bign::k_cols_inv_update<bign::NT> : bign::k_cols_inv_update<bign::NT / 2>;
+    if ((s0 = bign::smem_attrs(kdc, sm_dc)) != BM_OK) return s0;
     if ((s0 = bign::smem_attrs(bign::k_rows_mac, sm_rm)) != BM_OK) return s0;
-    if ((s0 = bign::smem_attrs(bign::k_cols_inv_update, sm_ci)) != BM_OK) return s0;
+    if ((s0 = bign::smem_attrs(kci, sm_ci)) != BM_OK) return s0;
     const dim3 g_dc(4 * (N2 / bign::TC), cnt), g_rm(N1 / trm, cnt), g_ci(2 * (N2 / bign::TC), cnt);
     for (u32 k = 0; k < steps; k++) {
-        bign::k_digits_cols<<<g_dc, bign::NT, sm_dc, st>>>(jobs, ct_in, ws_acc, k, status);
+        kdc<<<g_dc, nc, sm_dc, st>>>(jobs, ct_in, ws_acc, k, status);
         bign::k_rows_mac<<<g_rm, bign::NT, sm_rm, st>>>(jobs, ws_acc, k, trm);
         BM_CUDA_TRY(cudaGetLastError());
         // inverse: row pass of the two sums, then the column pass with the update
         bm_status s = bign::transform_rows(bign::LocJobs{jobs, ws_acc, 1}, cnt, 2, N, true, st);
         if (s != BM_OK) return s;
-        bign::k_cols_inv_update<<<g_ci, bign::NT, sm_ci, st>>>(jobs, ws_acc, k);
+        kci<<<g_ci, nc, sm_ci, st>>>(jobs, ws_acc, k);
         BM_CUDA_TRY(cudaGetLastError());
     }
     return BM_OK;
